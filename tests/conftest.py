@@ -1,0 +1,38 @@
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def pytest_configure(config):
+    config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a)")
+
+
+def load_golden(name):
+    """Parse a tests/golden/*.txt fixture into {section: [[float]]} plus m, n."""
+    path = os.path.join(ROOT, "tests", "golden", name)
+    out, cur = {}, None
+    with open(path) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            if line.startswith("m "):
+                parts = line.split()
+                out["m"], out["n"] = int(parts[1]), int(parts[3])
+                continue
+            if line.replace("_", "").isalnum() and not line[0].isdigit() and not line[0] == "-":
+                cur = line
+                out[cur] = []
+                continue
+            out[cur].append([float(v) for v in line.split()])
+    return out
+
+
+@pytest.fixture
+def golden():
+    return load_golden

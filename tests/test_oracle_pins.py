@@ -1,0 +1,374 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+None of these compare the oracle with itself: each check is a closed form, a
+library routine (LAPACK), a 60-digit computation, a special case that reduces to
+a textbook algorithm, or an identity of the method (Sec. 1, Alg. 1, Alg. 2,
+eq. (1), Table 1).  The mutation tests at the end plant plausible mistakes in
+the oracle and check that the pins catch them.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import bcgs as ob
+from paper_2507_21791_gb300 import synth
+
+U64 = np.finfo(np.float64).eps / 2
+VARIANTS = list(oracle.VARIANTS)
+
+
+def sign_normalized_lapack_qr(X):
+    Q, R = np.linalg.qr(X)
+    d = np.where(np.diag(R) < 0, -1.0, 1.0)
+    return Q * d[None, :], d[:, None] * R
+
+
+# ---------------------------------------------------------------- Householder
+
+@pytest.mark.parametrize("m,s", [(1, 1), (5, 1), (8, 8), (50, 7), (300, 24), (1000, 16)])
+def test_householder_matches_lapack(m, s):
+    X = np.random.default_rng(m * 31 + s).standard_normal((m, s))
+    Q, R = oracle.householder_qr(X)
+    Ql, Rl = sign_normalized_lapack_qr(X)
+    k = oracle.kappa(X)
+    tol = 20 * max(m, 8) ** 0.5 * s * k * U64
+    assert np.abs(R - Rl).max() / np.abs(Rl).max() < tol
+    assert np.abs(Q - Ql).max() < tol
+    assert np.all(np.diag(R) > 0)
+    assert np.allclose(np.tril(R, -1), 0.0, atol=0)
+
+
+def mp_qr(X, dps=60):
+    """60-digit economic QR by Cholesky of the exactly formed Gram matrix."""
+    mpmath = pytest.importorskip("mpmath")
+    mp = mpmath.mp
+    mp.dps = dps
+    m, n = X.shape
+    A = mp.matrix([[mp.mpf(float(v)) for v in row] for row in X])
+    G = A.T * A
+    L = mp.cholesky(G)
+    R = L.T
+    Q = A * mp.inverse(R)
+    Rf = np.array([[float(R[i, j]) for j in range(n)] for i in range(n)])
+    Qf = np.array([[float(Q[i, j]) for j in range(n)] for i in range(m)])
+    return Qf, Rf
+
+
+@pytest.mark.parametrize("kappa", [1e1, 1e6])
+def test_householder_matches_60_digit_qr(kappa):
+    X = synth.make_matrix_np(14, 6, kappa, seed=7)
+    Qe, Re = mp_qr(X)
+    Q, R = oracle.householder_qr(X)
+    tol = 50 * 6 * kappa * U64
+    assert np.linalg.norm(R - Re) / np.linalg.norm(Re) < tol
+    assert np.abs(Q - Qe).max() < tol
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+@pytest.mark.parametrize("s", [1, 2, 4])
+def test_variants_match_60_digit_qr(variant, s):
+    X = synth.make_matrix_np(24, 8, 1e3, seed=11)
+    Qe, Re = mp_qr(X)
+    Q, R = oracle.factor(X, s, variant)
+    tol = 100 * 8 * 1e3 * U64
+    assert np.linalg.norm(R - Re) / np.linalg.norm(Re) < tol
+    assert np.abs(Q - Qe).max() < tol
+
+
+# ---------------------------------------------------------------- closed forms
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_hand_example(variant, golden):
+    g = golden("hand_4x2.txt")
+    X, R, Q = np.array(g["X"]), np.array(g["R"]), np.array(g["Q"])
+    for s in (1, 2):
+        Qo, Ro = oracle.factor(X, s, variant)
+        assert np.abs(Ro - R).max() < 1e-14 * 10
+        assert np.abs(Qo - Q).max() < 1e-15 * 10
+
+
+def hadamard_case(golden):
+    g = golden("hadamard_16x8.txt")
+    m, n = g["m"], g["n"]
+    h = np.array([[1.0]])
+    while h.shape[0] < m:
+        h = np.block([[h, h], [h, -h]])
+    Q0 = h[:, :n] / 4.0
+    R0 = np.array(g["R0"])
+    X = np.array(g["X4"]) / 4.0
+    assert np.array_equal(Q0 @ R0, X)  # exact in binary
+    return X, Q0, R0
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+@pytest.mark.parametrize("s", [1, 2, 4, 8])
+def test_hadamard_exact_recovery(variant, s, golden):
+    X, Q0, R0 = hadamard_case(golden)
+    Q, R = oracle.factor(X, s, variant)
+    k = oracle.kappa(R0)
+    tol = 10 * 8 * k * U64
+    assert np.abs(R - R0).max() / np.abs(R0).max() < tol
+    assert np.abs(Q - Q0).max() < tol
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+@pytest.mark.parametrize("kappa", [1e2, 1e6])
+def test_recovery_of_R0(variant, kappa):
+    """X = Q0 R0 with known orthonormal Q0 and positive-diagonal R0."""
+    m, n, s = 600, 32, 4
+    Q0, _ = np.linalg.qr(np.random.default_rng(3).standard_normal((m, n)))
+    R0 = synth.make_upper_triangular_np(n, kappa, seed=5)
+    X = Q0 @ R0
+    Q, R = oracle.factor(X, s, variant)
+    k = oracle.kappa(R0)
+    tol = 10 * n * k * U64
+    assert np.linalg.norm(R - R0) / np.linalg.norm(R0) < tol
+    assert np.abs(Q - Q0).max() < tol
+
+
+# ---------------------------------------------------------------- special cases
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_s_equals_n_is_tsqr(variant):
+    X = synth.make_matrix_np(200, 12, 1e5, seed=9)
+    Q, R = oracle.factor(X, 12, variant)
+    Qh, Rh = oracle.householder_qr(X)
+    assert np.array_equal(Q, Qh) and np.array_equal(R, Rh)
+    Ql, Rl = sign_normalized_lapack_qr(X)
+    assert np.abs(R - Rl).max() / np.abs(Rl).max() < 1e-10
+
+
+def textbook_cgs2(X):
+    """Column-wise classical Gram-Schmidt with one reorthogonalization (CGS2),
+    vector form, normalization by the 2-norm."""
+    m, n = X.shape
+    Q = np.zeros((m, n))
+    R = np.zeros((n, n))
+    for j in range(n):
+        x = X[:, j].copy()
+        r1 = Q[:, :j].T @ x
+        v = x - Q[:, :j] @ r1
+        r2 = Q[:, :j].T @ v
+        w = v - Q[:, :j] @ r2
+        nrm = np.sqrt(w @ w)
+        Q[:, j] = w / nrm
+        R[:j, j] = r1 + r2
+        R[j, j] = nrm
+    return Q, R
+
+
+def test_s_equals_1_is_cgs2():
+    """BCGSI+ with s = 1 is CGSI+ (Sec. 4, Table 2's normalization point)."""
+    X = synth.make_matrix_np(400, 20, 1e6, seed=13)
+    Q, R = oracle.bcgsi_plus(X, 1)
+    Qc, Rc = textbook_cgs2(X)
+    # The second pass's diagonal differs from ||v|| only by O(u) terms.
+    assert np.linalg.norm(R - Rc) / np.linalg.norm(Rc) < 1e-12
+    assert np.abs(Q - Qc).max() < 1e-9
+
+
+@pytest.mark.parametrize("kappa", [1e2, 1e4])
+def test_cross_variant_agreement(kappa):
+    X = synth.make_matrix_np(1500, 48, kappa, seed=17)
+    Rs = [oracle.factor(X, 8, v)[1] for v in VARIANTS]
+    for R in Rs[1:]:
+        assert np.linalg.norm(R - Rs[0]) / np.linalg.norm(Rs[0]) < 50 * 48 * kappa * U64
+
+
+# ---------------------------------------------------------------- invariants
+
+@pytest.mark.parametrize("variant", VARIANTS)
+@pytest.mark.parametrize("kappa", [1e2, 1e5, 1e8])
+def test_invariants(variant, kappa):
+    m, n, s = 3000, 64, 8
+    X = synth.make_matrix_np(m, n, kappa, seed=19)
+    if variant == "bcgsi+p-1s" and kappa >= 1e8:
+        pytest.skip("outside Table 1's O(u) kappa^2 <= 1 range")
+    Q, R = oracle.factor(X, s, variant)
+    assert np.array_equal(np.tril(R, -1), np.zeros_like(R))
+    assert np.all(np.diag(R) > 0)
+    nx2 = np.linalg.norm(X, 2) ** 2
+    assert np.linalg.norm(X.T @ X - R.T @ R, 2) / nx2 < 100 * n * U64
+    assert oracle.residual(X, Q, R) < 1e-14
+    assert oracle.loo(Q) < 1e-13
+
+
+def test_pythagorean_identity():
+    """T - S^T S equals (X - Q S)^T (X - Q S) for S = Q^T X (Alg. 1, the chol
+    step): its Cholesky factor equals the R factor of X - Q S."""
+    rng = np.random.default_rng(23)
+    Qk, _ = np.linalg.qr(rng.standard_normal((800, 16)))
+    X = synth.make_matrix_np(800, 4, 1e2, seed=29) + 0.3 * Qk[:, :4]
+    S = Qk.T @ X
+    T = X.T @ X
+    Rp = oracle.chol(T - S.T @ S)
+    _, Rh = oracle.householder_qr(X - Qk @ S)
+    assert np.linalg.norm(Rp - Rh) / np.linalg.norm(Rh) < 1e-12
+
+
+def eq1_error(fn):
+    """|Q_k^T X_{k+1} - fn(Y_kk, P_k, Y_{1:k-1,k}, Z_{k-1})| on a case where
+    U_k is far from orthogonal to Q_{k-1}, so every term of eq. (1) matters."""
+    rng = np.random.default_rng(31)
+    m, c, s = 900, 12, 4
+    Qprev, _ = np.linalg.qr(rng.standard_normal((m, c)))
+    Uk = rng.standard_normal((m, s)) + Qprev[:, :s]
+    Xn = rng.standard_normal((m, s)) + Qprev[:, s:2 * s]
+    Y = Qprev.T @ Uk
+    Om = Uk.T @ Uk
+    Ykk = oracle.chol(Om - Y.T @ Y)
+    Qk = (Uk - Qprev @ Y) @ np.linalg.inv(Ykk)
+    P = Uk.T @ Xn
+    Z = Qprev.T @ Xn
+    return np.abs(Qk.T @ Xn - fn(Ykk, P, Y, Z)).max()
+
+
+def test_eq1_delayed_projection_equals_direct():
+    """Eq. (1): Q_k^T X_{k+1} = Y_kk^{-T} (P_k - Y_{1:k-1,k}^T Z_{k-1})."""
+    assert eq1_error(ob.delayed_projection) < 1e-12
+
+
+def test_variants_use_eq1(monkeypatch):
+    calls = []
+    good = ob.delayed_projection
+
+    def counting(*a):
+        calls.append(1)
+        return good(*a)
+    monkeypatch.setattr(ob, "delayed_projection", counting)
+    X = synth.make_matrix_np(200, 20, 1e2, seed=71)
+    for v in ("bcgsi+p-1s", "bcgsi+p-2s"):
+        calls.clear()
+        oracle.factor(X, 4, v)
+        assert len(calls) == 5 - 2  # k = 2..q-1
+
+
+def test_chol_closed_forms():
+    a, b, c = 4.0, 2.0, 5.0
+    R = oracle.chol(np.array([[a, b], [b, c]]))
+    exp = np.array([[2.0, 1.0], [0.0, 2.0]])  # sqrt(4)=2, 2/2=1, sqrt(5-1)=2
+    assert np.array_equal(R, exp)
+    R0 = synth.make_upper_triangular_np(10, 1e3, seed=37)
+    assert np.abs(oracle.chol(R0.T @ R0) - R0).max() / np.abs(R0).max() < 1e-10
+    with pytest.raises(oracle.Breakdown) as e:
+        oracle.chol(np.array([[1.0, 2.0], [2.0, 1.0]]), block=3)
+    assert e.value.kind == "not_spd" and e.value.block == 3
+
+
+def test_triangular_solves_by_multiplication():
+    rng = np.random.default_rng(41)
+    T = synth.make_upper_triangular_np(6, 1e2, seed=43)
+    V = rng.standard_normal((50, 6))
+    W = oracle.solve_right_upper(V, T)
+    assert np.abs(W @ T - V).max() < 1e-12
+    M = rng.standard_normal((6, 5))
+    W2 = oracle.solve_left_upper_t(T, M)
+    assert np.abs(T.T @ W2 - M).max() < 1e-12
+
+
+# ---------------------------------------------------------------- Table 1
+
+def test_table1_loo_ordering():
+    """Table 1: BCGSI+ and BCGSI+P-2S keep O(u) loss of orthogonality while
+    O(u) kappa <= 1 (here kappa = 1e10), BCGSI+P-1S needs O(u) kappa^2 <= 1 and
+    breaks down (or loses orthogonality) at kappa = 1e10."""
+    X = synth.make_matrix_np(3000, 64, 1e10, seed=47)
+    for v in ("bcgsi+", "bcgsi+p-2s"):
+        Q, R = oracle.factor(X, 8, v)
+        assert oracle.loo(Q) < 1e-13
+    try:
+        Q, _ = oracle.factor(X, 8, "bcgsi+p-1s")
+        assert oracle.loo(Q) > 1e-10
+    except oracle.Breakdown as e:
+        assert e.kind == "not_spd"
+
+
+# ---------------------------------------------------------------- degenerate inputs
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_breakdowns(variant):
+    X = synth.make_matrix_np(100, 8, 1e2, seed=53)
+    Xz = X.copy()
+    Xz[:, 0:2] = 0.0
+    with pytest.raises(oracle.Breakdown) as e:
+        oracle.factor(Xz, 2, variant)
+    assert e.value.kind == "rank_deficient" and e.value.block == 1
+    Xn = X.copy()
+    Xn[5, 0] = np.nan
+    with pytest.raises(oracle.Breakdown) as e:
+        oracle.factor(Xn, 2, variant)
+    assert e.value.kind == "nonfinite"
+    with pytest.raises(ValueError):
+        oracle.factor(X, 3, variant)
+    with pytest.raises(ValueError):
+        oracle.factor(X[:1], 2, variant)
+
+
+# ---------------------------------------------------------------- mutations
+
+def _recovery_error(variant):
+    m, n, s = 400, 24, 4
+    Q0, _ = np.linalg.qr(np.random.default_rng(59).standard_normal((m, n)))
+    R0 = synth.make_upper_triangular_np(n, 1e3, seed=61)
+    try:
+        Q, R = oracle.factor(Q0 @ R0, s, variant)
+    except oracle.Breakdown:
+        return np.inf  # a breakdown on this well-conditioned input also fails the pin
+    return max(np.linalg.norm(R - R0) / np.linalg.norm(R0), np.abs(Q - Q0).max())
+
+
+def test_mutation_dropped_term_in_eq1_is_caught(monkeypatch):
+    monkeypatch.setattr(ob, "delayed_projection",
+                        lambda Ykk, P, Y, Z: ob.solve_left_upper_t(Ykk, P))
+    assert eq1_error(ob.delayed_projection) > 1e-3
+
+
+def _solve_pin_error():
+    rng = np.random.default_rng(41)
+    T = synth.make_upper_triangular_np(6, 1e2, seed=43)
+    V = rng.standard_normal((50, 6))
+    return np.abs(ob.solve_right_upper(V, T) @ T - V).max()
+
+
+def test_mutation_transposed_index_in_solve_is_caught(monkeypatch):
+    def bad_solve(V, T):
+        s = T.shape[0]
+        W = np.zeros_like(V)
+        for j in range(s):
+            W[:, j] = (V[:, j] - W[:, :j] @ T[j, :j]) / T[j, j]
+        return W
+    assert _solve_pin_error() < 1e-12
+    monkeypatch.setattr(ob, "solve_right_upper", bad_solve)
+    assert _solve_pin_error() > 1e-3
+    # In BCGSI+P-1S the solve by S_{k+1,k+1} (far from identity) is exposed.
+    assert _recovery_error("bcgsi+p-1s") > 1e-6
+
+
+def test_mutation_wrong_sign_in_chol_is_caught(monkeypatch):
+    good = ob.chol
+
+    def bad_chol(A, block=1):
+        R = good(A, block)
+        return R - 2 * np.triu(R, 1)
+    R0 = synth.make_upper_triangular_np(10, 1e3, seed=37)
+    assert np.abs(ob.chol(R0.T @ R0) - R0).max() < 1e-10
+    monkeypatch.setattr(ob, "chol", bad_chol)
+    assert np.abs(ob.chol(R0.T @ R0) - R0).max() > 1e-3
+    # BCGSI+P-1S's S_{k+1,k+1} = chol(T - S^T S) is far from identity; in
+    # BCGSI+P-2S chol only factors Omega - Y^T Y ~ I, and BCGSI+ has no chol.
+    assert _recovery_error("bcgsi+p-1s") > 1e-6
+
+
+def test_mutation_missing_sign_normalization_is_caught(monkeypatch):
+    good = ob.householder_qr
+
+    def bad_hh(A, block=1):
+        Q, R = good(A, block)
+        return -Q, -R
+    monkeypatch.setattr(ob, "householder_qr", bad_hh)
+    X = synth.make_matrix_np(50, 6, 1e2, seed=67)
+    Q, R = ob.householder_qr(X)
+    Ql, Rl = sign_normalized_lapack_qr(X)
+    assert np.abs(R - Rl).max() > 1e-3
+    for v in VARIANTS:
+        assert _recovery_error(v) > 1e-6
