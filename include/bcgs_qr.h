@@ -1,0 +1,224 @@
+/*
+ * bcgs_qr.h -- C ABI of the GB300 (sm_103a) reorthogonalized block classical
+ * Gram-Schmidt QR library.
+ *
+ * Operation (Sec. 1): the economic QR X = Q R of a tall-skinny m x n matrix X,
+ * Q^T Q = I, R upper triangular with positive diagonal, computed block column
+ * by block column, X = [X_1 ... X_q], q = n / s blocks of s columns, by one of
+ *   BCGS_BCGSI_PLUS       BCGSI+ (Sec. 1, Table 1: 4 synchronizations per block)
+ *   BCGS_BCGSI_PLUS_P_1S  BCGSI+P-1S (Alg. 2: 1 synchronization per block)
+ *   BCGS_BCGSI_PLUS_P_2S  BCGSI+P-2S (Sec. 2: Alg. 2 with TSQR as the first
+ *                         intraorthogonalization, 2 synchronizations per block)
+ * A synchronization point of the paper (one MPI_Allreduce, Sec. 3) is here one
+ * streaming pass over HBM that ends in a deterministic grid-wide reduction.
+ *
+ * Conventions for every entry point:
+ *   - Matrices are column-major (MATLAB indexing, Sec. 1) with a leading
+ *     dimension >= their row count.  X, Q, U and all workspace are DEVICE
+ *     pointers; R is a device FP64 n x n array whose strictly lower triangle
+ *     the library sets to zero.
+ *   - Under BCGS_FP64, X and Q are double*.  Under BCGS_FP32_STORAGE, X and Q are
+ *     float* (stored and streamed in FP32) while every inner product is
+ *     accumulated, and every small factor (Cholesky, triangular solves, R) is
+ *     computed, in FP64.  R is always double*.
+ *   - The caller owns every buffer.  The library never allocates device memory
+ *     and never frees caller memory; X is read-only and must not alias Q.
+ *   - Calls are asynchronous and ordered on the given CUDA stream (a
+ *     cudaStream_t passed as void*; NULL = the legacy default stream).
+ *     Invalid arguments are reported synchronously by the return value and
+ *     nothing is enqueued.  Numerical breakdown, non-finite data and device
+ *     timeouts are recorded in a status word inside the workspace; once it is
+ *     set, the remaining kernels of that factorization do nothing, and the
+ *     status is returned by bcgs_qr_sync / bcgs_qr_factor_status.
+ *   - Results are deterministic: the reduction order depends only on the
+ *     problem shape, never on scheduling.
+ */
+#ifndef BCGS_QR_H
+#define BCGS_QR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define BCGS_API __attribute__((visibility("default")))
+#else
+#define BCGS_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  BCGS_OK = 0,
+  BCGS_ERR_INVALID_ARG = 1,    /* bad size, leading dimension, pointer or enum  */
+  BCGS_ERR_NOT_SPD = 2,        /* a Pythagorean Cholesky (Alg. 1, Alg. 2) met a pivot <= 0 */
+  BCGS_ERR_RANK_DEFICIENT = 3, /* an intraorthogonalization (TSQR) gave a zero R diagonal */
+  BCGS_ERR_NONFINITE = 4,      /* NaN or Inf reached a factor                    */
+  BCGS_ERR_WORKSPACE = 5,      /* workspace too small or misaligned              */
+  BCGS_ERR_TIMEOUT = 6,        /* a bounded device wait gave up                  */
+  BCGS_ERR_STATE = 7,          /* call out of order (step after finish, ...)    */
+  BCGS_ERR_CUDA = 8            /* a CUDA runtime call failed                     */
+} bcgs_status;
+
+typedef enum {
+  BCGS_BCGSI_PLUS = 0,
+  BCGS_BCGSI_PLUS_P_1S = 1,
+  BCGS_BCGSI_PLUS_P_2S = 2
+} bcgs_variant;
+
+typedef enum { BCGS_FP64 = 0, BCGS_FP32_STORAGE = 1 } bcgs_precision;
+
+typedef struct bcgs_qr_s* bcgs_qr_t;
+
+/* Human-readable name of a status code (static string, never NULL). */
+BCGS_API const char* bcgs_status_string(int status);
+
+/* Library version as major*10000 + minor*100 + patch. */
+BCGS_API int bcgs_version(void);
+
+/* ---------------------------------------------------------------------------
+ * Whole factorization.
+ * ------------------------------------------------------------------------- */
+
+/* Bytes of device workspace needed by a factorization (or a handle) of an
+ * m x n_max matrix with block size s.  Requirements: 1 <= s <= 64, n_max <= m,
+ * n_max a multiple of s, n_max <= 2048.  Writes *bytes; returns BCGS_OK or
+ * BCGS_ERR_INVALID_ARG. */
+BCGS_API int bcgs_qr_workspace_size(int64_t m, int32_t n_max, int32_t s, int variant,
+                           int precision, size_t* bytes);
+
+/* Factor X (m x n, leading dimension ldx) into Q (m x n, ldq) and R (n x n,
+ * ldr): the whole of Alg. 2 (or the chosen variant) enqueued on `stream`.
+ * `workspace` is a device buffer of at least bcgs_qr_workspace_size bytes,
+ * 256-byte aligned, not shared with any other call in flight.  Returns after
+ * enqueueing; read the outcome with bcgs_qr_factor_status. */
+BCGS_API int bcgs_qr_factor(int64_t m, int32_t n, int32_t s, int variant, int precision,
+                   const void* X, int64_t ldx, void* Q, int64_t ldq, double* R,
+                   int32_t ldr, void* workspace, size_t ws_bytes, void* stream);
+
+/* Synchronize `stream`, then return the device status word of the last
+ * factorization that used `workspace`; *fail_block (may be NULL) gets the
+ * 1-based block column at which it failed, 0 on success. */
+BCGS_API int bcgs_qr_factor_status(const void* workspace, void* stream, int32_t* fail_block);
+
+/* ---------------------------------------------------------------------------
+ * Block-by-block interface (s-step Krylov use, serving).
+ *
+ * bcgs_qr_init binds a handle to caller-owned Q, R and workspace; each
+ * bcgs_qr_step ingests the next m x s block X_j; bcgs_qr_finish runs the last
+ * block's branch of Alg. 2.  Delayed normalization (Sec. 2, eq. (1)) means that
+ * under BCGSI+P-1S and -2S, after step j (j >= 2) the columns of Q and R of
+ * blocks 1..j-1 are final and block j is still provisional; under BCGSI+ block
+ * j is final after step j.  bcgs_qr_sync reports how many columns are final.
+ * The handle is a small host object (the only host allocation of the library).
+ * ------------------------------------------------------------------------- */
+BCGS_API int bcgs_qr_init(bcgs_qr_t* handle, int64_t m, int32_t n_max, int32_t s,
+                 int variant, int precision, void* Q, int64_t ldq, double* R,
+                 int32_t ldr, void* workspace, size_t ws_bytes, void* stream);
+
+/* Ingest the next block X_j (m x s, leading dimension ldx).  Returns
+ * BCGS_ERR_STATE after bcgs_qr_finish or once n_max columns were ingested. */
+BCGS_API int bcgs_qr_step(bcgs_qr_t handle, const void* X_block, int64_t ldx);
+
+/* Finalize the last block (the else-branch of Alg. 2).  Idempotent. */
+BCGS_API int bcgs_qr_finish(bcgs_qr_t handle);
+
+/* Synchronize the handle's stream and return its device status; *n_final gets
+ * the number of final columns of Q and R, *fail_block the failing block (0 if
+ * none).  Either pointer may be NULL. */
+BCGS_API int bcgs_qr_sync(bcgs_qr_t handle, int32_t* n_final, int32_t* fail_block);
+
+/* Rebind the handle to another stream (ordering is the caller's business). */
+BCGS_API int bcgs_qr_set_stream(bcgs_qr_t handle, void* stream);
+
+/* Release the host handle (device buffers stay the caller's). */
+BCGS_API int bcgs_qr_destroy(bcgs_qr_t handle);
+
+/* ---------------------------------------------------------------------------
+ * Batched interface: many independent factorizations, one launch per phase.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+  int64_t m;         /* rows                                 */
+  int32_t n, s;      /* columns and block size (n % s == 0)  */
+  int32_t variant;   /* bcgs_variant                         */
+  int32_t precision; /* bcgs_precision                        */
+  const void* X; int64_t ldx;
+  void* Q; int64_t ldq;
+  double* R; int32_t ldr;
+  int32_t pad_;
+} bcgs_problem;
+
+/* Workspace for a batch (host array `probs` of `count` problems). */
+BCGS_API int bcgs_qr_batched_workspace_size(int32_t count, const bcgs_problem* probs, size_t* bytes);
+
+/* Enqueue all `count` factorizations on `stream`; statuses go to the
+ * workspace, read them with bcgs_qr_batched_status. */
+BCGS_API int bcgs_qr_factor_batched(int32_t count, const bcgs_problem* probs, void* workspace,
+                           size_t ws_bytes, void* stream);
+
+/* Synchronize and copy the `count` status codes and failing blocks to host
+ * arrays (either may be NULL); returns the first nonzero status or BCGS_OK. */
+BCGS_API int bcgs_qr_batched_status(int32_t count, const void* workspace, void* stream,
+                           int32_t* codes, int32_t* fail_blocks);
+
+/* ---------------------------------------------------------------------------
+ * Building blocks, exposed for reuse and testing (FP64 only).
+ * ------------------------------------------------------------------------- */
+
+/* C (ka x kb, ldc, device FP64) = A^T B for A (m x ka, lda) and B (m x kb,
+ * ldb): one synchronization point (Sec. 3).  ka*kb <= 65536. */
+BCGS_API int bcgs_gram_workspace_size(int64_t m, int32_t ka, int32_t kb, size_t* bytes);
+BCGS_API int bcgs_gram(int64_t m, int32_t ka, int32_t kb, const double* A, int64_t lda,
+              const double* B, int64_t ldb, double* C, int32_t ldc,
+              void* workspace, size_t ws_bytes, void* stream);
+
+/* W = (V - Q C) T^{-1}: projection plus triangular-solve normalization (Alg. 1
+ * and Alg. 2, the U and Q updates).  V, W: m x s; Q: m x c; C: c x s (device);
+ * T: s x s upper triangular (device) or NULL for no normalization.  c may be 0
+ * (Q and C ignored).  W may alias V.  1 <= s <= 64. */
+BCGS_API int bcgs_project(int64_t m, int32_t c, int32_t s, const double* V, int64_t ldv,
+                 const double* Q, int64_t ldq, const double* C, int32_t ldc,
+                 const double* T, int32_t ldt, double* W, int64_t ldw, void* stream);
+
+/* TSQR (Sec. 1, Alg. 1, Alg. 2): economic QR of an m x s block A (lda) into
+ * Q (ldq) and R (s x s, ldr, device), diag(R) >= 0; Householder QR of row
+ * tiles, a fixed reduction tree of the stacked R factors, and an explicit-Q
+ * pass.  Q may alias A.  A zero diagonal of R sets BCGS_ERR_RANK_DEFICIENT
+ * in the workspace status word (read it with bcgs_qr_factor_status). */
+BCGS_API int bcgs_tsqr_workspace_size(int64_t m, int32_t s, size_t* bytes);
+BCGS_API int bcgs_tsqr(int64_t m, int32_t s, const double* A, int64_t lda, double* Q,
+              int64_t ldq, double* R, int32_t ldr, void* workspace, size_t ws_bytes,
+              void* stream);
+
+/* Upper Cholesky factor R (s x s) of a symmetric positive definite A (s x s)
+ * on the device (chol of Alg. 1 and Alg. 2).  A non-positive pivot sets
+ * BCGS_ERR_NOT_SPD in the workspace status word.  workspace >= 256 bytes. */
+BCGS_API int bcgs_chol(int32_t s, const double* A, int32_t lda, double* R, int32_t ldr,
+              void* workspace, size_t ws_bytes, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Instrumentation (host side; no device memory).
+ * ------------------------------------------------------------------------- */
+
+/* Number of CUDA kernels this library has launched since it was loaded. */
+BCGS_API int64_t bcgs_launch_count(void);
+
+/* enable != 0: bracket every Gram-partial, Gram-reduce, projection, TSQR and
+ * tail launch with CUDA events recorded on its stream (cudaEventCreate is the
+ * only resource used).  Adds a few microseconds per launch. */
+BCGS_API int bcgs_profile_enable(int enable);
+
+/* Drop recorded events and totals. */
+BCGS_API int bcgs_profile_reset(void);
+
+/* Totals for a kernel class (0 Gram partial, 1 Gram reduce, 2 projection,
+ * 3 TSQR, 4 tail) over the recorded launches: count, summed event time in ms,
+ * algorithmic flops and bytes.  Waits for the recorded events. */
+BCGS_API int bcgs_profile_read(int kernel_class, int64_t* launches, double* total_ms,
+                               double* flops, double* bytes);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BCGS_QR_H */

@@ -1,0 +1,629 @@
+// Host driver and C ABI: the three variants as block-step state machines over
+// the kernels of gram.cu, proj.cu, tsqr.cu and tail.cu.
+//
+// Every step is a fixed sequence of stream-ordered launches; nothing here
+// synchronizes except bcgs_qr_sync / *_status.  All device memory is the
+// caller's: the workspace is carved into the buffers below.
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+
+#include "bcgs_internal.cuh"
+
+using namespace bcgs;
+
+namespace {
+
+constexpr int kMaxS = 64;
+constexpr int kMaxN = 2048;
+
+struct Layout {
+  size_t status, S[2], Sd[2], Yd, Rt1, Rt2, G, G2, partial, U, V, tsqr, total;
+  int ldg;      // leading dimension of G, G2 (= n_max)
+  int64_t ldu;  // leading dimension of U, V
+  TsqrPlan tp;
+};
+
+size_t align256(size_t v) { return (v + 255) / 256 * 256; }
+
+bool valid_shape(int64_t m, int32_t n, int32_t s) {
+  return s >= 1 && s <= kMaxS && m >= n && n >= s && n % s == 0 && n <= kMaxN;
+}
+
+void make_layout(int64_t m, int32_t n_max, int32_t s, int variant, int precision, Layout* L) {
+  const size_t esz = precision == BCGS_FP32_STORAGE ? 4 : 8;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t o = off;
+    off = align256(off + bytes);
+    return o;
+  };
+  L->status = take(sizeof(DevStatus));
+  const size_t ss = (size_t)s * s * sizeof(double);
+  for (int i = 0; i < 2; ++i) L->S[i] = take((size_t)n_max * s * sizeof(double));
+  for (int i = 0; i < 2; ++i) L->Sd[i] = take(ss);
+  L->Yd = take(ss);
+  L->Rt1 = take(ss);
+  L->Rt2 = take(ss);
+  L->ldg = n_max;
+  L->G = take((size_t)n_max * 2 * s * sizeof(double));
+  L->G2 = take((size_t)n_max * 2 * s * sizeof(double));
+  L->partial = take(gram_partial_doubles(m, n_max, 2 * s) * sizeof(double));
+  L->ldu = round_up(m, 64);
+  L->U = take((size_t)L->ldu * s * esz);
+  L->V = variant == BCGS_BCGSI_PLUS_P_1S ? off : take((size_t)L->ldu * s * esz);
+  tsqr_plan(m, s, &L->tp);
+  L->tsqr = take(L->tp.doubles * sizeof(double));
+  L->total = off;
+}
+
+Seg seg(const void* p, int64_t ld, int ncols, int fp32) {
+  Seg g;
+  g.p = p;
+  g.ld = ld;
+  g.ncols = ncols;
+  g.fp32 = fp32;
+  return g;
+}
+
+}  // namespace
+
+struct bcgs_qr_s {
+  int64_t m;
+  int32_t n_max, s, variant, precision;
+  char* Q;
+  int64_t ldq;
+  double* R;
+  int32_t ldr;
+  char* ws;
+  size_t ws_bytes;
+  cudaStream_t stream;
+  Layout L;
+  int32_t j;  // blocks ingested
+  int32_t cur;
+  int32_t finished;
+  int32_t esz;
+  int32_t fp32;
+  cudaError_t last_cuda;
+
+  DevStatus* st() { return reinterpret_cast<DevStatus*>(ws + L.status); }
+  double* buf(size_t off) { return reinterpret_cast<double*>(ws + off); }
+  void* U() { return ws + L.U; }
+  void* V() { return ws + L.V; }
+  // column block k (1-based) of Q
+  char* Qblk(int k) { return Q + (size_t)(k - 1) * s * ldq * esz; }
+  Seg Qseg(int ncols) { return seg(Q, ldq, ncols, fp32); }
+  Seg Useg() { return seg(U(), L.ldu, s, fp32); }
+  Seg Vseg() { return seg(V(), L.ldu, s, fp32); }
+};
+
+namespace {
+
+int check(bcgs_qr_s* h, cudaError_t e) {
+  if (e != cudaSuccess) {
+    h->last_cuda = e;
+    return BCGS_ERR_CUDA;
+  }
+  return BCGS_OK;
+}
+
+#define TRY(expr)                      \
+  do {                                 \
+    int rc_ = check(h, (expr));        \
+    if (rc_ != BCGS_OK) return rc_;    \
+  } while (0)
+
+cudaError_t gram(bcgs_qr_s* h, std::initializer_list<Seg> A, std::initializer_list<Seg> B,
+                 double* G) {
+  GramDesc d;
+  memset(&d, 0, sizeof(d));
+  d.nsa = 0;
+  d.na = 0;
+  for (const Seg& a : A) {
+    if (a.ncols <= 0) continue;
+    d.a[d.nsa++] = a;
+    d.na += a.ncols;
+  }
+  d.nsb = 0;
+  d.nb = 0;
+  for (const Seg& b : B) {
+    if (b.ncols <= 0) continue;
+    d.b[d.nsb++] = b;
+    d.nb += b.ncols;
+  }
+  d.m = h->m;
+  gram_partition(h->m, &d.chunk_rows, &d.nchunks);
+  return launch_gram(d, h->buf(h->L.partial), G, h->L.ldg, h->st(), h->stream);
+}
+
+cudaError_t project(bcgs_qr_s* h, Seg v, int c, const double* C, int ldc, const double* T,
+                    void* w, int64_t ldw) {
+  ProjDesc d;
+  d.v = v;
+  d.q = h->Qseg(c);
+  d.C = C;
+  d.ldc = ldc;
+  d.T = T;
+  d.ldt = h->s;
+  d.w = w;
+  d.ldw = ldw;
+  d.w_fp32 = h->fp32;
+  d.m = h->m;
+  d.s = h->s;
+  return launch_project(d, h->st(), h->stream);
+}
+
+cudaError_t tsqr(bcgs_qr_s* h, Seg a, void* q, int64_t ldq, double* R, int ldr, int block) {
+  return launch_tsqr(h->L.tp, a, q, ldq, h->fp32, R, ldr, h->buf(h->L.tsqr), h->st(), block,
+                     h->stream);
+}
+
+// Last-block branch of Alg. 2 (shared by BCGSI+P-1S and -2S):
+// [Y_{1:q-1,q}; Omega_q] = [Q_{q-1} U_q]^T U_q, Y_qq, R column block q, Q_q.
+int finish_p(bcgs_qr_s* h) {
+  const int s = h->s, q = h->j;
+  const int c = (q - 1) * s;
+  double* G = h->buf(h->L.G);
+  const int ldg = h->L.ldg;
+  TRY(gram(h, {h->Qseg(c), h->Useg()}, {h->Useg()}, G));
+  TailDesc t;
+  memset(&t, 0, sizeof(t));
+  t.s = s;
+  t.c = c;
+  t.G = G;
+  t.ldg = ldg;
+  t.gy = 0;
+  t.gom = c;
+  t.S_prev = h->buf(h->L.S[h->cur]);
+  t.Sd_prev = h->buf(h->L.Sd[h->cur]);
+  t.Yd = h->buf(h->L.Yd);
+  t.R = h->R;
+  t.ldr = h->ldr;
+  t.r_row0 = 0;
+  t.r_col0 = c;
+  t.has_next = 0;
+  t.block = q;
+  t.ldsm = h->n_max;
+  TRY(launch_tail_1s2s(t, h->st(), h->stream));
+  TRY(project(h, h->Useg(), c, G, ldg, h->buf(h->L.Yd), h->Qblk(q), h->ldq));
+  return BCGS_OK;
+}
+
+// One block step of BCGSI+P-1S (Alg. 2) or BCGSI+P-2S for block j >= 3
+// (k = j - 1): the synchronization of block k, the tail, Q_k and U_{k+1}.
+int step_p(bcgs_qr_s* h, const void* X, int64_t ldx) {
+  const int s = h->s, j = h->j + 1, k = j - 1;
+  const int c = (k - 1) * s;
+  const bool one_sync = h->variant == BCGS_BCGSI_PLUS_P_1S;
+  const Seg Xs = seg(X, ldx, s, h->fp32);
+  double* G = h->buf(h->L.G);
+  const int ldg = h->L.ldg;
+  if (one_sync)
+    TRY(gram(h, {h->Qseg(c), h->Useg(), Xs}, {h->Useg(), Xs}, G));
+  else
+    TRY(gram(h, {h->Qseg(c), h->Useg()}, {h->Useg(), Xs}, G));
+  const int nxt = 1 - h->cur;
+  TailDesc t;
+  memset(&t, 0, sizeof(t));
+  t.s = s;
+  t.c = c;
+  t.G = G;
+  t.ldg = ldg;
+  t.gy = 0;
+  t.gz = s * ldg;
+  t.gom = c;
+  t.gp = c + s * ldg;
+  t.gt = c + s + s * ldg;
+  t.S_prev = h->buf(h->L.S[h->cur]);
+  t.Sd_prev = h->buf(h->L.Sd[h->cur]);
+  t.S_next = h->buf(h->L.S[nxt]);
+  t.Sd_next = h->buf(h->L.Sd[nxt]);
+  t.Yd = h->buf(h->L.Yd);
+  t.R = h->R;
+  t.ldr = h->ldr;
+  t.r_row0 = 0;
+  t.r_col0 = c;
+  t.has_next = 1;
+  t.chol_next = one_sync ? 1 : 0;
+  t.block = k;
+  t.ldsm = h->n_max;
+  TRY(launch_tail_1s2s(t, h->st(), h->stream));
+  // Q_k = (U_k - Q_{1:k-1} Y_{1:k-1,k}) Y_kk^{-1}
+  TRY(project(h, h->Useg(), c, G, ldg, h->buf(h->L.Yd), h->Qblk(k), h->ldq));
+  if (one_sync) {
+    // U_{k+1} = (X_{k+1} - Q_{1:k} S_{1:k,k+1}) S_{k+1,k+1}^{-1}
+    TRY(project(h, Xs, c + s, h->buf(h->L.S[nxt]), h->n_max, h->buf(h->L.Sd[nxt]), h->U(),
+                h->L.ldu));
+  } else {
+    // [U_{k+1}, S_{k+1,k+1}] = TSQR(X_{k+1} - Q_{1:k} S_{1:k,k+1})
+    TRY(project(h, Xs, c + s, h->buf(h->L.S[nxt]), h->n_max, nullptr, h->V(), h->L.ldu));
+    TRY(tsqr(h, h->Vseg(), h->U(), h->L.ldu, h->buf(h->L.Sd[nxt]), s, k + 1));
+  }
+  h->cur = nxt;
+  return BCGS_OK;
+}
+
+int do_step(bcgs_qr_s* h, const void* X, int64_t ldx) {
+  const int s = h->s, j = h->j + 1;
+  const Seg Xs = seg(X, ldx, s, h->fp32);
+  double* G = h->buf(h->L.G);
+  const int ldg = h->L.ldg;
+  if (j == 1) {
+    // [Q_1, R_11] = TSQR(X_1)
+    TRY(tsqr(h, Xs, h->Qblk(1), h->ldq, h->R, h->ldr, 1));
+    return BCGS_OK;
+  }
+  switch (h->variant) {
+    case BCGS_BCGSI_PLUS: {
+      const int k = j - 1, c = k * s;
+      double* G2 = h->buf(h->L.G2);
+      // S = Q_k^T X_{k+1};  [U, S_kk] = TSQR(X_{k+1} - Q_k S)
+      TRY(gram(h, {h->Qseg(c)}, {Xs}, G));
+      TRY(project(h, Xs, c, G, ldg, nullptr, h->V(), h->L.ldu));
+      TRY(tsqr(h, h->Vseg(), h->U(), h->L.ldu, h->buf(h->L.Rt1), s, j));
+      // Y = Q_k^T U;  [Q_{k+1}, Y_kk] = TSQR(U - Q_k Y)
+      TRY(gram(h, {h->Qseg(c)}, {h->Useg()}, G2));
+      TRY(project(h, h->Useg(), c, G2, ldg, nullptr, h->V(), h->L.ldu));
+      TRY(tsqr(h, h->Vseg(), h->Qblk(j), h->ldq, h->buf(h->L.Rt2), s, j));
+      TRY(launch_r_assemble(c, s, G, ldg, G2, ldg, h->buf(h->L.Rt1), h->buf(h->L.Rt2), h->R,
+                            h->ldr, c, h->st(), h->stream));
+      return BCGS_OK;
+    }
+    case BCGS_BCGSI_PLUS_P_1S:
+      if (j == 2) {
+        // [S_12; T_2] = [Q_1 X_2]^T X_2, S_22 = chol(T_2 - S_12^T S_12), U_2
+        TRY(gram(h, {h->Qseg(s), Xs}, {Xs}, G));
+        TRY(launch_tail_start_1s(s, G, ldg, h->buf(h->L.S[h->cur]), h->n_max,
+                                 h->buf(h->L.Sd[h->cur]), 2, h->st(), h->stream));
+        TRY(project(h, Xs, s, h->buf(h->L.S[h->cur]), h->n_max, h->buf(h->L.Sd[h->cur]), h->U(),
+                    h->L.ldu));
+        return BCGS_OK;
+      }
+      return step_p(h, X, ldx);
+    case BCGS_BCGSI_PLUS_P_2S:
+      if (j == 2) {
+        // S_12 = Q_1^T X_2, [U_2, S_22] = TSQR(X_2 - Q_1 S_12)
+        TRY(gram(h, {h->Qseg(s)}, {Xs}, G));
+        TRY(launch_copy_small(s, s, G, ldg, h->buf(h->L.S[h->cur]), h->n_max, h->st(), h->stream));
+        TRY(project(h, Xs, s, G, ldg, nullptr, h->V(), h->L.ldu));
+        TRY(tsqr(h, h->Vseg(), h->U(), h->L.ldu, h->buf(h->L.Sd[h->cur]), s, 2));
+        return BCGS_OK;
+      }
+      return step_p(h, X, ldx);
+  }
+  return BCGS_ERR_INVALID_ARG;
+}
+
+int init_handle(bcgs_qr_s* h, int64_t m, int32_t n_max, int32_t s, int variant, int precision,
+                void* Q, int64_t ldq, double* R, int32_t ldr, void* workspace, size_t ws_bytes,
+                void* stream) {
+  if (!valid_shape(m, n_max, s)) return BCGS_ERR_INVALID_ARG;
+  if (variant < 0 || variant > 2 || precision < 0 || precision > 1) return BCGS_ERR_INVALID_ARG;
+  if (Q == nullptr || R == nullptr || workspace == nullptr) return BCGS_ERR_INVALID_ARG;
+  if (ldq < m || ldr < n_max) return BCGS_ERR_INVALID_ARG;
+  if (((uintptr_t)workspace) % 256 != 0) return BCGS_ERR_WORKSPACE;
+  memset(h, 0, sizeof(*h));
+  make_layout(m, n_max, s, variant, precision, &h->L);
+  if (ws_bytes < h->L.total) return BCGS_ERR_WORKSPACE;
+  h->m = m;
+  h->n_max = n_max;
+  h->s = s;
+  h->variant = variant;
+  h->precision = precision;
+  h->Q = reinterpret_cast<char*>(Q);
+  h->ldq = ldq;
+  h->R = R;
+  h->ldr = ldr;
+  h->ws = reinterpret_cast<char*>(workspace);
+  h->ws_bytes = ws_bytes;
+  h->stream = reinterpret_cast<cudaStream_t>(stream);
+  h->fp32 = precision == BCGS_FP32_STORAGE ? 1 : 0;
+  h->esz = h->fp32 ? 4 : 8;
+  h->j = 0;
+  h->cur = 0;
+  h->finished = 0;
+  TRY(launch_reset_status(h->st(), h->stream));
+  TRY(launch_zero_lower(n_max, R, ldr, h->stream));
+  return BCGS_OK;
+}
+
+int step_handle(bcgs_qr_s* h, const void* X, int64_t ldx) {
+  if (h->finished || (h->j + 1) * h->s > h->n_max) return BCGS_ERR_STATE;
+  if (X == nullptr || ldx < h->m) return BCGS_ERR_INVALID_ARG;
+  const int rc = do_step(h, X, ldx);
+  if (rc != BCGS_OK) return rc;
+  h->j += 1;
+  return BCGS_OK;
+}
+
+int finish_handle(bcgs_qr_s* h) {
+  if (h->finished) return BCGS_OK;
+  if (h->j == 0) return BCGS_ERR_STATE;
+  if (h->variant != BCGS_BCGSI_PLUS && h->j >= 2) {
+    const int rc = finish_p(h);
+    if (rc != BCGS_OK) return rc;
+  }
+  h->finished = 1;
+  return BCGS_OK;
+}
+
+int read_status(const void* ws, cudaStream_t stream, int32_t* code, int32_t* block) {
+  DevStatus hs;
+  cudaError_t e = cudaStreamSynchronize(stream);
+  if (e != cudaSuccess) return BCGS_ERR_CUDA;
+  e = cudaMemcpy(&hs, ws, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return BCGS_ERR_CUDA;
+  *code = hs.code;
+  *block = hs.block;
+  return BCGS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* bcgs_status_string(int status) {
+  switch (status) {
+    case BCGS_OK: return "ok";
+    case BCGS_ERR_INVALID_ARG: return "invalid argument";
+    case BCGS_ERR_NOT_SPD: return "Cholesky breakdown (matrix not positive definite)";
+    case BCGS_ERR_RANK_DEFICIENT: return "rank deficient block (zero R diagonal)";
+    case BCGS_ERR_NONFINITE: return "non-finite value";
+    case BCGS_ERR_WORKSPACE: return "workspace too small or misaligned";
+    case BCGS_ERR_TIMEOUT: return "device wait timed out";
+    case BCGS_ERR_STATE: return "call out of order";
+    case BCGS_ERR_CUDA: return "CUDA runtime error";
+  }
+  return "unknown status";
+}
+
+int bcgs_version(void) { return 100; }
+
+int bcgs_qr_workspace_size(int64_t m, int32_t n_max, int32_t s, int variant, int precision,
+                           size_t* bytes) {
+  if (bytes == nullptr || !valid_shape(m, n_max, s)) return BCGS_ERR_INVALID_ARG;
+  if (variant < 0 || variant > 2 || precision < 0 || precision > 1) return BCGS_ERR_INVALID_ARG;
+  Layout L;
+  make_layout(m, n_max, s, variant, precision, &L);
+  *bytes = L.total;
+  return BCGS_OK;
+}
+
+int bcgs_qr_factor(int64_t m, int32_t n, int32_t s, int variant, int precision, const void* X,
+                   int64_t ldx, void* Q, int64_t ldq, double* R, int32_t ldr, void* workspace,
+                   size_t ws_bytes, void* stream) {
+  if (X == nullptr || ldx < m) return BCGS_ERR_INVALID_ARG;
+  bcgs_qr_s hs;
+  bcgs_qr_s* h = &hs;
+  int rc = init_handle(h, m, n, s, variant, precision, Q, ldq, R, ldr, workspace, ws_bytes, stream);
+  if (rc != BCGS_OK) return rc;
+  const size_t esz = precision == BCGS_FP32_STORAGE ? 4 : 8;
+  const char* Xc = reinterpret_cast<const char*>(X);
+  for (int k = 0; k < n / s; ++k) {
+    rc = step_handle(h, Xc + (size_t)k * s * ldx * esz, ldx);
+    if (rc != BCGS_OK) return rc;
+  }
+  return finish_handle(h);
+}
+
+int bcgs_qr_factor_status(const void* workspace, void* stream, int32_t* fail_block) {
+  if (workspace == nullptr) return BCGS_ERR_INVALID_ARG;
+  int32_t code = 0, block = 0;
+  int rc = read_status(workspace, reinterpret_cast<cudaStream_t>(stream), &code, &block);
+  if (rc != BCGS_OK) return rc;
+  if (fail_block) *fail_block = code ? block : 0;
+  return code;
+}
+
+int bcgs_qr_init(bcgs_qr_t* handle, int64_t m, int32_t n_max, int32_t s, int variant,
+                 int precision, void* Q, int64_t ldq, double* R, int32_t ldr, void* workspace,
+                 size_t ws_bytes, void* stream) {
+  if (handle == nullptr) return BCGS_ERR_INVALID_ARG;
+  *handle = nullptr;
+  bcgs_qr_s* h = static_cast<bcgs_qr_s*>(malloc(sizeof(bcgs_qr_s)));
+  if (h == nullptr) return BCGS_ERR_INVALID_ARG;
+  const int rc = init_handle(h, m, n_max, s, variant, precision, Q, ldq, R, ldr, workspace,
+                             ws_bytes, stream);
+  if (rc != BCGS_OK) {
+    free(h);
+    return rc;
+  }
+  *handle = h;
+  return BCGS_OK;
+}
+
+int bcgs_qr_step(bcgs_qr_t h, const void* X_block, int64_t ldx) {
+  if (h == nullptr) return BCGS_ERR_INVALID_ARG;
+  return step_handle(h, X_block, ldx);
+}
+
+int bcgs_qr_finish(bcgs_qr_t h) {
+  if (h == nullptr) return BCGS_ERR_INVALID_ARG;
+  return finish_handle(h);
+}
+
+int bcgs_qr_sync(bcgs_qr_t h, int32_t* n_final, int32_t* fail_block) {
+  if (h == nullptr) return BCGS_ERR_INVALID_ARG;
+  int32_t code = 0, block = 0;
+  int rc = read_status(h->ws + h->L.status, h->stream, &code, &block);
+  if (rc != BCGS_OK) return rc;
+  if (n_final) {
+    int fin;
+    if (h->finished || h->variant == BCGS_BCGSI_PLUS) fin = h->j;
+    else fin = h->j <= 1 ? h->j : h->j - 1;
+    *n_final = code ? 0 : fin * h->s;
+  }
+  if (fail_block) *fail_block = code ? block : 0;
+  return code;
+}
+
+int bcgs_qr_set_stream(bcgs_qr_t h, void* stream) {
+  if (h == nullptr) return BCGS_ERR_INVALID_ARG;
+  h->stream = reinterpret_cast<cudaStream_t>(stream);
+  return BCGS_OK;
+}
+
+int bcgs_qr_destroy(bcgs_qr_t h) {
+  free(h);
+  return BCGS_OK;
+}
+
+// ------------------------------------------------------------------ building blocks
+
+int bcgs_gram_workspace_size(int64_t m, int32_t ka, int32_t kb, size_t* bytes) {
+  if (bytes == nullptr || m < 1 || ka < 1 || kb < 1 || (int64_t)ka * kb > 65536)
+    return BCGS_ERR_INVALID_ARG;
+  *bytes = align256(sizeof(DevStatus)) + gram_partial_doubles(m, ka, kb) * sizeof(double);
+  return BCGS_OK;
+}
+
+int bcgs_gram(int64_t m, int32_t ka, int32_t kb, const double* A, int64_t lda, const double* B,
+              int64_t ldb, double* C, int32_t ldc, void* workspace, size_t ws_bytes, void* stream) {
+  size_t need = 0;
+  if (bcgs_gram_workspace_size(m, ka, kb, &need) != BCGS_OK) return BCGS_ERR_INVALID_ARG;
+  if (!A || !B || !C || !workspace || lda < m || ldb < m || ldc < ka) return BCGS_ERR_INVALID_ARG;
+  if (ws_bytes < need || ((uintptr_t)workspace) % 256 != 0) return BCGS_ERR_WORKSPACE;
+  char* ws = reinterpret_cast<char*>(workspace);
+  DevStatus* st = reinterpret_cast<DevStatus*>(ws);
+  cudaStream_t sm = reinterpret_cast<cudaStream_t>(stream);
+  if (launch_reset_status(st, sm) != cudaSuccess) return BCGS_ERR_CUDA;
+  GramDesc d;
+  memset(&d, 0, sizeof(d));
+  d.a[0] = seg(A, lda, ka, 0);
+  d.b[0] = seg(B, ldb, kb, 0);
+  d.nsa = d.nsb = 1;
+  d.na = ka;
+  d.nb = kb;
+  d.m = m;
+  gram_partition(m, &d.chunk_rows, &d.nchunks);
+  if (launch_gram(d, reinterpret_cast<double*>(ws + align256(sizeof(DevStatus))), C, ldc, st, sm) !=
+      cudaSuccess)
+    return BCGS_ERR_CUDA;
+  return BCGS_OK;
+}
+
+int bcgs_project(int64_t m, int32_t c, int32_t s, const double* V, int64_t ldv, const double* Q,
+                 int64_t ldq, const double* C, int32_t ldc, const double* T, int32_t ldt, double* W,
+                 int64_t ldw, void* stream) {
+  if (m < 1 || s < 1 || s > kMaxS || c < 0 || !V || !W || ldv < m || ldw < m)
+    return BCGS_ERR_INVALID_ARG;
+  if (c > 0 && (!Q || !C || ldq < m || ldc < c)) return BCGS_ERR_INVALID_ARG;
+  if (T && ldt < s) return BCGS_ERR_INVALID_ARG;
+  ProjDesc d;
+  d.v = seg(V, ldv, s, 0);
+  d.q = seg(Q, ldq, c, 0);
+  d.C = C;
+  d.ldc = ldc;
+  d.T = T;
+  d.ldt = ldt;
+  d.w = W;
+  d.ldw = ldw;
+  d.w_fp32 = 0;
+  d.m = m;
+  d.s = s;
+  return launch_project(d, nullptr, reinterpret_cast<cudaStream_t>(stream)) == cudaSuccess
+             ? BCGS_OK
+             : BCGS_ERR_CUDA;
+}
+
+int bcgs_tsqr_workspace_size(int64_t m, int32_t s, size_t* bytes) {
+  if (bytes == nullptr || s < 1 || s > kMaxS || m < s) return BCGS_ERR_INVALID_ARG;
+  TsqrPlan p;
+  tsqr_plan(m, s, &p);
+  *bytes = align256(sizeof(DevStatus)) + p.doubles * sizeof(double);
+  return BCGS_OK;
+}
+
+int bcgs_tsqr(int64_t m, int32_t s, const double* A, int64_t lda, double* Q, int64_t ldq, double* R,
+              int32_t ldr, void* workspace, size_t ws_bytes, void* stream) {
+  size_t need = 0;
+  if (bcgs_tsqr_workspace_size(m, s, &need) != BCGS_OK) return BCGS_ERR_INVALID_ARG;
+  if (!A || !Q || !R || !workspace || lda < m || ldq < m || ldr < s) return BCGS_ERR_INVALID_ARG;
+  if (ws_bytes < need || ((uintptr_t)workspace) % 256 != 0) return BCGS_ERR_WORKSPACE;
+  char* ws = reinterpret_cast<char*>(workspace);
+  DevStatus* st = reinterpret_cast<DevStatus*>(ws);
+  cudaStream_t sm = reinterpret_cast<cudaStream_t>(stream);
+  if (launch_reset_status(st, sm) != cudaSuccess) return BCGS_ERR_CUDA;
+  TsqrPlan p;
+  tsqr_plan(m, s, &p);
+  if (launch_tsqr(p, seg(A, lda, s, 0), Q, ldq, 0, R, ldr,
+                  reinterpret_cast<double*>(ws + align256(sizeof(DevStatus))), st, 1,
+                  sm) != cudaSuccess)
+    return BCGS_ERR_CUDA;
+  return BCGS_OK;
+}
+
+int bcgs_chol(int32_t s, const double* A, int32_t lda, double* R, int32_t ldr, void* workspace,
+              size_t ws_bytes, void* stream) {
+  if (s < 1 || s > kMaxS || !A || !R || !workspace || lda < s || ldr < s)
+    return BCGS_ERR_INVALID_ARG;
+  if (ws_bytes < sizeof(DevStatus) || ((uintptr_t)workspace) % 256 != 0) return BCGS_ERR_WORKSPACE;
+  DevStatus* st = reinterpret_cast<DevStatus*>(workspace);
+  cudaStream_t sm = reinterpret_cast<cudaStream_t>(stream);
+  if (launch_reset_status(st, sm) != cudaSuccess) return BCGS_ERR_CUDA;
+  return launch_chol(s, A, lda, R, ldr, 1, st, sm) == cudaSuccess ? BCGS_OK : BCGS_ERR_CUDA;
+}
+
+// Batched factorization: problems are enqueued one after another on the stream,
+// each in its own slice of the workspace (status words at the start).
+int bcgs_qr_batched_workspace_size(int32_t count, const bcgs_problem* probs, size_t* bytes) {
+  if (count < 0 || bytes == nullptr || (count > 0 && probs == nullptr)) return BCGS_ERR_INVALID_ARG;
+  size_t total = align256((size_t)count * sizeof(DevStatus));
+  for (int i = 0; i < count; ++i) {
+    size_t b = 0;
+    const bcgs_problem& p = probs[i];
+    if (bcgs_qr_workspace_size(p.m, p.n, p.s, p.variant, p.precision, &b) != BCGS_OK)
+      return BCGS_ERR_INVALID_ARG;
+    total += align256(b);
+  }
+  *bytes = total;
+  return BCGS_OK;
+}
+
+int bcgs_qr_factor_batched(int32_t count, const bcgs_problem* probs, void* workspace,
+                           size_t ws_bytes, void* stream) {
+  size_t need = 0;
+  int rc = bcgs_qr_batched_workspace_size(count, probs, &need);
+  if (rc != BCGS_OK) return rc;
+  if (workspace == nullptr || ws_bytes < need || ((uintptr_t)workspace) % 256 != 0)
+    return BCGS_ERR_WORKSPACE;
+  char* ws = reinterpret_cast<char*>(workspace);
+  size_t off = align256((size_t)count * sizeof(DevStatus));
+  for (int i = 0; i < count; ++i) {
+    const bcgs_problem& p = probs[i];
+    size_t b = 0;
+    bcgs_qr_workspace_size(p.m, p.n, p.s, p.variant, p.precision, &b);
+    rc = bcgs_qr_factor(p.m, p.n, p.s, p.variant, p.precision, p.X, p.ldx, p.Q, p.ldq, p.R, p.ldr,
+                        ws + off, align256(b), stream);
+    if (rc != BCGS_OK) return rc;
+    // copy the problem's status word into the batch's status array once it is done
+    if (cudaMemcpyAsync(ws + (size_t)i * sizeof(DevStatus), ws + off, sizeof(DevStatus),
+                        cudaMemcpyDeviceToDevice,
+                        reinterpret_cast<cudaStream_t>(stream)) != cudaSuccess)
+      return BCGS_ERR_CUDA;
+    off += align256(b);
+  }
+  return BCGS_OK;
+}
+
+int bcgs_qr_batched_status(int32_t count, const void* workspace, void* stream, int32_t* codes,
+                           int32_t* fail_blocks) {
+  if (count < 0 || workspace == nullptr) return BCGS_ERR_INVALID_ARG;
+  cudaStream_t sm = reinterpret_cast<cudaStream_t>(stream);
+  if (cudaStreamSynchronize(sm) != cudaSuccess) return BCGS_ERR_CUDA;
+  int first = BCGS_OK;
+  const char* ws = reinterpret_cast<const char*>(workspace);
+  for (int i = 0; i < count; ++i) {
+    int32_t cb[2] = {0, 0};
+    if (cudaMemcpy(cb, ws + (size_t)i * sizeof(DevStatus), sizeof(cb), cudaMemcpyDeviceToHost) !=
+        cudaSuccess)
+      return BCGS_ERR_CUDA;
+    if (codes) codes[i] = cb[0];
+    if (fail_blocks) fail_blocks[i] = cb[0] ? cb[1] : 0;
+    if (first == BCGS_OK && cb[0] != 0) first = cb[0];
+  }
+  return first;
+}
+
+}  // extern "C"

@@ -1,0 +1,130 @@
+// Internal declarations shared by the translation units of the library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#include "../../include/bcgs_qr.h"
+
+namespace bcgs {
+
+// ---------------------------------------------------------------- status word
+// Lives at the start of every workspace.  code != 0 makes every later kernel of
+// the same factorization return immediately.
+struct DevStatus {
+  int32_t code;
+  int32_t block;   // 1-based block column where the failure happened
+  int32_t pad[62]; // keeps the following buffers 256-byte aligned
+};
+static_assert(sizeof(DevStatus) == 256, "status block is 256 bytes");
+
+__device__ __forceinline__ bool failed(const DevStatus* st) {
+  return st != nullptr && *((volatile const int32_t*)&st->code) != 0;
+}
+__device__ __forceinline__ void set_failure(DevStatus* st, int code, int block) {
+  if (atomicCAS(&st->code, 0, code) == 0) st->block = block;
+}
+
+// ---------------------------------------------------------------- operands
+// A column segment of a tall matrix: ncols columns of m rows, leading dim ld.
+// `fp32` selects the storage type (float when nonzero, double otherwise).
+struct Seg {
+  const void* p;
+  int64_t ld;
+  int32_t ncols;
+  int32_t fp32;
+};
+
+constexpr int kMaxSegA = 4;
+constexpr int kMaxSegB = 3;
+
+struct GramDesc {
+  Seg a[kMaxSegA];
+  Seg b[kMaxSegB];
+  int32_t nsa, nsb;
+  int32_t na, nb;     // total columns of A and B
+  int64_t m;
+  int64_t chunk_rows; // rows per partial-sum chunk (fixed by m)
+  int32_t nchunks;
+};
+
+inline int64_t round_up(int64_t v, int64_t a) { return (v + a - 1) / a * a; }
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// Deterministic row partition of the Gram reduction: depends on m only.
+void gram_partition(int64_t m, int64_t* chunk_rows, int32_t* nchunks);
+size_t gram_partial_doubles(int64_t m, int32_t na, int32_t nb);
+
+// Launchers (return cudaError_t of the launch).
+cudaError_t launch_gram(const GramDesc& d, double* partial, double* G, int ldg,
+                        DevStatus* st, cudaStream_t stream);
+
+// W = (V - Qseg C) T^{-1}; C (c x s, ldc) and T (s x s, ldt) on device; T may be null.
+struct ProjDesc {
+  Seg v;            // m x s input
+  Seg q;            // m x c basis (q.ncols = c; may be 0)
+  const double* C; int32_t ldc;
+  const double* T; int32_t ldt;
+  void* w; int64_t ldw; int32_t w_fp32;
+  int64_t m; int32_t s;
+};
+cudaError_t launch_project(const ProjDesc& d, DevStatus* st, cudaStream_t stream);
+
+// TSQR of an m x s block.
+struct TsqrPlan {
+  int64_t m; int32_t s;
+  int32_t mt;            // leaf tile rows
+  int32_t fan;           // children per tree node
+  int32_t nlevels;       // leaf level + node levels (root has 1 node)
+  int32_t nodes[32];     // nodes per level (level 0 = leaf tiles)
+  size_t off_h;          // leaf reflectors: nodes[0] * mt * s doubles
+  size_t off_tau[32];    // taus per level: nodes * s
+  size_t off_lvl[32];    // node-level stacked matrices (level >= 1): nodes * (fan*s) * s
+  size_t off_b[32];      // apply-phase coefficient blocks per level: nodes * s * s
+  size_t doubles;        // total
+};
+void tsqr_plan(int64_t m, int32_t s, TsqrPlan* plan);
+cudaError_t launch_tsqr(const TsqrPlan& plan, Seg a, void* q, int64_t ldq, int32_t q_fp32,
+                        double* R, int32_t ldr, double* work, DevStatus* st, int32_t block,
+                        cudaStream_t stream);
+
+// Small FP64 tails (one CTA each); see tail.cu for the exact formulas.
+struct TailDesc {
+  int32_t s, c;         // block size; rows of the Y / Z blocks (columns of the previous basis)
+  const double* G; int32_t ldg;  // reduced Gram output
+  int32_t gy, gz, gom, gp, gt;   // row/col offsets, see tail.cu
+  const double* S_prev;  // c x s first-pass coefficients S_{1:k-1,k}  (ld = n_max)
+  const double* Sd_prev; // s x s S_kk
+  double* S_next;        // (c+s) x s S_{1:k,k+1} (ld = n_max)
+  double* Sd_next;       // s x s
+  double* Y; double* Yd; // c x s (ld n_max) copy of Y_{1:k-1,k}; s x s Y_kk
+  double* R; int32_t ldr; int32_t r_row0, r_col0; // R block column destination
+  int32_t has_next, chol_next, block;
+  int32_t ldsm;          // leading dim of S/Y buffers (n_max)
+};
+cudaError_t launch_tail_1s2s(const TailDesc& d, DevStatus* st, cudaStream_t stream);
+// S22 = chol(T2 - S12^T S12) from the startup Gram [Q1 X2]^T X2 (1S only).
+cudaError_t launch_tail_start_1s(int32_t s, const double* G, int32_t ldg, double* S, int32_t ldsm,
+                                 double* Sd, int32_t block, DevStatus* st, cudaStream_t stream);
+// Copy S12 = G[0:s,0:s] (2S startup), and BCGSI+ R assembly.
+cudaError_t launch_copy_small(int32_t rows, int32_t cols, const double* A, int32_t lda,
+                              double* B, int32_t ldb, DevStatus* st, cudaStream_t stream);
+cudaError_t launch_r_assemble(int32_t c, int32_t s, const double* S, int32_t lds,
+                              const double* Y, int32_t ldy, const double* Sd, const double* Yd,
+                              double* R, int32_t ldr, int32_t col0, DevStatus* st,
+                              cudaStream_t stream);
+cudaError_t launch_chol(int32_t s, const double* A, int32_t lda, double* R, int32_t ldr,
+                        int32_t block, DevStatus* st, cudaStream_t stream);
+cudaError_t launch_zero_lower(int32_t n, double* R, int32_t ldr, cudaStream_t stream);
+cudaError_t launch_reset_status(DevStatus* st, cudaStream_t stream);
+
+// ---------------------------------------------------------------- instrumentation
+// Kernel classes timed by the optional profiler (bcgs_profile_read).
+enum ProfClass { kProfGramPartial = 0, kProfGramReduce = 1, kProfProject = 2, kProfTsqr = 3,
+                 kProfTail = 4, kProfClasses = 5 };
+void note_launch(int n);
+int prof_begin(cudaStream_t stream);  // -1 when profiling is off
+void prof_end(int slot, int cls, cudaStream_t stream, double flops, double bytes);
+
+}  // namespace bcgs

@@ -1,0 +1,324 @@
+// TSQR: the unconditionally stable intraorthogonalization of an m x s block
+// (Sec. 1; [Q_1, R_11] = TSQR(X_1) in Alg. 1 and Alg. 2; BCGSI+P-2S and BCGSI+
+// use it for every block).  The paper took TSQR from Trilinos (Sec. 4) and fixes
+// no tree; this is a fixed-shape tree on one GPU:
+//
+//   level 0     one CTA per row tile of mt rows: Householder QR in shared
+//               memory, reflectors kept in the workspace, the s x s R factor
+//               written into its parent's stacked matrix;
+//   level l>=1  one CTA per node: Householder QR of `fan` stacked R factors;
+//   root        diag(R) made >= 0 (signs D), R written out;
+//   apply       top-down, each node forms H [B; 0] for the coefficient block B
+//               it receives from its parent (the root starts from B = D), and
+//               the leaves write the explicit Q rows.
+//
+// The Householder step per column follows the oracle's convention
+// (beta = -sign(a_jj) ||a_j||, v_j = 1, tau = (beta - a_jj) / beta), so the
+// sign-normalized factors agree with a plain Householder QR up to rounding.
+#include "bcgs_internal.cuh"
+
+namespace bcgs {
+
+namespace {
+
+constexpr int kTsqrThreads = 256;
+constexpr int kWarps = kTsqrThreads / 32;
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// In-place Householder QR of the rows x s column-major matrix A (ld = rows) in
+// shared memory.  On return A holds R in its upper triangle and v_j below the
+// diagonal (v_j has an implicit 1 at row j); tau[j] the reflector scalars.
+__device__ void block_householder(double* A, int rows, int s, double* tau) {
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  for (int j = 0; j < s; ++j) {
+    double* aj = A + (size_t)j * rows;
+    if (warp == 0) {
+      double sum = 0.0;
+      for (int r = j + 1 + lane; r < rows; r += 32) sum = fma(aj[r], aj[r], sum);
+      sum = warp_sum(sum);
+      const double x0 = aj[j];
+      const double alpha = sqrt(fma(x0, x0, sum));
+      double t = 0.0, beta = 0.0, denom = 1.0;
+      if (alpha != 0.0) {
+        beta = x0 >= 0.0 ? -alpha : alpha;
+        denom = x0 - beta;
+        t = (beta - x0) / beta;
+      }
+      if (alpha != 0.0)
+        for (int r = j + 1 + lane; r < rows; r += 32) aj[r] = aj[r] / denom;
+      __syncwarp();
+      if (lane == 0) {
+        tau[j] = t;
+        if (alpha != 0.0) aj[j] = beta;
+      }
+    }
+    __syncthreads();
+    const double t = tau[j];
+    if (t != 0.0) {
+      for (int l = j + 1 + warp; l < s; l += kWarps) {
+        double* al = A + (size_t)l * rows;
+        double w = 0.0;
+        for (int r = j + 1 + lane; r < rows; r += 32) w = fma(aj[r], al[r], w);
+        w = warp_sum(w) + al[j];
+        w *= t;
+        __syncwarp();  // every lane has read al[j] before lane 0 updates it
+        if (lane == 0) al[j] -= w;
+        for (int r = j + 1 + lane; r < rows; r += 32) al[r] = fma(-aj[r], w, al[r]);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// E <- H_0 H_1 ... H_{s-1} E for reflectors stored as by block_householder.
+__device__ void block_apply_q(const double* V, const double* tau, double* E, int rows, int s) {
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  for (int j = s - 1; j >= 0; --j) {
+    const double t = tau[j];
+    if (t != 0.0) {
+      const double* vj = V + (size_t)j * rows;
+      for (int c = warp; c < s; c += kWarps) {
+        double* ec = E + (size_t)c * rows;
+        double w = 0.0;
+        for (int r = j + 1 + lane; r < rows; r += 32) w = fma(vj[r], ec[r], w);
+        w = warp_sum(w) + ec[j];
+        w *= t;
+        __syncwarp();
+        if (lane == 0) ec[j] -= w;
+        for (int r = j + 1 + lane; r < rows; r += 32) ec[r] = fma(-vj[r], w, ec[r]);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Root: make diag(R) >= 0 and write R (s x s, ldr) and the signs D into bout (s x s).
+__device__ void finish_root(const double* A, int rows, int s, double* R, int ldr, double* bout,
+                            DevStatus* st, int block) {
+  __shared__ int bad_rank, bad_fin;
+  if (threadIdx.x == 0) { bad_rank = 0; bad_fin = 0; }
+  __syncthreads();
+  for (int e = threadIdx.x; e < s * s; e += blockDim.x) {
+    const int i = e % s, j = e / s;
+    const double d = A[i + (size_t)i * rows] < 0.0 ? -1.0 : 1.0;
+    double v = i <= j ? d * A[i + (size_t)j * rows] : 0.0;
+    R[i + (size_t)j * ldr] = v;
+    bout[i + (size_t)j * s] = (i == j) ? d : 0.0;
+    if (!isfinite(v)) bad_fin = 1;
+    if (i == j && v == 0.0) bad_rank = 1;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (bad_fin) set_failure(st, BCGS_ERR_NONFINITE, block);
+    else if (bad_rank) set_failure(st, BCGS_ERR_RANK_DEFICIENT, block);
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kTsqrThreads)
+tsqr_leaf_factor(TsqrPlan p, Seg a, double* work, double* R, int32_t ldr, DevStatus* st,
+                 int32_t block) {
+  if (failed(st)) return;
+  extern __shared__ double sm[];
+  __shared__ double tau[64];
+  const int mt = p.mt, s = p.s;
+  double* A = sm;  // mt x s
+  const int t = blockIdx.x;
+  const int64_t row0 = (int64_t)t * mt;
+  const int rows_here = (int)(p.m - row0 < (int64_t)mt ? p.m - row0 : (int64_t)mt);
+  const T* src = reinterpret_cast<const T*>(a.p);
+  for (int e = threadIdx.x; e < mt * s; e += kTsqrThreads) {
+    const int r = e % mt, j = e / mt;
+    A[e] = r < rows_here ? (double)src[row0 + r + (int64_t)j * a.ld] : 0.0;
+  }
+  __syncthreads();
+  block_householder(A, mt, s, tau);
+  double* H = work + p.off_h + (size_t)t * mt * s;
+  for (int e = threadIdx.x; e < mt * s; e += kTsqrThreads) H[e] = A[e];
+  double* tg = work + p.off_tau[0] + (size_t)t * s;
+  for (int j = threadIdx.x; j < s; j += kTsqrThreads) tg[j] = tau[j];
+  if (p.nlevels == 1) {
+    finish_root(A, mt, s, R, ldr, work + p.off_b[0], st, block);
+    return;
+  }
+  // R_t -> parent's stacked matrix, rows [(t % fan) s, +s)
+  const int fan = p.fan, ldp = fan * s;
+  double* P = work + p.off_lvl[1] + (size_t)(t / fan) * ldp * s;
+  const int rbase = (t % fan) * s;
+  for (int e = threadIdx.x; e < s * s; e += kTsqrThreads) {
+    const int i = e % s, j = e / s;
+    P[rbase + i + (size_t)j * ldp] = i <= j ? A[i + (size_t)j * mt] : 0.0;
+  }
+}
+
+__global__ void __launch_bounds__(kTsqrThreads)
+tsqr_node_factor(TsqrPlan p, int32_t level, double* work, double* R, int32_t ldr, DevStatus* st,
+                 int32_t block) {
+  if (failed(st)) return;
+  extern __shared__ double sm[];
+  __shared__ double tau[64];
+  const int s = p.s, fan = p.fan, rows = fan * s;
+  const int n = blockIdx.x;
+  const int nchild = min(fan, p.nodes[level - 1] - n * fan);
+  double* A = sm;
+  double* G = work + p.off_lvl[level] + (size_t)n * rows * s;
+  for (int e = threadIdx.x; e < rows * s; e += kTsqrThreads) {
+    const int r = e % rows;
+    A[e] = r < nchild * s ? G[e] : 0.0;
+  }
+  __syncthreads();
+  block_householder(A, rows, s, tau);
+  for (int e = threadIdx.x; e < rows * s; e += kTsqrThreads) G[e] = A[e];
+  double* tg = work + p.off_tau[level] + (size_t)n * s;
+  for (int j = threadIdx.x; j < s; j += kTsqrThreads) tg[j] = tau[j];
+  if (level == p.nlevels - 1) {
+    finish_root(A, rows, s, R, ldr, work + p.off_b[level], st, block);
+    return;
+  }
+  double* P = work + p.off_lvl[level + 1] + (size_t)(n / fan) * rows * s;
+  const int rbase = (n % fan) * s;
+  for (int e = threadIdx.x; e < s * s; e += kTsqrThreads) {
+    const int i = e % s, j = e / s;
+    P[rbase + i + (size_t)j * rows] = i <= j ? A[i + (size_t)j * rows] : 0.0;
+  }
+}
+
+__global__ void __launch_bounds__(kTsqrThreads)
+tsqr_node_apply(TsqrPlan p, int32_t level, double* work, const DevStatus* st) {
+  if (failed(st)) return;
+  extern __shared__ double sm[];
+  __shared__ double tau[64];
+  const int s = p.s, fan = p.fan, rows = fan * s;
+  const int n = blockIdx.x;
+  const int nchild = min(fan, p.nodes[level - 1] - n * fan);
+  double* V = sm;
+  double* E = sm + (size_t)rows * s;
+  const double* G = work + p.off_lvl[level] + (size_t)n * rows * s;
+  const double* B = work + p.off_b[level] + (size_t)n * s * s;
+  for (int e = threadIdx.x; e < rows * s; e += kTsqrThreads) {
+    const int r = e % rows, j = e / rows;
+    V[e] = G[e];
+    E[e] = r < s ? B[r + (size_t)j * s] : 0.0;
+  }
+  for (int j = threadIdx.x; j < s; j += kTsqrThreads) tau[j] = work[p.off_tau[level] + (size_t)n * s + j];
+  __syncthreads();
+  block_apply_q(V, tau, E, rows, s);
+  for (int e = threadIdx.x; e < nchild * s * s; e += kTsqrThreads) {
+    const int g = e / (s * s), rem = e % (s * s);
+    const int i = rem % s, j = rem / s;
+    work[p.off_b[level - 1] + (size_t)(n * fan + g) * s * s + i + (size_t)j * s] =
+        E[g * s + i + (size_t)j * rows];
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kTsqrThreads)
+tsqr_leaf_apply(TsqrPlan p, const double* work, void* q, int64_t ldq, const DevStatus* st) {
+  if (failed(st)) return;
+  extern __shared__ double sm[];
+  __shared__ double tau[64];
+  const int mt = p.mt, s = p.s;
+  const int t = blockIdx.x;
+  double* V = sm;
+  double* E = sm + (size_t)mt * s;
+  const double* H = work + p.off_h + (size_t)t * mt * s;
+  const double* B = work + p.off_b[0] + (size_t)t * s * s;
+  for (int e = threadIdx.x; e < mt * s; e += kTsqrThreads) {
+    const int r = e % mt, j = e / mt;
+    V[e] = H[e];
+    E[e] = r < s ? B[r + (size_t)j * s] : 0.0;
+  }
+  for (int j = threadIdx.x; j < s; j += kTsqrThreads) tau[j] = work[p.off_tau[0] + (size_t)t * s + j];
+  __syncthreads();
+  block_apply_q(V, tau, E, mt, s);
+  const int64_t row0 = (int64_t)t * mt;
+  const int rows_here = (int)(p.m - row0 < (int64_t)mt ? p.m - row0 : (int64_t)mt);
+  T* dst = reinterpret_cast<T*>(q);
+  for (int e = threadIdx.x; e < mt * s; e += kTsqrThreads) {
+    const int r = e % mt, j = e / mt;
+    if (r < rows_here) dst[row0 + r + (int64_t)j * ldq] = (T)E[e];
+  }
+}
+
+template <typename T>
+cudaError_t launch_tsqr_t(const TsqrPlan& p, Seg a, void* q, int64_t ldq, double* R, int32_t ldr,
+                          double* work, DevStatus* st, int32_t block, cudaStream_t stream) {
+  const size_t leaf_f = (size_t)p.mt * p.s * sizeof(double);
+  const size_t node_f = (size_t)p.fan * p.s * p.s * sizeof(double);
+  cudaError_t e;
+  e = cudaFuncSetAttribute(tsqr_leaf_factor<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)leaf_f);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(tsqr_leaf_apply<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(2 * leaf_f));
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(tsqr_node_factor, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)node_f);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(tsqr_node_apply, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(2 * node_f));
+  if (e != cudaSuccess) return e;
+  const int slot = prof_begin(stream);
+  tsqr_leaf_factor<T><<<p.nodes[0], kTsqrThreads, leaf_f, stream>>>(p, a, work, R, ldr, st, block);
+  for (int l = 1; l < p.nlevels; ++l)
+    tsqr_node_factor<<<p.nodes[l], kTsqrThreads, node_f, stream>>>(p, l, work, R, ldr, st, block);
+  for (int l = p.nlevels - 1; l >= 1; --l)
+    tsqr_node_apply<<<p.nodes[l], kTsqrThreads, 2 * node_f, stream>>>(p, l, work, st);
+  tsqr_leaf_apply<T><<<p.nodes[0], kTsqrThreads, 2 * leaf_f, stream>>>(p, work, q, ldq, st);
+  // Householder QR and explicit Q of the m x s block: 2 m s^2 flops each.
+  prof_end(slot, kProfTsqr, stream, 4.0 * (double)p.m * p.s * p.s,
+           2.0 * (double)p.m * p.s * sizeof(T) + 2.0 * (double)p.nodes[0] * p.mt * p.s * 8.0);
+  note_launch(2 * p.nlevels);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+void tsqr_plan(int64_t m, int32_t s, TsqrPlan* p) {
+  p->m = m;
+  p->s = s;
+  // Leaf tiles of about 8192 doubles (64 KB of shared memory), at least s rows.
+  int64_t mt = round_up(8192 / s, 32);
+  if (mt > 1024) mt = 1024;
+  if (mt < round_up(s, 32)) mt = round_up(s, 32);
+  if (mt > round_up(m, 32)) mt = round_up(m, 32) < s ? s : round_up(m, 32);
+  p->mt = (int32_t)mt;
+  int fan = (int)(mt / s);
+  if (fan < 2) fan = 2;
+  p->fan = fan;
+  int lvl = 0;
+  p->nodes[0] = (int32_t)ceil_div(m, mt);
+  while (p->nodes[lvl] > 1 && lvl < 31) {
+    p->nodes[lvl + 1] = (int32_t)ceil_div(p->nodes[lvl], fan);
+    ++lvl;
+  }
+  p->nlevels = lvl + 1;
+  size_t off = 0;
+  p->off_h = off;
+  off += (size_t)p->nodes[0] * mt * s;
+  for (int l = 0; l < p->nlevels; ++l) {
+    p->off_tau[l] = off;
+    off += round_up((size_t)p->nodes[l] * s, 32);
+    p->off_b[l] = off;
+    off += (size_t)p->nodes[l] * s * s;
+    if (l >= 1) {
+      p->off_lvl[l] = off;
+      off += (size_t)p->nodes[l] * fan * s * s;
+    } else {
+      p->off_lvl[l] = 0;
+    }
+  }
+  p->doubles = round_up(off, 32);
+}
+
+cudaError_t launch_tsqr(const TsqrPlan& p, Seg a, void* q, int64_t ldq, int32_t q_fp32, double* R,
+                        int32_t ldr, double* work, DevStatus* st, int32_t block,
+                        cudaStream_t stream) {
+  if (p.m <= 0) return cudaSuccess;
+  (void)q_fp32;
+  return a.fp32 ? launch_tsqr_t<float>(p, a, q, ldq, R, ldr, work, st, block, stream)
+                : launch_tsqr_t<double>(p, a, q, ldq, R, ldr, work, st, block, stream);
+}
+
+}  // namespace bcgs

@@ -36,3 +36,27 @@ def load_golden(name):
 @pytest.fixture
 def golden():
     return load_golden
+
+
+def ensure_library():
+    """Build libbcgs_qr.so in-tree if it is missing (nvcc cross-compiles without a GPU)."""
+    lib = os.path.join(ROOT, "paper_2507_21791_gb300", "libbcgs_qr.so")
+    if not os.path.exists(lib):
+        import __graft_entry__
+
+        __graft_entry__.build()
+    return lib
+
+
+@pytest.fixture(scope="session")
+def cuda():
+    """The CUDA path: skips without a GPU, builds the library if needed."""
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    ensure_library()
+    from paper_2507_21791_gb300 import bcgs
+
+    bcgs.load_library()
+    return bcgs

@@ -1,0 +1,87 @@
+"""The C ABI library loads and exports every symbol include/bcgs_qr.h declares;
+host-side argument checks (no GPU needed: they return before any CUDA call)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from conftest import ROOT, ensure_library
+
+
+def declared_symbols():
+    hdr = open(os.path.join(ROOT, "include", "bcgs_qr.h")).read()
+    return sorted(set(re.findall(r"^BCGS_API\s+[\w\s\*]+?\b(bcgs_\w+)\s*\(", hdr, flags=re.M)))
+
+
+def test_header_declares_the_expected_entry_points():
+    syms = declared_symbols()
+    for name in ("bcgs_qr_init", "bcgs_qr_step", "bcgs_qr_factor", "bcgs_qr_finish", "bcgs_qr_sync",
+                 "bcgs_qr_factor_batched", "bcgs_gram", "bcgs_project", "bcgs_tsqr", "bcgs_chol"):
+        assert name in syms
+
+
+def test_library_exports_every_declared_symbol():
+    ensure_library()
+    from paper_2507_21791_gb300 import bcgs
+
+    lib = bcgs.load_library()
+    for name in declared_symbols():
+        assert hasattr(lib, name), name
+    bound = {n for n, _, _ in bcgs.SIGNATURES}
+    assert bound == set(declared_symbols())
+
+
+def test_status_strings_and_version():
+    ensure_library()
+    from paper_2507_21791_gb300 import bcgs
+
+    lib = bcgs.load_library()
+    assert lib.bcgs_version() >= 100
+    for code in range(9):
+        assert len(lib.bcgs_status_string(code)) > 0
+    assert lib.bcgs_status_string(99) == b"unknown status"
+
+
+def test_workspace_size_queries():
+    ensure_library()
+    from paper_2507_21791_gb300 import bcgs
+
+    m, n, s = 10000, 64, 8
+    sizes = {v: bcgs.workspace_size(m, n, s, v) for v in bcgs.VARIANTS}
+    # 1S needs no separate projected block V; the others do
+    assert sizes["bcgsi+p-1s"] < sizes["bcgsi+p-2s"]
+    assert bcgs.workspace_size(m, n, s, "bcgsi+p-1s", "fp32") < sizes["bcgsi+p-1s"]
+    big = bcgs.workspace_size(2 ** 22, 256, 16, "bcgsi+p-1s")
+    assert 2 ** 22 * 16 * 8 < big < 2 ** 22 * 16 * 8 * 3
+
+
+@pytest.mark.parametrize("m,n,s", [(100, 30, 8), (100, 16, 0), (4, 8, 8), (100, 64, 65),
+                                   (100, 4096, 8)])
+def test_invalid_shapes_rejected_without_a_gpu(m, n, s):
+    ensure_library()
+    from paper_2507_21791_gb300 import bcgs
+
+    lib = bcgs.load_library()
+    out = ctypes.c_size_t(0)
+    assert lib.bcgs_qr_workspace_size(m, n, s, 1, 0, ctypes.byref(out)) == 1
+    # factor with bogus pointers: rejected before anything is enqueued
+    assert lib.bcgs_qr_factor(m, n, s, 1, 0, 8, m, 16, m, 32, n, 256, 1 << 20, None) == 1
+
+
+def test_bad_enums_and_null_pointers_rejected():
+    ensure_library()
+    from paper_2507_21791_gb300 import bcgs
+
+    lib = bcgs.load_library()
+    out = ctypes.c_size_t(0)
+    assert lib.bcgs_qr_workspace_size(100, 16, 8, 3, 0, ctypes.byref(out)) == 1
+    assert lib.bcgs_qr_workspace_size(100, 16, 8, 1, 2, ctypes.byref(out)) == 1
+    assert lib.bcgs_qr_factor(100, 16, 8, 1, 0, None, 100, 16, 100, 32, 16, 256, 1 << 20, None) == 1
+    h = ctypes.c_void_p(None)
+    assert lib.bcgs_qr_init(ctypes.byref(h), 100, 16, 8, 1, 0, None, 100, 32, 16, 256, 1 << 20, None) == 1
+    assert lib.bcgs_qr_step(None, None, 100) == 1
+    # misaligned workspace
+    assert lib.bcgs_qr_factor(100, 16, 8, 1, 0, 8, 100, 16, 100, 32, 16, 257, 1 << 20, None) == 5
+    # too small workspace
+    assert lib.bcgs_qr_factor(100, 16, 8, 1, 0, 8, 100, 16, 100, 32, 16, 256, 1024, None) == 5

@@ -1,0 +1,155 @@
+"""End-to-end parity of the three variants on the GPU (through the C ABI)
+against the CPU oracle, on seeded inputs with controlled kappa.
+
+Gates (backward quantities, kappa-independent):
+    ||X - Q R||_F / ||X||_F <= 1e-13,   ||I - Q^T Q||_2 <= 1e-12
+for kappa <= 1e8 (BCGSI+P-1S only where u kappa^2 << 1, Table 1).
+Forward agreement with the oracle (both are backward stable, so the factors
+differ by O(kappa u) times a modest polynomial in n):
+    ||R - R_oracle||_F / ||R_oracle||_F <= 10 n kappa u,  max |Q - Q_oracle| <= 10 n kappa u.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2507_21791_gb300 import synth
+
+U64 = np.finfo(np.float64).eps / 2
+VARIANTS = ["bcgsi+", "bcgsi+p-1s", "bcgsi+p-2s"]
+pytestmark = pytest.mark.gpu
+
+
+def run_gpu(cuda, X, s, variant):
+    Q, R, code, blk = cuda.factor(cuda.to_device_colmajor(X), s, variant)
+    return Q.cpu().numpy(), R.cpu().numpy(), code, blk
+
+
+def check_against_oracle(X, Q, R, s, variant, kappa_gate=True):
+    n = X.shape[1]
+    Qo, Ro = oracle.factor(X, s, variant)
+    k = oracle.kappa(Ro)
+    res, loo = oracle.residual(X, Q, R), oracle.loo(Q)
+    assert res <= 1e-13, res
+    assert loo <= 1e-12, loo
+    tol = 10 * n * k * U64
+    assert np.linalg.norm(R - Ro) / np.linalg.norm(Ro) <= tol
+    assert np.max(np.abs(Q - Qo)) <= tol
+    assert np.array_equal(np.tril(R, -1), np.zeros_like(R))
+    assert np.all(np.diag(R) > 0)
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_small_config_m10000_n64_s8_kappa1e4(cuda, variant):
+    X = synth.make_matrix_np(10000, 64, 1e4, seed=1000)
+    Q, R, code, _ = run_gpu(cuda, X, 8, variant)
+    assert code == 0
+    check_against_oracle(X, Q, R, 8, variant)
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+@pytest.mark.parametrize("m,n,s", [(8, 8, 8), (50, 8, 4), (300, 12, 1), (1001, 24, 8),
+                                   (4099, 96, 32), (70000, 48, 16), (33, 32, 16), (200, 6, 3),
+                                   (130, 128, 64)])
+def test_shapes(cuda, variant, m, n, s):
+    X = synth.make_matrix_np(m, n, 1e3, seed=m * 3 + n)
+    Q, R, code, _ = run_gpu(cuda, X, s, variant)
+    assert code == 0
+    check_against_oracle(X, Q, R, s, variant)
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+@pytest.mark.parametrize("kappa", [1e2, 1e5, 1e8])
+def test_kappa_sweep(cuda, variant, kappa):
+    if variant == "bcgsi+p-1s" and kappa >= 1e8:
+        pytest.skip("BCGSI+P-1S needs O(u) kappa^2 <= 1 (Table 1)")
+    X = synth.make_matrix_np(20000, 64, kappa, seed=int(np.log10(kappa)))
+    Q, R, code, _ = run_gpu(cuda, X, 8, variant)
+    assert code == 0
+    check_against_oracle(X, Q, R, 8, variant)
+
+
+def test_row_scaled_input(cuda):
+    X = synth.make_matrix_np(20000, 64, 1e5, seed=77, row_scaled=True)
+    for v in VARIANTS:
+        Q, R, code, _ = run_gpu(cuda, X, 16, v)
+        assert code == 0
+        check_against_oracle(X, Q, R, 16, v)
+
+
+def test_one_sync_breaks_down_beyond_its_range(cuda):
+    """kappa = 1e10: u kappa^2 >> 1, BCGSI+P-1S's Pythagorean chol fails (Table 1);
+    BCGSI+ and BCGSI+P-2S keep O(u) loss of orthogonality."""
+    X = synth.make_matrix_np(5000, 64, 1e10, seed=5)
+    _, _, code, blk = run_gpu(cuda, X, 8, "bcgsi+p-1s")
+    with pytest.raises(oracle.Breakdown):
+        oracle.factor(X, 8, "bcgsi+p-1s")
+    assert cuda.STATUS[code] in ("not_spd", "nonfinite") and blk >= 2
+    for v in ("bcgsi+", "bcgsi+p-2s"):
+        Q, R, code, _ = run_gpu(cuda, X, 8, v)
+        assert code == 0
+        assert oracle.loo(Q) <= 1e-12 and oracle.residual(X, Q, R) <= 1e-13
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_breakdown_statuses(cuda, variant):
+    X = synth.make_matrix_np(2000, 32, 1e2, seed=9)
+    Xz = X.copy()
+    Xz[:, :8] = 0.0
+    _, _, code, blk = run_gpu(cuda, Xz, 8, variant)
+    assert cuda.STATUS[code] == "rank_deficient" and blk == 1
+    Xn = X.copy()
+    Xn[17, 20] = np.nan
+    _, _, code, blk = run_gpu(cuda, Xn, 8, variant)
+    assert cuda.STATUS[code] in ("nonfinite", "not_spd", "rank_deficient") and blk == 3
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_bitwise_determinism(cuda, variant):
+    X = synth.make_matrix_np(30000, 48, 1e4, seed=21)
+    Xd = cuda.to_device_colmajor(X)
+    Q1, R1, _, _ = cuda.factor(Xd, 8, variant)
+    Q2, R2, _, _ = cuda.factor(Xd, 8, variant)
+    assert np.array_equal(Q1.cpu().numpy(), Q2.cpu().numpy())
+    assert np.array_equal(R1.cpu().numpy(), R2.cpu().numpy())
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_step_interface_matches_factor(cuda, variant):
+    """bcgs_qr_step over blocks gives the same bits as bcgs_qr_factor, and the
+    number of final columns follows delayed normalization (Sec. 2)."""
+    m, n, s = 5000, 40, 8
+    X = synth.make_matrix_np(m, n, 1e3, seed=31)
+    Xd = cuda.to_device_colmajor(X)
+    Qf, Rf, _, _ = cuda.factor(Xd, s, variant)
+    h = cuda.QRHandle(m, n, s, variant)
+    for j in range(n // s):
+        h.step(Xd[:, j * s:(j + 1) * s])
+        code, n_final, _ = h.sync()
+        assert code == 0
+        if variant == "bcgsi+":
+            assert n_final == (j + 1) * s
+        else:
+            assert n_final == max(j, 1) * s
+    h.finish()
+    code, n_final, _ = h.sync()
+    assert code == 0 and n_final == n
+    assert np.array_equal(h.Q.cpu().numpy(), Qf.cpu().numpy())
+    assert np.array_equal(h.R.cpu().numpy(), Rf.cpu().numpy())
+    with pytest.raises(cuda.BCGSError):
+        h.step(Xd[:, :s])
+    h.close()
+
+
+def test_leading_dimensions_larger_than_m(cuda):
+    import torch
+
+    m, n, s = 3000, 32, 8
+    X = synth.make_matrix_np(m, n, 1e3, seed=41)
+    big = torch.zeros((n, m + 37), dtype=torch.float64, device="cuda")
+    big[:, :m] = torch.from_numpy(np.ascontiguousarray(X.T)).cuda()
+    Xd = big.T[:m]
+    Q = torch.zeros((n, m + 5), dtype=torch.float64, device="cuda").T[:m]
+    R = torch.zeros((n, n + 3), dtype=torch.float64, device="cuda").T[:n]
+    Q, R, code, _ = cuda.factor(Xd, s, "bcgsi+p-1s", Q=Q, R=R)
+    assert code == 0
+    check_against_oracle(X, Q.cpu().numpy(), R.cpu().numpy(), s, "bcgsi+p-1s")
