@@ -1,0 +1,402 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 BCGS QR library.
+
+Workload (one step = one whole factorization, i.e. every block step of the hot
+path over one synthetic matrix): single FP64 economic QR of X = U diag(sigma) V^T,
+m = 2^22 rows, n = 256 columns, block size s = 16 (q = 16 blocks),
+kappa = 1e5 (inside every variant's O(u)-loss-of-orthogonality range, so the
+variants are compared at equal loss of orthogonality), BCGSI+P-1S timed; BCGSI+
+and BCGSI+P-2S are timed the same way for the speedup.
+
+value  = algorithmic HBM bytes of the fused BCGSI+P-1S schedule per step / time
+         (GB/s); bytes per step = 8 m s q(q-1)/2 (each block reads the previous
+         basis once) + 5 * 8 m n (X twice, U written and read, Q written).
+e2e    = the same metric through bcgs_qr_factor with pinned host buffers: the
+         host->device copy of X and the device->host copy of Q and R are inside
+         the timed region.
+X (8.6 GB) and Q (8.6 GB) are far larger than the 129 MB L2, so no L2 flush is
+needed between steps.
+
+`--impl reference` times the CPU oracle (the method's plain FP64 restatement)
+on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "BCGSI+P-1S HBM GB/s & speedup vs BCGSI+ at equal loss-of-orth.; p99 latency"
+M, N, S, KAPPA = 2 ** 22, 256, 16, 1e5
+WORKLOAD = "single FP64 QR m=2^22 n=256 s=16 (q=16) BCGSI+P-1S, X=U diag(sigma) V^T kappa=1e5"
+FP64_PEAK_TFLOPS = 1.25  # GB300 FP64 rate of the profiling recipe's table (nominal)
+# DRAM traffic per launch of the dominant kernel from one ncu capture
+# (profiles/gram_partial_kernel.md); None until a capture of the current kernel exists.
+GRAM_TRAFFIC = None
+ORACLE_SAMPLE_ROWS = 2 ** 17
+
+
+def alg_bytes_1s(m, n, s, b=8):
+    q = n // s
+    return b * m * s * q * (q - 1) / 2 + 5 * b * m * n
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--no-compare", action="store_true", help="skip timing BCGSI+ and -2S")
+    p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    p.add_argument("--kernel", default=None, choices=["gram", "project", "tsqr"],
+                   help="time one building block alone (for profiling on small cases)")
+    p.add_argument("--m", type=int, default=2 ** 19, help="rows for --kernel")
+    return p.parse_args()
+
+
+# ------------------------------------------------------------------ CPU oracle
+
+ORACLE_SNIPPET = r"""
+import json, os, sys, time
+sys.path.insert(0, {root!r})
+import numpy as np
+import oracle
+from paper_2507_21791_gb300 import synth
+m, n, s, kappa, budget = {m}, {n}, {s}, {kappa}, {budget}
+X = synth.make_matrix_np(m, n, kappa, seed=1101)
+reps, t0 = 0, time.perf_counter()
+while True:
+    Q, R = oracle.bcgsi_plus_p_1s(X, s)
+    reps += 1
+    el = time.perf_counter() - t0
+    if el >= budget or reps >= 20:
+        break
+print(json.dumps({{"reps": reps, "seconds": el, "loo": oracle.loo(Q),
+                   "residual": oracle.residual(X, Q, R)}}))
+"""
+
+
+def run_oracle_sample(budget_s=10.0, rows=ORACLE_SAMPLE_ROWS):
+    cores = os.cpu_count() or 1
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[k] = str(cores)
+    code = ORACLE_SNIPPET.format(root=ROOT, m=rows, n=N, s=S, kappa=KAPPA, budget=budget_s)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
+    if r.returncode != 0:
+        raise RuntimeError("oracle sample failed: " + r.stderr[-2000:])
+    out = json.loads(r.stdout.strip().splitlines()[-1])
+    gbs = alg_bytes_1s(rows, N, S) * out["reps"] / out["seconds"] / 1e9
+    return {"value": gbs, "unit": "GB/s", "cores": cores, "kind": "oracle",
+            "sample": f"BCGSI+P-1S oracle (numpy FP64) on m={rows} rows x n={N}, s={S}, "
+                      f"kappa={KAPPA:g}; {out['reps']} factorization(s) in {out['seconds']:.1f} s; "
+                      f"GB/s = algorithmic bytes of that m per factorization / time",
+            "seconds": out["seconds"], "loo": out["loo"], "residual": out["residual"]}
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.index}",
+                                       f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.f.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ GPU arm
+
+def main_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # Oracle sample first, in a fresh process, before heavy GPU work.
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = run_oracle_sample()
+
+    import __graft_entry__
+
+    if not os.path.exists(os.path.join(ROOT, "paper_2507_21791_gb300", "libbcgs_qr.so")):
+        __graft_entry__.build()
+    from paper_2507_21791_gb300 import bcgs, synth
+
+    bcgs.load_library()
+    stream = torch.cuda.current_stream(dev)
+    X = synth.make_matrix_torch(M, N, KAPPA, seed=1000 + 1 * 100 + rank, device=str(dev))
+    torch.cuda.synchronize()
+
+    def run_variant(variant, profile=False):
+        Q = bcgs.empty_colmajor(M, N, torch.float64, dev)
+        R = bcgs.empty_colmajor(N, N, torch.float64, dev)
+        ws = torch.empty(bcgs.workspace_size(M, N, S, variant), dtype=torch.uint8, device=dev)
+        for _ in range(args.warmup):
+            bcgs.factor_async(X, S, variant, "fp64", Q, R, ws)
+        code, blk = bcgs.factor_status(ws)
+        if code != 0:
+            raise RuntimeError(f"{variant}: status {bcgs.STATUS[code]} at block {blk}")
+        barrier()
+        clocks = ClockSampler(local) if profile else None
+        if clocks:
+            clocks.start()
+            time.sleep(0.3)
+            bcgs.profile_enable(True)
+        l0 = bcgs.launch_count()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            bcgs.factor_async(X, S, variant, "fp64", Q, R, ws)
+        e1.record(stream)
+        barrier()
+        launches = bcgs.launch_count() - l0
+        ms = e0.elapsed_time(e1) / args.steps
+        prof = None
+        if clocks:
+            prof = {k: bcgs.profile_read(k) for k in bcgs.PROFILE_CLASSES}
+            bcgs.profile_enable(False)
+            prof["clocks"] = clocks.stop()
+        code, blk = bcgs.factor_status(ws)
+        if code != 0:
+            raise RuntimeError(f"{variant}: status {bcgs.STATUS[code]} at block {blk}")
+        eye = torch.eye(N, dtype=torch.float64, device=dev)
+        G = (eye - Q.T @ Q).cpu().numpy()
+        loo = float(np.linalg.norm(G, 2))
+        D = X - Q @ R
+        res = math.sqrt((D * D).sum().item() / (X * X).sum().item())
+        del D
+        del ws
+        return {"ms": ms, "launches": launches, "loo": loo, "residual": res, "prof": prof,
+                "Q": Q, "R": R}
+
+    main = run_variant("bcgsi+p-1s", profile=True)
+    t = torch.tensor([main["ms"]], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = t.item()
+    value = world * alg_bytes_1s(M, N, S) / (ms_max * 1e-3) / 1e9
+
+    # e2e through the public API with pinned host buffers
+    Xh = torch.empty((N, M), dtype=torch.float64, pin_memory=True).T
+    Xh.copy_(X)
+    Qh = torch.empty((N, M), dtype=torch.float64, pin_memory=True).T
+    Rh = torch.empty((N, N), dtype=torch.float64, pin_memory=True).T
+    Xd = bcgs.empty_colmajor(M, N, torch.float64, dev)
+    Qd, Rd = main["Q"], main["R"]
+    ws = torch.empty(bcgs.workspace_size(M, N, S, "bcgsi+p-1s"), dtype=torch.uint8, device=dev)
+
+    def e2e_step():
+        Xd.copy_(Xh, non_blocking=True)
+        bcgs.factor_async(Xd, S, "bcgsi+p-1s", "fp64", Qd, Rd, ws)
+        Qh.copy_(Qd, non_blocking=True)
+        Rh.copy_(Rd, non_blocking=True)
+
+    for _ in range(args.warmup):
+        e2e_step()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        e2e_step()
+    e1.record(stream)
+    barrier()
+    ms_e2e = e0.elapsed_time(e1) / args.steps
+    te = torch.tensor([ms_e2e], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_value = world * alg_bytes_1s(M, N, S) / (te.item() * 1e-3) / 1e9
+    del ws, Xd, Xh, Qh, Rh
+
+    compare = {}
+    if not args.no_compare:
+        for v in ("bcgsi+", "bcgsi+p-2s"):
+            r = run_variant(v)
+            compare[v] = {"ms": r["ms"], "loo": r["loo"], "residual": r["residual"]}
+            del r
+    compare["bcgsi+p-1s"] = {"ms": main["ms"], "loo": main["loo"], "residual": main["residual"]}
+    speedup = None
+    if "bcgsi+" in compare:
+        speedup = {v: compare["bcgsi+"]["ms"] / compare[v]["ms"] for v in ("bcgsi+p-1s", "bcgsi+p-2s")}
+
+    prof = main["prof"]
+    gl, gms, gfl, gby = prof["gram_partial"]
+    achieved = gfl / (gms * 1e-3) / 1e12 if gms > 0 else None
+    step_ms_total = sum(prof[k][1] for k in bcgs.PROFILE_CLASSES)
+    roofline = {
+        "bound": "alu", "kernel": "gram_partial_kernel (FP64 DFMA)",
+        "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+        "frac": achieved / FP64_PEAK_TFLOPS if achieved else None,
+        "peak_source": "FP64 rate of the profiling recipe (nominal; a DFMA probe measured 1.20)",
+        "traffic": GRAM_TRAFFIC,
+        "launches": gl, "avg_launch_ms": gms / max(gl, 1),
+        "share_of_timed_kernel_time": gms / step_ms_total if step_ms_total else None,
+        "hbm_frac_of_measured_copy": value / 6669.5,
+    }
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "m": M, "n": N, "s": S, "kappa": KAPPA,
+                   "variant": "bcgsi+p-1s", "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "inputs larger than L2 (X and Q 8.6 GB each); no flush"},
+        "e2e": {"value": e2e_value, "unit": "GB/s", "h2d_bytes_per_step": M * N * 8,
+                "d2h_bytes_per_step": M * N * 8 + N * N * 8, "ms_per_step": te.item()},
+        "gpu_launches": main["launches"],
+        "roofline": roofline,
+        "speedup_vs_bcgsi_plus_at_equal_loo": speedup,
+        "variants": compare,
+        "clocks": prof["clocks"],
+        "kernel_time_ms_per_step": {k: prof[k][1] / args.steps for k in bcgs.PROFILE_CLASSES},
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main_kernel(args):
+    """One building block of the cfg shape (n = 256, s = 16) on m rows, alone:
+    gram = the largest synchronization of a BCGSI+P-1S factorization,
+    [Q_{1:14} U X]^T [U X] (256 x 32); project = U = (X - Q_{1:15} S) S_kk^{-1};
+    tsqr = TSQR of an m x 16 block."""
+    import torch
+
+    import __graft_entry__
+
+    if not os.path.exists(os.path.join(ROOT, "paper_2507_21791_gb300", "libbcgs_qr.so")):
+        __graft_entry__.build()
+    from paper_2507_21791_gb300 import bcgs, synth
+
+    bcgs.load_library()
+    m = args.m
+    g = torch.Generator(device="cuda")
+    g.manual_seed(7)
+    A = torch.randn((N, m), dtype=torch.float64, device="cuda", generator=g).T
+    B = torch.randn((2 * S, m), dtype=torch.float64, device="cuda", generator=g).T
+    C = torch.randn((N - S, S), dtype=torch.float64, device="cuda", generator=g).T.contiguous().T
+    T = (torch.eye(S, dtype=torch.float64, device="cuda") * 2.0).T
+    X16 = synth.make_matrix_torch(m, S, 1e3, seed=9)
+
+    def once():
+        if args.kernel == "gram":
+            bcgs.gram(A, B)
+        elif args.kernel == "project":
+            bcgs.project(B[:, :S], A[:, :N - S], C[:N - S], T)
+        else:
+            bcgs.tsqr(X16)
+
+    for _ in range(args.warmup):
+        once()
+    torch.cuda.synchronize()
+    bcgs.profile_enable(True)
+    for _ in range(args.steps):
+        once()
+    torch.cuda.synchronize()
+    cls = {"gram": "gram_partial", "project": "project", "tsqr": "tsqr"}[args.kernel]
+    n, ms, fl, by = bcgs.profile_read(cls)
+    bcgs.profile_enable(False)
+    print(json.dumps({"kernel": args.kernel, "m": m, "launches": n, "avg_ms": ms / max(n, 1),
+                      "tflops": fl / (ms * 1e-3) / 1e12, "alg_gbs": by / (ms * 1e-3) / 1e9}))
+
+
+def main_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    per_step = []
+    info = None
+    budget = 4.0
+    for i in range(args.warmup + args.steps):
+        info = run_oracle_sample(budget_s=budget, rows=2 ** 15)
+        if i >= args.warmup:
+            per_step.append(info["value"])
+    value = statistics.median(per_step)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "m": M, "n": N, "s": S, "kappa": KAPPA,
+                   "variant": "bcgsi+p-1s", "sample_rows": 2 ** 15},
+        "cpu_baseline": {"value": value, "unit": "GB/s", "cores": info["cores"], "kind": "oracle",
+                         "sample": info["sample"]},
+        "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.kernel:
+        main_kernel(a)
+    elif a.impl == "reference":
+        main_reference(a)
+    else:
+        main_ours(a)

@@ -48,30 +48,50 @@ def make_matrix_np(m: int, n: int, kappa: float, seed: int, row_scaled: bool = F
     return np.asfortranarray(x)
 
 
+def _orthonormalize_torch(g):
+    """Orthonormal factor of a tall Gaussian g on the device by Cholesky QR
+    applied twice (CholQR2); the n x n Cholesky factors and inverses are formed
+    on the host with numpy.  A tall Gaussian is well conditioned
+    (kappa ~ (1 + sqrt(n/m)) / (1 - sqrt(n/m))), so two passes leave
+    ||I - U^T U|| = O(u).  Only device matmuls are used, so the draw also works
+    where torch's device linear-algebra library cannot be loaded."""
+    import torch
+
+    u = g
+    for _ in range(2):
+        w = (u.T @ u).cpu().numpy()
+        L = np.linalg.cholesky(w)
+        rinv = np.linalg.inv(L.T)
+        u = u @ torch.as_tensor(rinv, dtype=u.dtype, device=u.device)
+    return u
+
+
 def make_matrix_torch(m: int, n: int, kappa: float, seed: int, device: str = "cuda",
                       row_scaled: bool = False):
     """Device draw of the same construction (torch generator on `device`).
 
-    Used for inputs too large to draw on the host in reasonable time.  Returns a
-    column-major float64 tensor (the transpose of a contiguous n x m tensor).
-    The device stream of random numbers differs from numpy's, so a matrix drawn
-    here is compared with the oracle by copying it to the host.
+    Used for inputs too large to draw on the host in reasonable time.  U is the
+    orthonormal factor of a seeded device Gaussian (CholQR2, see above), V the
+    Householder factor of a seeded host Gaussian.  Returns a column-major
+    float64 tensor (the transpose of a contiguous n x m tensor).  The device
+    stream of random numbers differs from numpy's, so a matrix drawn here is
+    compared with the oracle by copying it to the host.
     """
     import torch
 
     gen = torch.Generator(device=device)
     gen.manual_seed(seed)
     g = torch.randn(m, n, generator=gen, dtype=torch.float64, device=device)
-    u, _ = torch.linalg.qr(g)
+    u = _orthonormalize_torch(g)
     del g
-    gv = torch.randn(n, n, generator=gen, dtype=torch.float64, device=device)
-    v, _ = torch.linalg.qr(gv)
-    sig = torch.as_tensor(sigma_logspaced(n, kappa), dtype=torch.float64, device=device)
-    xt = (v * sig[None, :]) @ u.T  # n x m contiguous == column-major m x n
+    v = orthonormal_np(np.random.default_rng(seed), n, n)
+    sig = sigma_logspaced(n, kappa)
+    vs = torch.as_tensor(v * sig[None, :], dtype=torch.float64, device=device)
+    xt = vs @ u.T  # n x m contiguous == column-major m x n
     del u
     if row_scaled:
         z = torch.randn(m, generator=gen, dtype=torch.float64, device=device)
-        norms = torch.linalg.vector_norm(xt, dim=0)
+        norms = torch.sqrt((xt * xt).sum(dim=0))
         norms = torch.where(norms == 0, torch.ones_like(norms), norms)
         xt.mul_((torch.exp(2.0 * z) / norms)[None, :])
     return xt.T  # m x n view, stride (1, m)
