@@ -39,9 +39,12 @@ METRIC = "BCGSI+P-1S HBM GB/s & speedup vs BCGSI+ at equal loss-of-orth.; p99 la
 M, N, S, KAPPA = 2 ** 22, 256, 16, 1e5
 WORKLOAD = "single FP64 QR m=2^22 n=256 s=16 (q=16) BCGSI+P-1S, X=U diag(sigma) V^T kappa=1e5"
 FP64_PEAK_TFLOPS = 1.25  # GB300 FP64 rate of the profiling recipe's table (nominal)
-# DRAM traffic per launch of the dominant kernel from one ncu capture
-# (profiles/gram_partial_kernel.md); None until a capture of the current kernel exists.
-GRAM_TRAFFIC = None
+# DRAM traffic of the dominant kernel relative to its algorithmic bytes, from one
+# ncu capture of the current kernel (profiles/gram_partial_kernel_m524288_256x32.md:
+# (1.208285 GB + 3.823 MB) / (524288 * 288 * 8 B + 304 * 256 * 32 * 8 B)); traffic
+# grows with the rows processed, so a full launch moves this ratio times its
+# algorithmic bytes.  None once the kernel changes until it is captured again.
+GRAM_TRAFFIC_RATIO = (1.208285e9 + 3.823104e6) / (524288 * 288 * 8 + 304 * 256 * 32 * 8)
 ORACLE_SAMPLE_ROWS = 2 ** 17
 
 
@@ -290,7 +293,9 @@ def main_ours(args):
         "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
         "frac": achieved / FP64_PEAK_TFLOPS if achieved else None,
         "peak_source": "FP64 rate of the profiling recipe (nominal; a DFMA probe measured 1.20)",
-        "traffic": GRAM_TRAFFIC,
+        "traffic": GRAM_TRAFFIC_RATIO * gby / max(gl, 1) if GRAM_TRAFFIC_RATIO else None,
+        "traffic_note": "bytes per launch: ncu dram read+write / algorithmic bytes of a "
+                        "m=524288 capture, times this run's algorithmic bytes per launch",
         "launches": gl, "avg_launch_ms": gms / max(gl, 1),
         "share_of_timed_kernel_time": gms / step_ms_total if step_ms_total else None,
         "hbm_frac_of_measured_copy": value / 6669.5,
