@@ -173,6 +173,32 @@ BCGS_API int bcgs_gram(int64_t m, int32_t ka, int32_t kb, const double* A, int64
               const double* B, int64_t ldb, double* C, int32_t ldc,
               void* workspace, size_t ws_bytes, void* stream);
 
+/* Allocation-free C = A^T B.  The paper has no counterpart: this entry point
+ * exists for callers that can neither call cudaMalloc nor lend the library a
+ * workspace, such as a host framework that owns all device memory through its
+ * own pool (allocating behind its back fragments the pool, and cudaMalloc /
+ * cudaFree may synchronize the device) or a latency-bound loop that must never
+ * reach the allocator.  It computes the same result as bcgs_gram, with the
+ * same deterministic reduction order, but keeps the chunk partial sums in a
+ * fixed array of BCGS_GRAM_NOALLOC_MAX_PARTIALS doubles (8 MiB) compiled into
+ * the library; every GPU that loads the library holds that array until the
+ * process exits.  The caller still passes A, B and C.
+ *   Limit: the number of row chunks of m times ka * kb must not exceed
+ *   BCGS_GRAM_NOALLOC_MAX_PARTIALS.  The row chunk count is at most
+ *   min(304, ceil(m / 64)), so ka * kb <= 3449 always fits; larger requests
+ *   return BCGS_ERR_WORKSPACE and enqueue nothing.  ka * kb <= 65536 and the
+ *   argument rules of bcgs_gram apply (BCGS_ERR_INVALID_ARG otherwise).
+ *   Set-up: the first call on each device looks up the device address of the
+ *   array (once per device, with that device current), so make the first call
+ *   on a device before any stream capture begins.
+ *   Sharing: all calls use the same array.  Calls whose kernels may overlap on
+ *   the GPU (different streams, or host threads without ordering) race on it
+ *   and give wrong results; order them on one stream.
+ *   No cudaMalloc, cudaFree or allocating library routine is called. */
+#define BCGS_GRAM_NOALLOC_MAX_PARTIALS 1048576
+BCGS_API int bcgs_gram_noalloc(int64_t m, int32_t ka, int32_t kb, const double* A, int64_t lda,
+                               const double* B, int64_t ldb, double* C, int32_t ldc, void* stream);
+
 /* W = (V - Q C) T^{-1}: projection plus triangular-solve normalization (Alg. 1
  * and Alg. 2, the U and Q updates).  V, W: m x s; Q: m x c; C: c x s (device);
  * T: s x s upper triangular (device) or NULL for no normalization.  c may be 0

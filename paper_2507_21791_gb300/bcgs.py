@@ -57,6 +57,7 @@ SIGNATURES = [
     ("bcgs_tsqr_workspace_size", ctypes.c_int, [_i64, _i32, _psz]),
     ("bcgs_tsqr", ctypes.c_int, [_i64, _i32, _vp, _i64, _vp, _i64, _vp, _i32, _vp, _sz, _vp]),
     ("bcgs_chol", ctypes.c_int, [_i32, _vp, _i32, _vp, _i32, _vp, _sz, _vp]),
+    ("bcgs_gram_noalloc", ctypes.c_int, [_i64, _i32, _i32, _vp, _i64, _vp, _i64, _vp, _i32, _vp]),
     ("bcgs_launch_count", ctypes.c_int64, []),
     ("bcgs_profile_enable", ctypes.c_int, [ctypes.c_int]),
     ("bcgs_profile_reset", ctypes.c_int, []),
@@ -289,6 +290,22 @@ def gram(A, B, stream=None):
     _check(lib.bcgs_gram(m, ka, kb, A.data_ptr(), _colmajor_ld(A), B.data_ptr(), _colmajor_ld(B),
                          C.data_ptr(), _colmajor_ld(C), ws.data_ptr(), ws.numel(),
                          _stream_ptr(stream)), "bcgs_gram")
+    return C
+
+
+def gram_noalloc(A, B, C=None, stream=None):
+    """C = A^T B through bcgs_gram_noalloc (no device memory is allocated by the
+    library; C is allocated here unless given)."""
+    import torch
+
+    lib = load_library()
+    m, ka = A.shape
+    kb = B.shape[1]
+    if C is None:
+        C = empty_colmajor(ka, kb, torch.float64, A.device)
+    _check(lib.bcgs_gram_noalloc(m, ka, kb, A.data_ptr(), _colmajor_ld(A), B.data_ptr(),
+                                 _colmajor_ld(B), C.data_ptr(), _colmajor_ld(C),
+                                 _stream_ptr(stream)), "bcgs_gram_noalloc")
     return C
 
 
