@@ -61,6 +61,8 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--no-compare", action="store_true", help="skip timing BCGSI+ and -2S")
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    p.add_argument("--no-forms", action="store_true",
+                   help="skip the FP32-storage, batched and serving forms")
     p.add_argument("--kernel", default=None, choices=["gram", "project", "tsqr"],
                    help="time one building block alone (for profiling on small cases)")
     p.add_argument("--m", type=int, default=2 ** 19, help="rows for --kernel")
@@ -284,6 +286,13 @@ def main_ours(args):
     if "bcgsi+" in compare:
         speedup = {v: compare["bcgsi+"]["ms"] / compare[v]["ms"] for v in ("bcgsi+p-1s", "bcgsi+p-2s")}
 
+    forms = None
+    if not args.no_forms and world == 1:
+        del main["Q"], main["R"]
+        forms = {"fp32_storage": bench_fp32(args, dev, stream),
+                 "batched": bench_batched(args, dev, stream),
+                 "serving": bench_serving(args, dev)}
+
     prof = main["prof"]
     gl, gms, gfl, gby = prof["gram_partial"]
     achieved = gfl / (gms * 1e-3) / 1e12 if gms > 0 else None
@@ -320,10 +329,112 @@ def main_ours(args):
         "clocks": prof["clocks"],
         "kernel_time_ms_per_step": {k: prof[k][1] / args.steps for k in bcgs.PROFILE_CLASSES},
         "cpu_baseline": cpu,
+        "forms": forms,
+        "p99_latency_ms": (forms["serving"]["lambda_2000"]["call_latency_ms"]["p99"]
+                           if forms else None),
     }
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+# ------------------------------------------------------------------ forms
+
+def _timed(fn, warmup, steps, stream):
+    import torch
+
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def bench_fp32(args, dev, stream):
+    """Precision form: m = 2^24, n = 128, s = 32, BCGSI+P-1S, X and Q in FP32,
+    Gram / Cholesky / R in FP64; accuracy against the FP64 X."""
+    import numpy as np
+    import torch
+
+    from paper_2507_21791_gb300 import bcgs, synth
+
+    m, n, s, kappa = 2 ** 24, 128, 32, 1e4
+    X64 = synth.make_matrix_torch(m, n, kappa, seed=1200, device=str(dev))
+    X = X64.float()
+    Q = bcgs.empty_colmajor(m, n, torch.float32, dev)
+    R = bcgs.empty_colmajor(n, n, torch.float64, dev)
+    ws = torch.empty(bcgs.workspace_size(m, n, s, "bcgsi+p-1s", "fp32"), dtype=torch.uint8, device=dev)
+    ms = _timed(lambda: bcgs.factor_async(X, s, "bcgsi+p-1s", "fp32", Q, R, ws), args.warmup,
+                args.steps, stream)
+    code, blk = bcgs.factor_status(ws)
+    Qd = Q.double()
+    eye = torch.eye(n, dtype=torch.float64, device=dev)
+    loo = float(np.linalg.norm((eye - Qd.T @ Qd).cpu().numpy(), 2))
+    D = X64 - Qd @ R
+    res = math.sqrt((D * D).sum().item() / (X64 * X64).sum().item())
+    del D, Qd, X64
+    return {"workload": f"FP32 storage m=2^24 n=128 s=32 BCGSI+P-1S kappa={kappa:g}",
+            "value": alg_bytes_1s(m, n, s, b=4) / (ms * 1e-3) / 1e9, "unit": "GB/s",
+            "ms_per_step": ms, "status": bcgs.STATUS[code], "loo": loo,
+            "residual_vs_fp64_x": res, "bound": "FP64 ALU (products accumulated in FP64)"}
+
+
+def bench_batched(args, dev, stream):
+    """Batched form: 512 FP64 QRs, m = round(2^U(12,18)), n in {32, 64, 128},
+    kappa = 10^U(1,8), s picked by the autotuner from {4, 8, 16}; BCGSI+P-2S
+    (kappa up to 1e8 is outside BCGSI+P-1S's O(u) kappa^2 <= 1 range); the
+    batch is one CUDA-graph launch."""
+    import numpy as np
+    import torch
+
+    from paper_2507_21791_gb300 import synth
+    from paper_2507_21791_gb300.batched import Batch, BlockSizeTuner, alg_bytes
+
+    rng = np.random.default_rng(1300)
+    tuner = BlockSizeTuner(candidates=(4, 8, 16), variant="bcgsi+p-2s")
+    Xs, ss, total = [], [], 0.0
+    for i in range(512):
+        m = synth.log_uniform_int(rng, 12, 18)
+        n = int(rng.choice([32, 64, 128]))
+        kappa = 10.0 ** rng.uniform(1, 8)
+        Xs.append(synth.make_matrix_torch(m, n, kappa, seed=1300 + i, device=str(dev)))
+    for X in Xs:
+        m, n = X.shape
+        ss.append(tuner.pick(m, n, device=str(dev)))
+        total += alg_bytes(m, n, ss[-1], "bcgsi+p-2s")
+    b = Batch(Xs, ss, variant="bcgsi+p-2s")
+    b.capture()
+    ms = _timed(b.replay, args.warmup, args.steps, stream)
+    codes, _ = b.status()
+    return {"workload": "512 FP64 QRs m=2^U(12,18) n in {32,64,128} kappa=10^U(1,8) BCGSI+P-2S, "
+                        "one CUDA-graph launch", "value": total / (ms * 1e-3) / 1e9, "unit": "GB/s",
+            "instances_per_s": 512 / (ms * 1e-3), "ms_per_batch": ms,
+            "failed": sum(1 for c in codes if c != 0), "autotuned_s": tuner.table}
+
+
+def bench_serving(args, dev):
+    """Serving form: Poisson requests (Krylov-like bases: m = 2^U(14,20), q ~ U{4..32}
+    blocks of s in {4, 8, 16}, kappa up to 1e8), one block per call, Q and R
+    resident, admission against a 120 GB budget, BCGSI+P-2S."""
+    from paper_2507_21791_gb300.serving import GpuBackend, Server, draw_sources, make_requests
+
+    sources, meta = draw_sources(24, seed=1400, device=str(dev))
+    out = {}
+    for rate, window in ((2000.0, 4.0), (10.0, 4.0)):
+        be = GpuBackend(sources, variant="bcgsi+p-2s", nstreams=32, device=str(dev))
+        srv = Server(be, budget_bytes=120e9)
+        reqs = make_requests(rate, window, meta, seed=int(rate))
+        rep = srv.run(reqs, duration=window)
+        rep["offered_req_per_s"] = rate
+        rep["arrivals"] = len(reqs)
+        out[f"lambda_{int(rate)}"] = rep
+    return {"workload": "Poisson Krylov-basis requests, m=2^U(14,20), q~U{4..32}, s in {4,8,16}, "
+                        "120 GB budget, BCGSI+P-2S, pool of 24 pre-generated bases", **out}
 
 
 def main_kernel(args):

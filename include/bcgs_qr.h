@@ -152,8 +152,13 @@ typedef struct {
 /* Workspace for a batch (host array `probs` of `count` problems). */
 BCGS_API int bcgs_qr_batched_workspace_size(int32_t count, const bcgs_problem* probs, size_t* bytes);
 
-/* Enqueue all `count` factorizations on `stream`; statuses go to the
- * workspace, read them with bcgs_qr_batched_status. */
+/* Enqueue all `count` factorizations, ordered after the work already on
+ * `stream` and before anything enqueued on it later; statuses go to the
+ * workspace, read them with bcgs_qr_batched_status.  Problems run concurrently
+ * on 16 internal streams (created on the first call on a device and kept until
+ * exit) that fork from and join back into `stream`, so capturing `stream` into
+ * a CUDA graph captures the whole batch as one graph.  Each problem's result is
+ * the same as bcgs_qr_factor's for it alone (fixed reduction order). */
 BCGS_API int bcgs_qr_factor_batched(int32_t count, const bcgs_problem* probs, void* workspace,
                            size_t ws_bytes, void* stream);
 

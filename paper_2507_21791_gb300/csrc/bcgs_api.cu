@@ -7,6 +7,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <mutex>
 #include <new>
 
 #include "bcgs_internal.cuh"
@@ -359,6 +360,37 @@ int read_status(const void* ws, cudaStream_t stream, int32_t* code, int32_t* blo
   return BCGS_OK;
 }
 
+// Internal streams of the batched form, created on first use per device and
+// kept for the life of the process (streams and events only; no memory).
+constexpr int kBatchLanes = 16;
+struct BatchStreams {
+  cudaStream_t lane[kBatchLanes];
+  cudaEvent_t fork;
+  cudaEvent_t join[kBatchLanes];
+};
+std::mutex g_batch_mu;
+BatchStreams* g_batch[64] = {nullptr};
+
+int batch_streams(BatchStreams** out) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return BCGS_ERR_CUDA;
+  std::lock_guard<std::mutex> lk(g_batch_mu);
+  if (g_batch[dev] == nullptr) {
+    BatchStreams* bs = new (std::nothrow) BatchStreams;
+    if (bs == nullptr) return BCGS_ERR_INVALID_ARG;
+    for (int l = 0; l < kBatchLanes; ++l) {
+      if (cudaStreamCreateWithFlags(&bs->lane[l], cudaStreamNonBlocking) != cudaSuccess)
+        return BCGS_ERR_CUDA;
+      if (cudaEventCreateWithFlags(&bs->join[l], cudaEventDisableTiming) != cudaSuccess)
+        return BCGS_ERR_CUDA;
+    }
+    if (cudaEventCreateWithFlags(&bs->fork, cudaEventDisableTiming) != cudaSuccess) return BCGS_ERR_CUDA;
+    g_batch[dev] = bs;
+  }
+  *out = g_batch[dev];
+  return BCGS_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -565,8 +597,11 @@ int bcgs_chol(int32_t s, const double* A, int32_t lda, double* R, int32_t ldr, v
   return launch_chol(s, A, lda, R, ldr, 1, st, sm) == cudaSuccess ? BCGS_OK : BCGS_ERR_CUDA;
 }
 
-// Batched factorization: problems are enqueued one after another on the stream,
-// each in its own slice of the workspace (status words at the start).
+// Batched factorization: each problem gets its own slice of the workspace
+// (status words at the start) and its kernels run in order on one of 16
+// internal lanes forked from, and joined back into, the caller's stream, so
+// independent problems overlap on the GPU.  The whole call can be captured
+// into one CUDA graph by capturing the caller's stream.
 int bcgs_qr_batched_workspace_size(int32_t count, const bcgs_problem* probs, size_t* bytes) {
   if (count < 0 || bytes == nullptr || (count > 0 && probs == nullptr)) return BCGS_ERR_INVALID_ARG;
   size_t total = align256((size_t)count * sizeof(DevStatus));
@@ -588,23 +623,65 @@ int bcgs_qr_factor_batched(int32_t count, const bcgs_problem* probs, void* works
   if (rc != BCGS_OK) return rc;
   if (workspace == nullptr || ws_bytes < need || ((uintptr_t)workspace) % 256 != 0)
     return BCGS_ERR_WORKSPACE;
-  char* ws = reinterpret_cast<char*>(workspace);
+  cudaStream_t origin = reinterpret_cast<cudaStream_t>(stream);
+  BatchStreams* bs = nullptr;
+  rc = batch_streams(&bs);
+  if (rc != BCGS_OK) return rc;
+  // Fork: every lane waits for the work already queued on the caller's stream.
+  if (cudaEventRecord(bs->fork, origin) != cudaSuccess) return BCGS_ERR_CUDA;
+  for (int l = 0; l < kBatchLanes; ++l)
+    if (cudaStreamWaitEvent(bs->lane[l], bs->fork, 0) != cudaSuccess) return BCGS_ERR_CUDA;
+  // Problems go to lanes largest first (longest-processing-time order), each
+  // to the lane with the least work so far; each lane runs its problems in turn.
+  int* order = static_cast<int*>(malloc(sizeof(int) * (count > 0 ? count : 1)));
+  double* work = static_cast<double*>(malloc(sizeof(double) * (count > 0 ? count : 1)));
+  size_t* offs = static_cast<size_t*>(malloc(sizeof(size_t) * (count > 0 ? count : 1)));
+  if (!order || !work || !offs) {
+    free(order); free(work); free(offs);
+    return BCGS_ERR_INVALID_ARG;
+  }
   size_t off = align256((size_t)count * sizeof(DevStatus));
   for (int i = 0; i < count; ++i) {
+    order[i] = i;
+    work[i] = (double)probs[i].m * probs[i].n * probs[i].n;
+    offs[i] = off;
+    size_t b = 0;
+    bcgs_qr_workspace_size(probs[i].m, probs[i].n, probs[i].s, probs[i].variant, probs[i].precision, &b);
+    off += align256(b);
+  }
+  for (int i = 1; i < count; ++i) {  // insertion sort by decreasing work (stable)
+    int v = order[i], j = i - 1;
+    while (j >= 0 && work[order[j]] < work[v]) { order[j + 1] = order[j]; --j; }
+    order[j + 1] = v;
+  }
+  double load[kBatchLanes] = {0};
+  char* ws = reinterpret_cast<char*>(workspace);
+  rc = BCGS_OK;
+  for (int t = 0; t < count && rc == BCGS_OK; ++t) {
+    const int i = order[t];
+    int lane = 0;
+    for (int l = 1; l < kBatchLanes; ++l)
+      if (load[l] < load[lane]) lane = l;
+    load[lane] += work[i] + 1e7;  // + a per-problem launch cost
     const bcgs_problem& p = probs[i];
     size_t b = 0;
     bcgs_qr_workspace_size(p.m, p.n, p.s, p.variant, p.precision, &b);
+    cudaStream_t ls = bs->lane[lane];
     rc = bcgs_qr_factor(p.m, p.n, p.s, p.variant, p.precision, p.X, p.ldx, p.Q, p.ldq, p.R, p.ldr,
-                        ws + off, align256(b), stream);
-    if (rc != BCGS_OK) return rc;
-    // copy the problem's status word into the batch's status array once it is done
-    if (cudaMemcpyAsync(ws + (size_t)i * sizeof(DevStatus), ws + off, sizeof(DevStatus),
-                        cudaMemcpyDeviceToDevice,
-                        reinterpret_cast<cudaStream_t>(stream)) != cudaSuccess)
-      return BCGS_ERR_CUDA;
-    off += align256(b);
+                        ws + offs[i], align256(b), ls);
+    if (rc == BCGS_OK &&
+        cudaMemcpyAsync(ws + (size_t)i * sizeof(DevStatus), ws + offs[i], sizeof(DevStatus),
+                        cudaMemcpyDeviceToDevice, ls) != cudaSuccess)
+      rc = BCGS_ERR_CUDA;
   }
-  return BCGS_OK;
+  free(order); free(work); free(offs);
+  // Join: the caller's stream waits for every lane (also on failure, so that
+  // nothing enqueued so far is left unordered).
+  for (int l = 0; l < kBatchLanes; ++l) {
+    if (cudaEventRecord(bs->join[l], bs->lane[l]) != cudaSuccess) return BCGS_ERR_CUDA;
+    if (cudaStreamWaitEvent(origin, bs->join[l], 0) != cudaSuccess) return BCGS_ERR_CUDA;
+  }
+  return rc;
 }
 
 int bcgs_qr_batched_status(int32_t count, const void* workspace, void* stream, int32_t* codes,

@@ -52,6 +52,14 @@ struct GramDesc {
 inline int64_t round_up(int64_t v, int64_t a) { return (v + a - 1) / a * a; }
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
+// cudaFuncSetAttribute(MaxDynamicSharedMemorySize) only when `bytes` exceeds what
+// was already set for this kernel (keyed by its address) on the current device.
+cudaError_t ensure_dyn_smem_ptr(const void* kernel, size_t bytes);
+template <typename Kernel>
+inline cudaError_t ensure_dyn_smem(Kernel kern, size_t bytes) {
+  return ensure_dyn_smem_ptr(reinterpret_cast<const void*>(kern), bytes);
+}
+
 // Deterministic row partition of the Gram reduction: depends on m only.
 void gram_partition(int64_t m, int64_t* chunk_rows, int32_t* nchunks);
 size_t gram_partial_doubles(int64_t m, int32_t na, int32_t nb);

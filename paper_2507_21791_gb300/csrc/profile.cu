@@ -44,6 +44,34 @@ cudaEvent_t get_event() {
 
 void note_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
+namespace {
+struct SmemEntry {
+  const void* kernel;
+  int dev;
+  size_t bytes;
+};
+std::mutex g_smem_mu;
+std::vector<SmemEntry> g_smem;
+}  // namespace
+
+cudaError_t ensure_dyn_smem_ptr(const void* kernel, size_t bytes) {
+  if (bytes <= 48 * 1024) return cudaSuccess;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) dev = -1;
+  std::lock_guard<std::mutex> lk(g_smem_mu);
+  for (auto& e : g_smem)
+    if (e.kernel == kernel && e.dev == dev && e.bytes >= bytes) return cudaSuccess;
+  cudaError_t err = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (err != cudaSuccess) return err;
+  for (auto& e : g_smem)
+    if (e.kernel == kernel && e.dev == dev) {
+      e.bytes = bytes;
+      return cudaSuccess;
+    }
+  g_smem.push_back({kernel, dev, bytes});
+  return cudaSuccess;
+}
+
 int prof_begin(cudaStream_t stream) {
   if (!g_enabled.load(std::memory_order_relaxed)) return -1;
   std::lock_guard<std::mutex> lk(g_mu);

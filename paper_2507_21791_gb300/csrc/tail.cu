@@ -256,7 +256,7 @@ __global__ void reset_status_kernel(DevStatus* st) {
 cudaError_t launch_tail_1s2s(const TailDesc& d, DevStatus* st, cudaStream_t stream) {
   if (d.s > kMaxS) return cudaErrorInvalidValue;
   const size_t smem = 4 * (size_t)d.s * d.s * sizeof(double);
-  cudaError_t e = cudaFuncSetAttribute(tail_1s2s_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = ensure_dyn_smem(tail_1s2s_kernel, (size_t)(smem));
   if (e != cudaSuccess) return e;
   const int slot = prof_begin(stream);
   tail_1s2s_kernel<<<1, kTailThreads, smem, stream>>>(d, st);
@@ -269,7 +269,7 @@ cudaError_t launch_tail_start_1s(int32_t s, const double* G, int32_t ldg, double
                                  double* Sd, int32_t block, DevStatus* st, cudaStream_t stream) {
   if (s > kMaxS) return cudaErrorInvalidValue;
   const size_t smem = 2 * (size_t)s * s * sizeof(double);
-  cudaError_t e = cudaFuncSetAttribute(tail_start_1s_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = ensure_dyn_smem(tail_start_1s_kernel, (size_t)(smem));
   if (e != cudaSuccess) return e;
   tail_start_1s_kernel<<<1, kTailThreads, smem, stream>>>(s, G, ldg, S, ldsm, Sd, block, st);
   note_launch(1);
@@ -297,7 +297,7 @@ cudaError_t launch_chol(int32_t s, const double* A, int32_t lda, double* R, int3
                         int32_t block, DevStatus* st, cudaStream_t stream) {
   if (s > kMaxS) return cudaErrorInvalidValue;
   const size_t smem = 2 * (size_t)s * s * sizeof(double);
-  cudaError_t e = cudaFuncSetAttribute(chol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = ensure_dyn_smem(chol_kernel, (size_t)(smem));
   if (e != cudaSuccess) return e;
   chol_kernel<<<1, kTailThreads, smem, stream>>>(s, A, lda, R, ldr, block, st);
   note_launch(1);

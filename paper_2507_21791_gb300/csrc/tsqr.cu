@@ -251,13 +251,13 @@ cudaError_t launch_tsqr_t(const TsqrPlan& p, Seg a, void* q, int64_t ldq, double
   const size_t leaf_f = (size_t)p.mt * p.s * sizeof(double);
   const size_t node_f = (size_t)p.fan * p.s * p.s * sizeof(double);
   cudaError_t e;
-  e = cudaFuncSetAttribute(tsqr_leaf_factor<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)leaf_f);
+  e = ensure_dyn_smem(tsqr_leaf_factor<T>, (size_t)(leaf_f));
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(tsqr_leaf_apply<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(2 * leaf_f));
+  e = ensure_dyn_smem(tsqr_leaf_apply<T>, (size_t)(2 * leaf_f));
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(tsqr_node_factor, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)node_f);
+  e = ensure_dyn_smem(tsqr_node_factor, (size_t)(node_f));
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(tsqr_node_apply, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(2 * node_f));
+  e = ensure_dyn_smem(tsqr_node_apply, (size_t)(2 * node_f));
   if (e != cudaSuccess) return e;
   const int slot = prof_begin(stream);
   tsqr_leaf_factor<T><<<p.nodes[0], kTsqrThreads, leaf_f, stream>>>(p, a, work, R, ldr, st, block);

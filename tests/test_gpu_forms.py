@@ -1,0 +1,101 @@
+"""The batched and served forms on the GPU.
+
+Batched: one bcgs_qr_factor_batched call (and its CUDA-graph replay) over uneven
+problems gives, for every problem, the same bits as bcgs_qr_factor alone and
+meets the FP64 gates.  Served: each basis's Q and R are the same alone and in
+the mix (bitwise: the reduction order depends only on the problem's shape),
+and every admitted request meets the gates.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2507_21791_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def test_batched_matches_single_and_graph_replay(cuda):
+    import torch
+
+    from paper_2507_21791_gb300.batched import Batch
+
+    rng = np.random.default_rng(3)
+    Xs, ss, Xh = [], [], []
+    for i in range(12):
+        m = int(2 ** rng.uniform(12, 15))
+        n = int(rng.choice([32, 64]))
+        s = int(rng.choice([4, 8, 16]))
+        X = synth.make_matrix_np(m, n, 10 ** rng.uniform(1, 6), seed=100 + i)
+        Xh.append(X)
+        Xs.append(cuda.to_device_colmajor(X))
+        ss.append(s)
+    b = Batch(Xs, ss, variant="bcgsi+p-2s")
+    b.enqueue()
+    codes, _ = b.status()
+    assert codes == [0] * len(Xs)
+    first = [(q.clone(), r.clone()) for q, r in zip(b.Qs, b.Rs)]
+    for i, (X, s) in enumerate(zip(Xs, ss)):
+        Q, R, code, _ = cuda.factor(X, s, "bcgsi+p-2s")
+        assert code == 0
+        assert torch.equal(Q, b.Qs[i]) and torch.equal(R, b.Rs[i])
+        Qh, Rh = Q.cpu().numpy(), R.cpu().numpy()
+        assert oracle.loo(Qh) <= 1e-12 and oracle.residual(Xh[i], Qh, Rh) <= 1e-13
+    for q in b.Qs:
+        q.zero_()
+    b.capture()
+    b.replay()
+    torch.cuda.synchronize()
+    codes, _ = b.status()
+    assert codes == [0] * len(Xs)
+    for (q0, r0), q, r in zip(first, b.Qs, b.Rs):
+        assert torch.equal(q0, q) and torch.equal(r0, r)
+
+
+def _serve(cuda, sources, meta, rids, arrivals, budget=8e9):
+    from paper_2507_21791_gb300.serving import GpuBackend, Request, Server
+
+    be = GpuBackend(sources, variant="bcgsi+p-2s", nstreams=8)
+    srv = Server(be, budget_bytes=budget)
+    reqs = [Request(rid=r, arrival=a, m=meta[r][0], n=meta[r][1], s=meta[r][2], source=r)
+            for r, a in zip(rids, arrivals)]
+    rep = srv.run(reqs, duration=120.0)
+    return {r.rid: r for r in srv.done}, rep
+
+
+def test_served_results_are_the_same_alone_and_in_the_mix(cuda):
+    import torch
+
+    from paper_2507_21791_gb300.serving import draw_sources
+
+    sources, meta = draw_sources(10, seed=5, m_exp=(12, 15), p_range=(2, 6))
+    targets = [0, 3, 7]
+    alone = {}
+    for r in targets:
+        done, rep = _serve(cuda, sources, meta, [r], [0.0])
+        assert rep["failed"] == 0
+        alone[r] = done[r].result
+    done, rep = _serve(cuda, sources, meta, list(range(10)), [0.0] * 10)
+    assert rep["requests_done"] == 10 and rep["failed"] == 0 and rep["max_active"] > 1
+    for r in targets:
+        Qa, Ra = alone[r]
+        Qm, Rm = done[r].result
+        assert torch.equal(Qa, Qm) and torch.equal(Ra, Rm)
+    for r, req in done.items():
+        m, n, s = meta[r]
+        X = sources[r][:m, :n].cpu().numpy()
+        Q, R = req.result[0].cpu().numpy(), req.result[1].cpu().numpy()
+        assert oracle.loo(Q) <= 1e-12 and oracle.residual(X, Q, R) <= 1e-13
+
+
+def test_server_respects_the_budget(cuda):
+    from paper_2507_21791_gb300.serving import draw_sources
+
+    sources, meta = draw_sources(8, seed=6, m_exp=(13, 15), p_range=(2, 4))
+    from paper_2507_21791_gb300.serving import GpuBackend
+
+    be = GpuBackend(sources, variant="bcgsi+p-2s")
+    per = max(be.bytes_for(type("R", (), {"m": m, "n": n, "s": s})) for m, n, s in meta)
+    done, rep = _serve(cuda, sources, meta, list(range(8)), [0.0] * 8, budget=2.2 * per)
+    assert rep["requests_done"] == 8
+    assert rep["peak_reserved_gb"] * 1e9 <= 2.2 * per

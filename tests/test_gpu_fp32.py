@@ -1,0 +1,68 @@
+"""The FP32-storage form: X, Q and U stored and streamed in FP32, every inner
+product accumulated and every small factor computed in FP64.
+
+The paper does not analyse mixed precision; the stated per-config bounds are
+derived from the storage unit roundoff u32 = 2^-24 ~ 6e-8 (Q itself is rounded to
+FP32, so ||I - Q^T Q|| cannot be below ~u32):
+    ||I - Q^T Q||_2 <= 1e-6,  ||X - Q R||_F / ||X||_F <= 1e-6  (against the FP64 X)
+for kappa <= 1e4, and for BCGSI+ and BCGSI+P-2S also at kappa = 1e6.  R is formed
+in FP64 from FP64 Gram entries, so it stays close to the FP64 oracle's R:
+    ||R - R_oracle||_F / ||R_oracle||_F <= 10 n u32.
+BCGSI+P-1S needs O(u) kappa^2 <= 1 (Table 1); with u = u32 that is kappa << 4e3,
+and at kappa = 1e6 its Pythagorean Cholesky breaks down, which is reported as a
+status, not as a wrong result.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2507_21791_gb300 import synth
+
+U32 = 2.0 ** -24
+VARIANTS = ["bcgsi+", "bcgsi+p-1s", "bcgsi+p-2s"]
+pytestmark = pytest.mark.gpu
+
+
+def run_fp32(cuda, X, s, variant):
+    import torch
+
+    Xf = cuda.to_device_colmajor(X, dtype=torch.float32)
+    Q, R, code, blk = cuda.factor(Xf, s, variant)
+    assert Q.dtype == torch.float32 and R.dtype == torch.float64
+    return Q.double().cpu().numpy(), R.cpu().numpy(), code, blk
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+@pytest.mark.parametrize("kappa", [1e2, 1e4, 1e6])
+def test_fp32_storage_accuracy(cuda, variant, kappa):
+    m, n, s = 2 ** 16, 64, 8
+    X = synth.make_matrix_np(m, n, kappa, seed=7)
+    Q, R, code, blk = run_fp32(cuda, X, s, variant)
+    if variant == "bcgsi+p-1s" and kappa >= 1e6:
+        assert cuda.STATUS[code] == "not_spd" and blk >= 2
+        return
+    assert code == 0
+    assert oracle.loo(Q) <= 1e-6
+    assert oracle.residual(X, Q, R) <= 1e-6
+    _, Ro = oracle.factor(X, s, variant)
+    assert np.linalg.norm(R - Ro) / np.linalg.norm(Ro) <= 10 * n * U32
+    assert np.all(np.diag(R) > 0)
+
+
+def test_fp32_storage_block_size_32(cuda):
+    """The precision-form shape (s = 32) at reduced m."""
+    m, n, s = 2 ** 18, 128, 32
+    X = synth.make_matrix_np(m, n, 1e4, seed=8)
+    Q, R, code, _ = run_fp32(cuda, X, s, "bcgsi+p-1s")
+    assert code == 0
+    assert oracle.loo(Q) <= 1e-6 and oracle.residual(X, Q, R) <= 1e-6
+
+
+def test_fp32_storage_is_deterministic(cuda):
+    import torch
+
+    X = synth.make_matrix_np(30000, 48, 1e3, seed=9)
+    Xf = cuda.to_device_colmajor(X, dtype=torch.float32)
+    a = cuda.factor(Xf, 8, "bcgsi+p-1s")
+    b = cuda.factor(Xf, 8, "bcgsi+p-1s")
+    assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])
