@@ -66,6 +66,8 @@ def parse():
     p.add_argument("--kernel", default=None, choices=["gram", "project", "tsqr"],
                    help="time one building block alone (for profiling on small cases)")
     p.add_argument("--m", type=int, default=2 ** 19, help="rows for --kernel")
+    p.add_argument("--engine", default="auto", choices=["auto", "fp64", "tensor"],
+                   help="Gram engine (bcgs_set_option)")
     return p.parse_args()
 
 
@@ -451,6 +453,7 @@ def main_kernel(args):
     from paper_2507_21791_gb300 import bcgs, synth
 
     bcgs.load_library()
+    bcgs.set_gram_engine(args.engine)
     m = args.m
     g = torch.Generator(device="cuda")
     g.manual_seed(7)
@@ -478,7 +481,8 @@ def main_kernel(args):
     cls = {"gram": "gram_partial", "project": "project", "tsqr": "tsqr"}[args.kernel]
     n, ms, fl, by = bcgs.profile_read(cls)
     bcgs.profile_enable(False)
-    print(json.dumps({"kernel": args.kernel, "m": m, "launches": n, "avg_ms": ms / max(n, 1),
+    print(json.dumps({"kernel": args.kernel, "m": m, "engine": bcgs.get_gram_engine(),
+                      "launches": n, "avg_ms": ms / max(n, 1),
                       "tflops": fl / (ms * 1e-3) / 1e12, "alg_gbs": by / (ms * 1e-3) / 1e9}))
 
 

@@ -185,9 +185,11 @@ BCGS_API int bcgs_gram(int64_t m, int32_t ka, int32_t kb, const double* A, int64
  * cudaFree may synchronize the device) or a latency-bound loop that must never
  * reach the allocator.  It computes the same result as bcgs_gram, with the
  * same deterministic reduction order, but keeps the chunk partial sums in a
- * fixed array of BCGS_GRAM_NOALLOC_MAX_PARTIALS doubles (8 MiB) compiled into
- * the library; every GPU that loads the library holds that array until the
- * process exits.  The caller still passes A, B and C.
+ * fixed array compiled into the library: BCGS_GRAM_NOALLOC_MAX_PARTIALS doubles
+ * (8 MiB) of partials plus 65536 words of column maxima for the tensor-core
+ * engine (BCGS_OPT_GRAM_ENGINE picks the engine as for bcgs_gram); every GPU
+ * that loads the library holds that array until the process exits.  The
+ * caller still passes A, B and C.
  *   Limit: the number of row chunks of m times ka * kb must not exceed
  *   BCGS_GRAM_NOALLOC_MAX_PARTIALS.  The row chunk count is at most
  *   min(304, ceil(m / 64)), so ka * kb <= 3449 always fits; larger requests
@@ -227,6 +229,29 @@ BCGS_API int bcgs_tsqr(int64_t m, int32_t s, const double* A, int64_t lda, doubl
  * BCGS_ERR_NOT_SPD in the workspace status word.  workspace >= 256 bytes. */
 BCGS_API int bcgs_chol(int32_t s, const double* A, int32_t lda, double* R, int32_t ldr,
               void* workspace, size_t ws_bytes, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Options (process-wide, host side).
+ *
+ * BCGS_OPT_GRAM_ENGINE selects how the synchronization's inner products are
+ * computed:
+ *   0  the FP64 pipe (DFMA, chunked fixed-order sums);
+ *   1  (default) tensor cores when the call has at least BCGS_OPT_TC_MIN_ROWS
+ *      rows and at most 64 columns on the right: each FP64 (or FP32) operand
+ *      is split exactly into nine 7-bit integer digits relative to its
+ *      column's maximum, digit pairs are multiplied on the bf16 tensor cores
+ *      with exact integer sums, and one FP64 rounding per row chunk remains
+ *      (error per product term <= 2^-57.5 max|a_i| max|b_j|);
+ *   2  tensor cores whenever the shape allows it.
+ * BCGS_OPT_TC_MIN_ROWS is the row threshold of engine 1 (default 16384).
+ * Both engines use the same row partition, so each is deterministic; they
+ * differ by rounding.  Returns BCGS_ERR_INVALID_ARG for an unknown option or
+ * value.
+ * ------------------------------------------------------------------------- */
+#define BCGS_OPT_GRAM_ENGINE 1
+#define BCGS_OPT_TC_MIN_ROWS 2
+BCGS_API int bcgs_set_option(int option, int64_t value);
+BCGS_API int64_t bcgs_get_option(int option);
 
 /* ---------------------------------------------------------------------------
  * Instrumentation (host side; no device memory).

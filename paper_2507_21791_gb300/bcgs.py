@@ -58,6 +58,8 @@ SIGNATURES = [
     ("bcgs_tsqr", ctypes.c_int, [_i64, _i32, _vp, _i64, _vp, _i64, _vp, _i32, _vp, _sz, _vp]),
     ("bcgs_chol", ctypes.c_int, [_i32, _vp, _i32, _vp, _i32, _vp, _sz, _vp]),
     ("bcgs_gram_noalloc", ctypes.c_int, [_i64, _i32, _i32, _vp, _i64, _vp, _i64, _vp, _i32, _vp]),
+    ("bcgs_set_option", ctypes.c_int, [ctypes.c_int, ctypes.c_int64]),
+    ("bcgs_get_option", ctypes.c_int64, [ctypes.c_int]),
     ("bcgs_launch_count", ctypes.c_int64, []),
     ("bcgs_profile_enable", ctypes.c_int, [ctypes.c_int]),
     ("bcgs_profile_reset", ctypes.c_int, []),
@@ -360,6 +362,24 @@ def chol(A, stream=None):
     blk = ctypes.c_int32(0)
     code = lib.bcgs_qr_factor_status(ws.data_ptr(), sp, ctypes.byref(blk))
     return R, code
+
+
+OPT_GRAM_ENGINE, OPT_TC_MIN_ROWS = 1, 2
+ENGINES = {"fp64": 0, "auto": 1, "tensor": 2}
+
+
+def set_gram_engine(engine: str = "auto", min_rows: int | None = None):
+    """Choose the Gram engine: "fp64" (FP64 pipe), "auto" (tensor cores for
+    large shapes, the default) or "tensor" (whenever the shape allows)."""
+    lib = load_library()
+    _check(lib.bcgs_set_option(OPT_GRAM_ENGINE, ENGINES[engine]), "bcgs_set_option")
+    if min_rows is not None:
+        _check(lib.bcgs_set_option(OPT_TC_MIN_ROWS, int(min_rows)), "bcgs_set_option")
+
+
+def get_gram_engine() -> str:
+    v = load_library().bcgs_get_option(OPT_GRAM_ENGINE)
+    return {0: "fp64", 1: "auto", 2: "tensor"}[int(v)]
 
 
 def launch_count() -> int:

@@ -7,6 +7,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <atomic>
 #include <mutex>
 #include <new>
 
@@ -20,7 +21,7 @@ constexpr int kMaxS = 64;
 constexpr int kMaxN = 2048;
 
 struct Layout {
-  size_t status, S[2], Sd[2], Yd, Rt1, Rt2, G, G2, partial, U, V, tsqr, total;
+  size_t status, S[2], Sd[2], Yd, Rt1, Rt2, G, G2, partial, amax, U, V, tsqr, total;
   int ldg;      // leading dimension of G, G2 (= n_max)
   int64_t ldu;  // leading dimension of U, V
   TsqrPlan tp;
@@ -51,6 +52,7 @@ void make_layout(int64_t m, int32_t n_max, int32_t s, int variant, int precision
   L->G = take((size_t)n_max * 2 * s * sizeof(double));
   L->G2 = take((size_t)n_max * 2 * s * sizeof(double));
   L->partial = take(gram_partial_doubles(m, n_max, 2 * s) * sizeof(double));
+  L->amax = take(((size_t)n_max + 4 * (size_t)s) * sizeof(unsigned long long));
   L->ldu = round_up(m, 64);
   L->U = take((size_t)L->ldu * s * esz);
   L->V = variant == BCGS_BCGSI_PLUS_P_1S ? off : take((size_t)L->ldu * s * esz);
@@ -69,6 +71,20 @@ Seg seg(const void* p, int64_t ld, int ncols, int fp32) {
 }
 
 }  // namespace
+
+namespace bcgs {
+namespace {
+std::atomic<int> g_engine{1};
+std::atomic<long long> g_tc_min_rows{16384};
+}  // namespace
+int gram_engine() { return g_engine.load(); }
+int64_t gram_tc_min_rows() { return g_tc_min_rows.load(); }
+bool use_tensor_gram(const GramDesc& d) {
+  const int e = gram_engine();
+  if (e == 0 || !gram_tc_supported(d)) return false;
+  return e == 2 || d.m >= gram_tc_min_rows();
+}
+}  // namespace bcgs
 
 struct bcgs_qr_s {
   int64_t m;
@@ -134,7 +150,11 @@ cudaError_t gram(bcgs_qr_s* h, std::initializer_list<Seg> A, std::initializer_li
     d.nb += b.ncols;
   }
   d.m = h->m;
+  d.block = h->j + 1;
   gram_partition(h->m, &d.chunk_rows, &d.nchunks);
+  if (use_tensor_gram(d))
+    return launch_gram_tc(d, h->buf(h->L.partial), G, h->L.ldg,
+                          reinterpret_cast<unsigned long long*>(h->ws + h->L.amax), h->st(), h->stream);
   return launch_gram(d, h->buf(h->L.partial), G, h->L.ldg, h->st(), h->stream);
 }
 
@@ -412,6 +432,28 @@ const char* bcgs_status_string(int status) {
 
 int bcgs_version(void) { return 100; }
 
+int bcgs_set_option(int option, int64_t value) {
+  switch (option) {
+    case BCGS_OPT_GRAM_ENGINE:
+      if (value < 0 || value > 2) return BCGS_ERR_INVALID_ARG;
+      g_engine.store((int)value);
+      return BCGS_OK;
+    case BCGS_OPT_TC_MIN_ROWS:
+      if (value < 1) return BCGS_ERR_INVALID_ARG;
+      g_tc_min_rows.store(value);
+      return BCGS_OK;
+  }
+  return BCGS_ERR_INVALID_ARG;
+}
+
+int64_t bcgs_get_option(int option) {
+  switch (option) {
+    case BCGS_OPT_GRAM_ENGINE: return g_engine.load();
+    case BCGS_OPT_TC_MIN_ROWS: return g_tc_min_rows.load();
+  }
+  return -1;
+}
+
 int bcgs_qr_workspace_size(int64_t m, int32_t n_max, int32_t s, int variant, int precision,
                            size_t* bytes) {
   if (bytes == nullptr || !valid_shape(m, n_max, s)) return BCGS_ERR_INVALID_ARG;
@@ -506,7 +548,8 @@ int bcgs_qr_destroy(bcgs_qr_t h) {
 int bcgs_gram_workspace_size(int64_t m, int32_t ka, int32_t kb, size_t* bytes) {
   if (bytes == nullptr || m < 1 || ka < 1 || kb < 1 || (int64_t)ka * kb > 65536)
     return BCGS_ERR_INVALID_ARG;
-  *bytes = align256(sizeof(DevStatus)) + gram_partial_doubles(m, ka, kb) * sizeof(double);
+  *bytes = align256(sizeof(DevStatus)) + align256(gram_partial_doubles(m, ka, kb) * sizeof(double)) +
+           ((size_t)ka + kb) * sizeof(unsigned long long);
   return BCGS_OK;
 }
 
@@ -529,10 +572,16 @@ int bcgs_gram(int64_t m, int32_t ka, int32_t kb, const double* A, int64_t lda, c
   d.nb = kb;
   d.m = m;
   gram_partition(m, &d.chunk_rows, &d.nchunks);
-  if (launch_gram(d, reinterpret_cast<double*>(ws + align256(sizeof(DevStatus))), C, ldc, st, sm) !=
-      cudaSuccess)
-    return BCGS_ERR_CUDA;
-  return BCGS_OK;
+  double* partial = reinterpret_cast<double*>(ws + align256(sizeof(DevStatus)));
+  cudaError_t e;
+  if (use_tensor_gram(d)) {
+    auto* amax = reinterpret_cast<unsigned long long*>(
+        ws + align256(sizeof(DevStatus)) + align256(gram_partial_doubles(m, ka, kb) * sizeof(double)));
+    e = launch_gram_tc(d, partial, C, ldc, amax, st, sm);
+  } else {
+    e = launch_gram(d, partial, C, ldc, st, sm);
+  }
+  return e == cudaSuccess ? BCGS_OK : BCGS_ERR_CUDA;
 }
 
 int bcgs_project(int64_t m, int32_t c, int32_t s, const double* V, int64_t ldv, const double* Q,

@@ -23,7 +23,18 @@ __device__ __forceinline__ bool failed(const DevStatus* st) {
   return st != nullptr && *((volatile const int32_t*)&st->code) != 0;
 }
 __device__ __forceinline__ void set_failure(DevStatus* st, int code, int block) {
-  if (atomicCAS(&st->code, 0, code) == 0) st->block = block;
+  if (st != nullptr && atomicCAS(&st->code, 0, code) == 0) st->block = block;
+}
+// The same answer for every thread of the CTA (thread 0 reads, then a barrier).
+// Needed in kernels whose own CTAs may set a failure while others start: a
+// per-thread read could then send part of a CTA home before a barrier.
+__device__ __forceinline__ bool block_failed(const DevStatus* st) {
+  __shared__ int s_failed;
+  if (threadIdx.x == 0) s_failed = failed(st) ? 1 : 0;
+  __syncthreads();
+  const bool f = s_failed != 0;
+  __syncthreads();
+  return f;
 }
 
 // ---------------------------------------------------------------- operands
@@ -47,6 +58,7 @@ struct GramDesc {
   int64_t m;
   int64_t chunk_rows; // rows per partial-sum chunk (fixed by m)
   int32_t nchunks;
+  int32_t block;      // 1-based block column reported with a failure (0 = none)
 };
 
 inline int64_t round_up(int64_t v, int64_t a) { return (v + a - 1) / a * a; }
@@ -67,6 +79,18 @@ size_t gram_partial_doubles(int64_t m, int32_t na, int32_t nb);
 // Launchers (return cudaError_t of the launch).
 cudaError_t launch_gram(const GramDesc& d, double* partial, double* G, int ldg,
                         DevStatus* st, cudaStream_t stream);
+// Chunk partials -> G, added in chunk order.
+cudaError_t launch_gram_reduce(const double* partial, int32_t nchunks, int32_t na, int32_t nb,
+                               double* G, int32_t ldg, const DevStatus* st, cudaStream_t stream);
+// Tensor-core Gram (gram_tc.cu): same partition and partial layout; needs
+// na + nb unsigned 64-bit words of scratch for the column maxima; nb <= 64.
+bool gram_tc_supported(const GramDesc& d);
+cudaError_t launch_gram_tc(const GramDesc& d, double* partial, double* G, int ldg,
+                           unsigned long long* amax, DevStatus* st, cudaStream_t stream);
+// Library-wide choice of the Gram engine (bcgs_set_option).
+int gram_engine();       // 0 FP64 pipe only, 1 tensor cores for large shapes (default), 2 always
+int64_t gram_tc_min_rows();
+bool use_tensor_gram(const GramDesc& d);
 
 // W = (V - Qseg C) T^{-1}; C (c x s, ldc) and T (s x s, ldt) on device; T may be null.
 struct ProjDesc {

@@ -156,17 +156,23 @@ cudaError_t launch_gram_t(const GramDesc& d, double* partial, double* G, int ldg
            (double)d.m * (d.na + d.nb) * esz + (double)d.nchunks * d.na * d.nb * 8.0);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const int nout_all = d.na * d.nb;
-  const int slot2 = prof_begin(stream);
-  gram_reduce_kernel<<<(nout_all + 255) / 256, 256, 0, stream>>>(partial, d.nchunks, d.na, d.nb, G,
-                                                                  ldg, st);
-  prof_end(slot2, kProfGramReduce, stream, (double)d.nchunks * nout_all,
-           (double)d.nchunks * nout_all * 8.0 + nout_all * 8.0);
-  note_launch(2);
-  return cudaGetLastError();
+  note_launch(1);
+  return launch_gram_reduce(partial, d.nchunks, d.na, d.nb, G, ldg, st, stream);
 }
 
 }  // namespace
+
+cudaError_t launch_gram_reduce(const double* partial, int32_t nchunks, int32_t na, int32_t nb,
+                               double* G, int32_t ldg, const DevStatus* st, cudaStream_t stream) {
+  const int nout_all = na * nb;
+  const int slot2 = prof_begin(stream);
+  gram_reduce_kernel<<<(nout_all + 255) / 256, 256, 0, stream>>>(partial, nchunks, na, nb, G, ldg,
+                                                                  st);
+  prof_end(slot2, kProfGramReduce, stream, (double)nchunks * nout_all,
+           (double)nchunks * nout_all * 8.0 + nout_all * 8.0);
+  note_launch(1);
+  return cudaGetLastError();
+}
 
 void gram_partition(int64_t m, int64_t* chunk_rows, int32_t* nchunks) {
   // About two chunks per SM of a 152-SM GB300 for large m; at least 64 rows each.

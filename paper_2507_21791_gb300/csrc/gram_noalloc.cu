@@ -19,10 +19,13 @@
 namespace bcgs {
 namespace {
 
-// Capacity of the partial-sum array in doubles: 2^20 doubles = 8 MiB.
+// The array: 2^20 doubles (8 MiB) of chunk partials, then 65544 words for the
+// column maxima of the tensor-core engine (ka * kb <= 65536 implies
+// ka + kb <= 65537).
 constexpr size_t kNoAllocPartials = BCGS_GRAM_NOALLOC_MAX_PARTIALS;
+constexpr size_t kNoAllocAmax = 65544;
 
-static __device__ __align__(256) double g_gram_partials[kNoAllocPartials];
+static __device__ __align__(256) double g_gram_partials[kNoAllocPartials + kNoAllocAmax];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_setup_mu;
@@ -74,10 +77,14 @@ extern "C" int bcgs_gram_noalloc(int64_t m, int32_t ka, int32_t kb, const double
   double* partials = nullptr;
   const int rc = partials_on_current_device(&partials);
   if (rc != BCGS_OK) return rc;
-  // No status word: nothing in the Gram path records a failure, and a null
-  // status pointer makes the kernels skip the check.
-  if (launch_gram(d, partials, C, ldc, nullptr, reinterpret_cast<cudaStream_t>(stream)) !=
-      cudaSuccess)
-    return BCGS_ERR_CUDA;
-  return BCGS_OK;
+  // No status word: a null status pointer makes the kernels skip the check
+  // (the tensor-core engine then writes no partials for a non-finite column).
+  cudaError_t e;
+  if (use_tensor_gram(d)) {
+    auto* amax = reinterpret_cast<unsigned long long*>(partials + kNoAllocPartials);
+    e = launch_gram_tc(d, partials, C, ldc, amax, nullptr, reinterpret_cast<cudaStream_t>(stream));
+  } else {
+    e = launch_gram(d, partials, C, ldc, nullptr, reinterpret_cast<cudaStream_t>(stream));
+  }
+  return e == cudaSuccess ? BCGS_OK : BCGS_ERR_CUDA;
 }
