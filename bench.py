@@ -39,12 +39,28 @@ METRIC = "BCGSI+P-1S HBM GB/s & speedup vs BCGSI+ at equal loss-of-orth.; p99 la
 M, N, S, KAPPA = 2 ** 22, 256, 16, 1e5
 WORKLOAD = "single FP64 QR m=2^22 n=256 s=16 (q=16) BCGSI+P-1S, X=U diag(sigma) V^T kappa=1e5"
 FP64_PEAK_TFLOPS = 1.25  # GB300 FP64 rate of the profiling recipe's table (nominal)
-# DRAM traffic of the dominant kernel relative to its algorithmic bytes, from one
-# ncu capture of the current kernel (profiles/gram_partial_kernel_m524288_256x32.md:
-# (1.208285 GB + 3.823 MB) / (524288 * 288 * 8 B + 304 * 256 * 32 * 8 B)); traffic
-# grows with the rows processed, so a full launch moves this ratio times its
-# algorithmic bytes.  None once the kernel changes until it is captured again.
-GRAM_TRAFFIC_RATIO = (1.208285e9 + 3.823104e6) / (524288 * 288 * 8 + 304 * 256 * 32 * 8)
+# DRAM traffic of a kernel relative to its algorithmic bytes, from one ncu capture
+# of the current kernel on a smaller case (profiles/); traffic grows with the rows
+# processed, so a full launch moves this ratio times its algorithmic bytes.  A
+# kernel that changed since its capture has no entry (traffic reported as null).
+TRAFFIC_RATIO = {
+    # profiles/gram_partial_kernel_m524288_256x32.md:
+    # (1.208285 GB + 3.823 MB) / (524288 * 288 * 8 B + 304 * 256 * 32 * 8 B)
+    "gram_partial_kernel": (1.208285e9 + 3.823104e6) / (524288 * 288 * 8 + 304 * 256 * 32 * 8),
+}
+
+
+def measured_peaks():
+    """HBM copy bandwidth measured on the GB300s (MEASURED_PEAKS.json,
+    written by the pool's driver), else the profiling recipe's fallback."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "bf16_tflops": float(d["bf16_tflops"]),
+                "source": "of measured (MEASURED_PEAKS.json hbm_gbs, STREAM-style copy)"}
+    except (OSError, KeyError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "source": "of fallback (profiling recipe)"}
 ORACLE_SAMPLE_ROWS = 2 ** 17
 
 
@@ -67,7 +83,7 @@ def parse():
                    help="time one building block alone (for profiling on small cases)")
     p.add_argument("--m", type=int, default=2 ** 19, help="rows for --kernel")
     p.add_argument("--engine", default="auto", choices=["auto", "fp64", "tensor"],
-                   help="Gram engine (bcgs_set_option)")
+                   help="inner-product engine of the Gram and projection kernels")
     return p.parse_args()
 
 
@@ -193,6 +209,8 @@ def main_ours(args):
     from paper_2507_21791_gb300 import bcgs, synth
 
     bcgs.load_library()
+    bcgs.set_gram_engine(args.engine)
+    engine = args.engine
     stream = torch.cuda.current_stream(dev)
     X = synth.make_matrix_torch(M, N, KAPPA, seed=1000 + 1 * 100 + rank, device=str(dev))
     torch.cuda.synchronize()
@@ -296,21 +314,38 @@ def main_ours(args):
                  "serving": bench_serving(args, dev)}
 
     prof = main["prof"]
-    gl, gms, gfl, gby = prof["gram_partial"]
-    achieved = gfl / (gms * 1e-3) / 1e12 if gms > 0 else None
+    peaks = measured_peaks()
     step_ms_total = sum(prof[k][1] for k in bcgs.PROFILE_CLASSES)
-    roofline = {
-        "bound": "alu", "kernel": "gram_partial_kernel (FP64 DFMA)",
-        "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-        "frac": achieved / FP64_PEAK_TFLOPS if achieved else None,
-        "peak_source": "FP64 rate of the profiling recipe (nominal; a DFMA probe measured 1.20)",
-        "traffic": GRAM_TRAFFIC_RATIO * gby / max(gl, 1) if GRAM_TRAFFIC_RATIO else None,
-        "traffic_note": "bytes per launch: ncu dram read+write / algorithmic bytes of a "
-                        "m=524288 capture, times this run's algorithmic bytes per launch",
+    # dominant kernel class of the timed region (by summed event time)
+    dom = max(("gram_partial", "project"), key=lambda k: prof[k][1])
+    gl, gms, gfl, gby = prof[dom]
+    kernel_name = {"gram_partial": "gram_tc_kernel" if engine != "fp64" else "gram_partial_kernel",
+                   "project": "proj_tc_kernel" if engine != "fp64" else "project_kernel"}[dom]
+    if engine == "fp64":
+        achieved = gfl / (gms * 1e-3) / 1e12
+        roofline = {"bound": "alu", "kernel": kernel_name + " (FP64 DFMA)", "achieved": achieved,
+                    "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                    "peak_source": "FP64 rate of the profiling recipe (nominal; a DFMA probe measured 1.20)"}
+    else:
+        achieved = gby / (gms * 1e-3) / 1e9
+        roofline = {"bound": "hbm", "kernel": kernel_name + " (exact bf16 digit products on tcgen05)",
+                    "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                    "frac": achieved / peaks["hbm_gbs"], "peak_source": peaks["source"],
+                    "fp64_equivalent_tflops": gfl / (gms * 1e-3) / 1e12}
+    roofline.update({
+        "traffic": TRAFFIC_RATIO[kernel_name] * gby / max(gl, 1) if kernel_name in TRAFFIC_RATIO else None,
+        "traffic_note": "bytes per launch: ncu dram read+write / algorithmic bytes of a smaller capture, "
+                        "times this run's algorithmic bytes per launch (null: not captured for this kernel)",
         "launches": gl, "avg_launch_ms": gms / max(gl, 1),
         "share_of_timed_kernel_time": gms / step_ms_total if step_ms_total else None,
-        "hbm_frac_of_measured_copy": value / 6669.5,
-    }
+        "step_hbm_frac_of_measured_copy": value / peaks["hbm_gbs"],
+    })
+    others = {}
+    for k in ("gram_partial", "project", "tsqr"):
+        n_, ms_, fl_, by_ = prof[k]
+        if ms_ > 0:
+            others[k] = {"ms_per_step": ms_ / args.steps, "alg_gbs": by_ / (ms_ * 1e-3) / 1e9,
+                         "fp64_equiv_tflops": fl_ / (ms_ * 1e-3) / 1e12}
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -326,6 +361,8 @@ def main_ours(args):
                 "d2h_bytes_per_step": M * N * 8 + N * N * 8, "ms_per_step": te.item()},
         "gpu_launches": main["launches"],
         "roofline": roofline,
+        "kernels": others,
+        "engine": engine,
         "speedup_vs_bcgsi_plus_at_equal_loo": speedup,
         "variants": compare,
         "clocks": prof["clocks"],

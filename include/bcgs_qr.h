@@ -233,13 +233,16 @@ BCGS_API int bcgs_chol(int32_t s, const double* A, int32_t lda, double* R, int32
 /* ---------------------------------------------------------------------------
  * Options (process-wide, host side).
  *
- * BCGS_OPT_GRAM_ENGINE selects how the synchronization's inner products are
+ * BCGS_OPT_GRAM_ENGINE selects how the inner products of the synchronization
+ * (the Gram reduction) and of the projection (Q C in (V - Q C) T^{-1}) are
  * computed:
  *   0  the FP64 pipe (DFMA, chunked fixed-order sums);
  *   1  (default) tensor cores when the call has at least BCGS_OPT_TC_MIN_ROWS
- *      rows and at most 64 columns on the right: each FP64 (or FP32) operand
- *      is split exactly into nine 7-bit integer digits relative to its
- *      column's maximum, digit pairs are multiplied on the bf16 tensor cores
+ *      rows (and, for the Gram, at most 64 columns on the right; for the
+ *      projection s <= 32): each FP64 (or FP32) operand
+ *      is split exactly into nine 7-bit integer digits relative to the
+ *      maximum along its contraction line (a column of a Gram operand, a row
+ *      of Q), digit pairs are multiplied on the bf16 tensor cores
  *      with exact integer sums, and one FP64 rounding per row chunk remains
  *      (error per product term <= 2^-57.5 max|a_i| max|b_j|);
  *   2  tensor cores whenever the shape allows it.

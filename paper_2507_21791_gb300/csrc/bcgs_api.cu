@@ -84,6 +84,11 @@ bool use_tensor_gram(const GramDesc& d) {
   if (e == 0 || !gram_tc_supported(d)) return false;
   return e == 2 || d.m >= gram_tc_min_rows();
 }
+bool use_tensor_project(const ProjDesc& d) {
+  const int e = gram_engine();
+  if (e == 0 || !project_tc_supported(d)) return false;
+  return e == 2 || d.m >= gram_tc_min_rows();
+}
 }  // namespace bcgs
 
 struct bcgs_qr_s {
@@ -172,6 +177,7 @@ cudaError_t project(bcgs_qr_s* h, Seg v, int c, const double* C, int ldc, const 
   d.w_fp32 = h->fp32;
   d.m = h->m;
   d.s = h->s;
+  if (use_tensor_project(d)) return launch_project_tc(d, h->st(), h->stream);
   return launch_project(d, h->st(), h->stream);
 }
 
@@ -603,9 +609,10 @@ int bcgs_project(int64_t m, int32_t c, int32_t s, const double* V, int64_t ldv, 
   d.w_fp32 = 0;
   d.m = m;
   d.s = s;
-  return launch_project(d, nullptr, reinterpret_cast<cudaStream_t>(stream)) == cudaSuccess
-             ? BCGS_OK
-             : BCGS_ERR_CUDA;
+  cudaStream_t sm = reinterpret_cast<cudaStream_t>(stream);
+  const cudaError_t e = use_tensor_project(d) ? launch_project_tc(d, nullptr, sm)
+                                              : launch_project(d, nullptr, sm);
+  return e == cudaSuccess ? BCGS_OK : BCGS_ERR_CUDA;
 }
 
 int bcgs_tsqr_workspace_size(int64_t m, int32_t s, size_t* bytes) {

@@ -102,6 +102,10 @@ struct ProjDesc {
   int64_t m; int32_t s;
 };
 cudaError_t launch_project(const ProjDesc& d, DevStatus* st, cudaStream_t stream);
+// Tensor-core form (proj_tc.cu): s <= 32 and c >= 1.
+bool project_tc_supported(const ProjDesc& d);
+cudaError_t launch_project_tc(const ProjDesc& d, DevStatus* st, cudaStream_t stream);
+bool use_tensor_project(const ProjDesc& d);
 
 // TSQR of an m x s block.
 struct TsqrPlan {

@@ -36,102 +36,17 @@
 // records BCGS_ERR_TIMEOUT and returns after freeing its tensor memory.
 #include <string.h>
 
-#include "bcgs_internal.cuh"
+#include "tc_common.cuh"
 
 namespace bcgs {
 namespace {
+using namespace tc;
 
 constexpr int kThreads = 256;
-constexpr int kDigits = 9;
 constexpr int kBlockRows = 64;    // rows (K) per MMA stage: one 128-byte SW128 row of bf16
 constexpr int kFlushBlocks = 1;   // 64 rows between tensor-memory read-backs
 constexpr int kMTile = 128;       // A columns per CTA (MMA M)
 constexpr int kATile = kMTile * 128;  // bytes of one digit tile of A (128 rows x 128 B)
-constexpr long long kWaitCycles = 2000000000LL;  // about one second at GB300 clocks
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-// tcgen05 shared-memory descriptor: K-major, 128-byte swizzle, 8-row groups
-// 1024 bytes apart.
-__device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
-  uint64_t d = (uint64_t)((saddr & 0x3FFFF) >> 4);
-  d |= (uint64_t)1 << 16;
-  d |= (uint64_t)(1024 >> 4) << 32;
-  d |= (uint64_t)1 << 46;
-  d |= (uint64_t)2 << 61;
-  return d;
-}
-
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
-                                         uint32_t accumulate) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-      "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
-}
-
-__device__ __forceinline__ bool mbar_try(uint32_t mbar, uint32_t phase) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      " selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(mbar), "r"(phase));
-  return ok != 0;
-}
-
-template <typename T>
-__device__ __forceinline__ double ld_elem(const void* base, int64_t idx) {
-  return (double)__ldg(reinterpret_cast<const T*>(base) + idx);
-}
-
-// 63-bit fixed-point magnitude of a relative to the column exponent field
-// `cexp` (the biased exponent of the column's max |a|): N = |a| 2^(63 - E),
-// E = cexp - 1022.  neg receives the sign bit.
-__device__ __forceinline__ uint64_t fixed56(double a, int cexp, uint32_t& neg) {
-  const uint64_t bits = (uint64_t)__double_as_longlong(a);
-  neg = (uint32_t)(bits >> 63);
-  const int e = (int)((bits >> 52) & 0x7FF);
-  if (e == 0) return 0;  // zero or subnormal
-  const uint64_t mant = (bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-  const int sh = e - cexp + 10;  // <= 10 because |a| <= max
-  if (sh >= 0) return mant << (sh > 10 ? 10 : sh);
-  return -sh < 64 ? (mant >> (-sh)) : 0;
-}
-
-// bf16 bit pattern of the signed integer (neg ? -d : d), 0 <= d < 128:
-// (2^23 + d) - 2^23 in fp32 with the sign folded into both operands.
-__device__ __forceinline__ uint32_t digit_f32(uint32_t d, uint32_t neg) {
-  const float big = __int_as_float((int)(0x4B000000u | d | (neg << 31)));
-  const float off = __int_as_float((int)(0xCB000000u ^ (neg << 31)));
-  return __float_as_uint(big + off);
-}
-
-// Split 8 consecutive rows of one column into the 9 digit tiles: tile t gets
-// the 16 bytes (8 bf16) at row `row` (the MMA M/N index), 16-byte chunk `g`,
-// swizzled as SW128 expects (chunk ^ (row % 8)).
-__device__ __forceinline__ void split8(const double (&v)[8], int cexp, uint8_t* tiles, int tile_bytes,
-                                       int row, int g) {
-  uint64_t N[8];
-  uint32_t ng[8];
-#pragma unroll
-  for (int e = 0; e < 8; ++e) N[e] = fixed56(v[e], cexp, ng[e]);
-  const int off = row * 128 + ((g ^ (row & 7)) << 4);
-#pragma unroll
-  for (int t = 0; t < kDigits; ++t) {
-    const int sh = 56 - 7 * t;
-    uint32_t w[4];
-#pragma unroll
-    for (int p = 0; p < 4; ++p) {
-      const uint32_t d0 = (uint32_t)(N[2 * p] >> sh) & 0x7Fu;
-      const uint32_t d1 = (uint32_t)(N[2 * p + 1] >> sh) & 0x7Fu;
-      w[p] = __byte_perm(digit_f32(d0, ng[2 * p]), digit_f32(d1, ng[2 * p + 1]), 0x7632);
-    }
-    *reinterpret_cast<uint4*>(tiles + t * tile_bytes + off) = make_uint4(w[0], w[1], w[2], w[3]);
-  }
-}
 
 struct TcCols {
   int32_t a_off[kMaxSegA + 1];

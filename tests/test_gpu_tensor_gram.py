@@ -112,3 +112,25 @@ def test_row_scaled_heavy_tails_meet_the_gates(cuda):
             assert oracle.loo(Qh) <= 1e-12
     finally:
         cuda.set_gram_engine("auto")
+
+
+@pytest.mark.parametrize("m,c,s,with_t", [(129, 3, 2, True), (10000, 56, 8, True), (10000, 56, 8, False),
+                                          (65537, 240, 16, True), (3000, 96, 32, True), (1000, 500, 5, True),
+                                          (40000, 64, 16, False)])
+def test_tensor_project_parity(tensor, m, c, s, with_t):
+    """(V - Q C) T^{-1} with Q C on the tensor cores (row exponents of Q, column
+    exponents of C) against the oracle; same derived FP64 tolerance as the
+    FP64-pipe kernel (the digit error c 2^-57.5 max|q_r| max|c_j| is below it)."""
+    rng = np.random.default_rng(m + c + s)
+    V = rng.standard_normal((m, s))
+    Q = np.linalg.qr(rng.standard_normal((m, c)))[0]
+    C = rng.standard_normal((c, s))
+    T = synth.make_upper_triangular_np(s, 10.0, seed=s) if with_t else None
+    Wo = oracle.project_normalize(V, Q, C, T if with_t else np.eye(s))
+    W = tensor.project(tensor.to_device_colmajor(V), tensor.to_device_colmajor(Q),
+                       tensor.to_device_colmajor(C),
+                       tensor.to_device_colmajor(T) if with_t else None).cpu().numpy()
+    scale = np.abs(V) + np.abs(Q) @ np.abs(C)
+    kt = oracle.kappa(T) if with_t else 1.0
+    tol = 4 * (c + s + 2) * U64 * kt * np.max(scale) / (np.min(np.abs(np.diag(T))) if with_t else 1)
+    assert np.max(np.abs(W - Wo)) <= tol
