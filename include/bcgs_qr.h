@@ -240,11 +240,11 @@ BCGS_API int bcgs_chol(int32_t s, const double* A, int32_t lda, double* R, int32
  *   1  (default) tensor cores when the call has at least BCGS_OPT_TC_MIN_ROWS
  *      rows (and, for the Gram, at most 64 columns on the right; for the
  *      projection s <= 32): each FP64 (or FP32) operand
- *      is split exactly into nine 7-bit integer digits relative to the
+ *      is split exactly into eight 8-bit integer digits relative to the
  *      maximum along its contraction line (a column of a Gram operand, a row
  *      of Q), digit pairs are multiplied on the bf16 tensor cores
  *      with exact integer sums, and one FP64 rounding per row chunk remains
- *      (error per product term <= 2^-57.5 max|a_i| max|b_j|);
+ *      (error per product term <= 2^-57.1 max|a_i| max|b_j|);
  *   2  tensor cores whenever the shape allows it.
  * BCGS_OPT_TC_MIN_ROWS is the row threshold of engine 1 (default 16384).
  * Both engines use the same row partition, so each is deterministic; they

@@ -8,32 +8,30 @@
 //
 //   * every column i of A (and j of B) gets the exponent E_i with
 //     max_r |a_ri| < 2^E_i (a column-max pass precedes the kernel);
-//   * a_ri = sign * N * 2^(E_i - 63) with the integer N < 2^63 (truncated),
-//     N = sum_t d_t 2^(56 - 7t), nine digits 0 <= d_t < 128 (t = 0..8);
-//     each signed digit is an integer of at most 7 bits, exact in bf16;
-//   * d^A_t (x) d^B_u for t + u <= 8 (45 digit pairs) run as bf16 tcgen05.mma
-//     with fp32 accumulation in tensor memory, one accumulator per level
-//     l = t + u; a level sums at most (l+1) * 64 * 127^2 < 2^24 over 64 rows,
-//     so every accumulator stays an exact integer;
-//   * every 64 rows the nine level accumulators are read back (tcgen05.ld),
-//     combined exactly in 32-bit and added into two int64 accumulators
-//     (levels 0-4 and 5-8);
-//   * at the end of its chunk a CTA writes
-//     2^(E_i + E_j - 70) (hi 2^28 + lo) as the FP64 chunk partial.
+//   * each entry becomes eight signed 8-bit digits relative to E_i, exact bf16
+//     integers (tc_common.cuh);
+//   * the 36 digit pairs t + u <= 7 run as bf16 tcgen05.mma with fp32
+//     accumulation in tensor memory, one accumulator per level l = t + u,
+//     exact over a 32-row block;
+//   * after every block the eight level sums are read back (tcgen05.ld) and
+//     added exactly into two int64 accumulators per output;
+//   * at the end of its chunk a CTA writes 2^(E_i + E_j - 70) (hi 2^32 + lo)
+//     as the FP64 chunk partial.
 //
-// Dropped digit pairs (t + u >= 9) and the truncation of N bound the error of a
-// product term by 2^(E_i + E_j - 59.5) <= 2^-57.5 max|a_i| max|b_j|; the
-// integer sums are exact, so the chunk partial carries one FP64 rounding.  The
-// partials are added in chunk order by the reduction kernel of gram.cu.
-// (Fixed point relative to the column maximum loses log2(max|a_i| / |a_ri|)
-// bits on small entries; nine digits keep heavy-tailed columns, such as rows
-// with lognormal norms, at FP64-level accuracy.)
+// The error of one product term is at most 2^-57.1 max|a_i| max|b_j| (dropped
+// digit pairs and truncation); the integer sums are exact, so the chunk
+// partial carries one FP64 rounding.  The partials are added in chunk order by
+// the reduction kernel of gram.cu.  (Fixed point relative to the column maximum
+// loses log2(max|a_i| / |a_ri|) bits on small entries; 64 bits keep heavy-tailed
+// columns, such as rows with lognormal norms, at FP64-level accuracy.)
 //
-// One CTA (256 threads) per (chunk, 128-column tile of A); all threads split
-// a 64-row block into swizzled (SW128, K-major) bf16 tiles in shared memory,
-// one thread issues the 180 MMAs of the block, all eight warps read tensor
-// memory back.  Every wait on the MMA barrier is bounded; on timeout the kernel
-// records BCGS_ERR_TIMEOUT and returns after freeing its tensor memory.
+// One CTA (512 threads) per (chunk, 128-column tile of A, 32-column tile of B),
+// software-pipelined over 32-row blocks: cp.async stages block b+2 in shared
+// memory while all threads split block b+1 into K-major bf16 digit tiles (one of
+// two buffers) and the tensor cores run the MMAs of block b (issued by one
+// thread, one per digit of A and 16-row step); then the warps read the level sums of block b back.  Every
+// wait on the MMA barrier is bounded; on timeout the kernel records
+// BCGS_ERR_TIMEOUT and returns after freeing its tensor memory.
 #include <string.h>
 
 #include "tc_common.cuh"
@@ -42,11 +40,11 @@ namespace bcgs {
 namespace {
 using namespace tc;
 
-constexpr int kThreads = 256;
-constexpr int kBlockRows = 64;    // rows (K) per MMA stage: one 128-byte SW128 row of bf16
-constexpr int kFlushBlocks = 1;   // 64 rows between tensor-memory read-backs
-constexpr int kMTile = 128;       // A columns per CTA (MMA M)
-constexpr int kATile = kMTile * 128;  // bytes of one digit tile of A (128 rows x 128 B)
+constexpr int kThreads = 512;
+constexpr int kBlockRows = 32;          // rows (K) per MMA stage
+constexpr int kChunks = kBlockRows / 8;  // 16-byte chunks of K per operand row in a digit tile
+constexpr int kMTile = 128;              // A columns per CTA (MMA M)
+constexpr int kATile = kMTile * kBlockRows * 2;  // bytes of one digit tile of A
 
 struct TcCols {
   int32_t a_off[kMaxSegA + 1];
@@ -97,21 +95,25 @@ __global__ void __launch_bounds__(kThreads, 1)
 gram_tc_kernel(GramDesc d, TcCols cm, const unsigned long long* __restrict__ amax,
                double* __restrict__ partial, DevStatus* st) {
   static_assert(NBT == 16 || NBT == 32, "N tile");
-  constexpr int kBTile = NBT * 128;       // bytes of one digit tile of B
-  constexpr int kTmemCols = kDigits * NBT <= 256 ? (kDigits * NBT <= 128 ? 128 : 256) : 512;
-  constexpr int kHalf = NBT / 2;          // output columns per thread in the read-back
+  constexpr int kBTile = NBT * kBlockRows * 2;          // bytes of one digit tile of B
+  constexpr int kStage = kDigits * (kATile + kBTile);  // one buffer of digit tiles
+  constexpr int kCols = kMTile + NBT;                  // columns staged per block
+  constexpr int kColBytes = kBlockRows * (int)sizeof(T) + 16;  // staged column, padded
+  constexpr int kTmemCols = kDigits * NBT <= 128 ? 128 : (kDigits * NBT <= 256 ? 256 : 512);
+  constexpr int kHalf = 8;                             // output columns per thread in the read-back
+  constexpr int kGroups = NBT / kHalf;                 // column groups (warps w / 4 < kGroups read back)
   if (block_failed(st)) return;
   extern __shared__ uint8_t dyn[];
   __shared__ __align__(8) uint64_t mbar;
   __shared__ uint32_t tmem_base_s;
   __shared__ int s_cexp_a[kMTile];
   __shared__ int s_cexp_b[NBT];
+  __shared__ const T* s_colptr[kCols];
   __shared__ int s_bad;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(dyn) + 1023) & ~uintptr_t(1023));
-  uint8_t* At = base;                         // kDigits tiles of kATile bytes
-  uint8_t* Bt = base + kDigits * kATile;      // kDigits tiles of kBTile bytes
+  uint8_t* digits = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(dyn) + 1023) & ~uintptr_t(1023));
+  uint8_t* staging = digits + 2 * kStage;
 
   const int chunk = blockIdx.x;
   const int col0 = blockIdx.y * kMTile;       // first A column of this tile
@@ -126,179 +128,175 @@ gram_tc_kernel(GramDesc d, TcCols cm, const unsigned long long* __restrict__ ama
   __syncthreads();
   for (int i = tid; i < kMTile; i += kThreads) {
     int e = 0;
+    const T* p = nullptr;
     if (i < ncol_a) {
-      const unsigned long long b = amax[col0 + i];
-      e = cexp_of(b);
+      const int ca = col0 + i;
+      e = cexp_of(amax[ca]);
       if (e == 0x7FF) s_bad = 1;
+      const int sg = find_seg<kMaxSegA>(cm.a_off, d.nsa, ca);
+      p = reinterpret_cast<const T*>(d.a[sg].p) + (int64_t)(ca - cm.a_off[sg]) * d.a[sg].ld;
     }
     s_cexp_a[i] = e;
+    s_colptr[i] = p;
   }
   for (int j = tid; j < NBT; j += kThreads) {
     int e = 0;
+    const T* p = nullptr;
     if (j < nb) {
-      const unsigned long long b = amax[d.na + jb0 + j];
-      e = cexp_of(b);
+      const int cb = jb0 + j;
+      e = cexp_of(amax[d.na + cb]);
       if (e == 0x7FF) s_bad = 1;
+      const int sg = find_seg<kMaxSegB>(cm.b_off, d.nsb, cb);
+      p = reinterpret_cast<const T*>(d.b[sg].p) + (int64_t)(cb - cm.b_off[sg]) * d.b[sg].ld;
     }
     s_cexp_b[j] = e;
+    s_colptr[kMTile + j] = p;
   }
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
-                     smem_u32(&tmem_base_s)),
-                 "n"(kTmemCols));
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
-  }
-  if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&mbar)));
-    asm volatile("fence.mbarrier_init.release.cluster;\n");
-  }
-  asm volatile("tcgen05.fence::before_thread_sync;\n");
+  if (warp == 0) tmem_alloc<kTmemCols>(&tmem_base_s);
+  if (tid == 0) mbar_init(&mbar);
+  tc_before_sync();
   __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;\n");
+  tc_after_sync();
   const uint32_t tmem = tmem_base_s;
   const bool bad = s_bad != 0;
   if (bad && tid == 0) set_failure(st, BCGS_ERR_NONFINITE, d.block);
+  const T* any_ptr = reinterpret_cast<const T*>(d.a[0].p);
+
+  // global -> staging (column-major, one warp per 32 contiguous rows of a column)
+  auto stage_copy = [&](int64_t r0) {
+    for (int e = tid; e < kCols * kBlockRows; e += kThreads) {
+      const int col = e / kBlockRows, r = e - col * kBlockRows;
+      const T* p = s_colptr[col];
+      const bool valid = p != nullptr && r0 + r < r_end;
+      void* dst = staging + col * kColBytes + r * (int)sizeof(T);
+      if constexpr (sizeof(T) == 8) cp_async8(dst, valid ? p + r0 + r : any_ptr, valid);
+      else cp_async4(dst, valid ? p + r0 + r : any_ptr, valid);
+    }
+    cp_async_commit();
+  };
+  // staging -> digit tiles of buffer `buf`: task (column, 8-row group g); consecutive
+  // threads take consecutive columns (conflict-free staging reads and tile writes)
+  auto split_block = [&](int buf) {
+    uint8_t* dA = digits + buf * kStage;
+    uint8_t* dB = dA + kDigits * kATile;
+    for (int e = tid; e < kCols * kChunks; e += kThreads) {
+      const int g = e / kCols, col = e - g * kCols;
+      const T* src = reinterpret_cast<const T*>(staging + col * kColBytes) + 8 * g;
+      double v[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) v[k] = (double)src[k];
+      if (col < kMTile) split8_interleave(v, s_cexp_a[col], dA, kATile, col, g, kChunks);
+      else split8_interleave(v, s_cexp_b[col - kMTile], dB, kBTile, col - kMTile, g, kChunks);
+    }
+  };
+  // One MMA per (digit t of A, 16-row K step): the B digit tiles are contiguous,
+  // so [B_0 ... B_{8-t}] is a single K-major operand of (9-t) NBT rows whose
+  // product with A_t lands, tile u, in the accumulator of level t + u (tensor
+  // memory columns (t + u) NBT); pieces of at most 256 columns.
+  auto issue_mma = [&](int buf) {
+    const uint32_t a0 = smem_u32(digits + buf * kStage);
+    const uint32_t b0 = a0 + kDigits * kATile;
+    constexpr int kMaxLev = 256 / NBT;
+#pragma unroll 1
+    for (int t = 0; t < kDigits; ++t) {
+      const int nlev = kDigits - t;
+#pragma unroll 1
+      for (int l0 = 0; l0 < nlev; l0 += kMaxLev) {
+        const int nl = nlev - l0 < kMaxLev ? nlev - l0 : kMaxLev;
+        const uint32_t id = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)((nl * NBT) >> 3) << 17) |
+                            ((uint32_t)(kMTile >> 4) << 24);
+        const uint32_t dcol = tmem + (uint32_t)((t + l0) * NBT);
+#pragma unroll
+        for (int kk = 0; kk < kBlockRows / 16; ++kk)
+          mma_bf16(dcol, desc_interleave(a0 + t * kATile + kk * 256, 128, kChunks * 128),
+                   desc_interleave(b0 + l0 * kBTile + kk * 256, 128, kChunks * 128), id,
+                   (t == 0 && kk == 0) ? 0u : 1u);
+      }
+    }
+    mma_commit(&mbar);
+  };
 
   // read-back role: lane quadrant (warp % 4) -> A column, half (warp / 4) -> B columns
   const int my_i = 32 * (warp & 3) + lane;
   const int my_j0 = (warp >> 2) * kHalf;
+  const bool reader = (warp >> 2) < kGroups;
   long long hi[kHalf], lo[kHalf];
 #pragma unroll
   for (int j = 0; j < kHalf; ++j) hi[j] = lo[j] = 0;
 
-  const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NBT >> 3) << 17) |
-                         ((uint32_t)(kMTile >> 4) << 24);
   uint32_t phase = 0;
   bool timed_out = false;
   const int nblocks = bad ? 0 : (int)((r_end - r_begin + kBlockRows - 1) / kBlockRows);
 
-  for (int b = 0; b < nblocks; ++b) {
-    const int64_t r0 = r_begin + (int64_t)b * kBlockRows;
-    // ---- split A: tasks (column, 8-row group)
-    for (int e = tid; e < kMTile * 8; e += kThreads) {
-      const int i = e >> 3, g = e & 7;
-      double v[8];
-      if (i < ncol_a) {
-        const int ca = col0 + i;
-        const int sg = find_seg<kMaxSegA>(cm.a_off, d.nsa, ca);
-        const int64_t cbase = (int64_t)(ca - cm.a_off[sg]) * d.a[sg].ld;
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-          const int64_t row = r0 + 8 * g + k;
-          v[k] = row < r_end ? ld_elem<T>(d.a[sg].p, cbase + row) : 0.0;
-        }
-      } else {
-#pragma unroll
-        for (int k = 0; k < 8; ++k) v[k] = 0.0;
-      }
-      split8(v, s_cexp_a[i], At, kATile, i, g);
-    }
-    // ---- split B
-    for (int e = tid; e < NBT * 8; e += kThreads) {
-      const int j = e >> 3, g = e & 7;
-      double v[8];
-      if (j < nb) {
-        const int sg = find_seg<kMaxSegB>(cm.b_off, d.nsb, jb0 + j);
-        const int64_t cbase = (int64_t)(jb0 + j - cm.b_off[sg]) * d.b[sg].ld;
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-          const int64_t row = r0 + 8 * g + k;
-          v[k] = row < r_end ? ld_elem<T>(d.b[sg].p, cbase + row) : 0.0;
-        }
-      } else {
-#pragma unroll
-        for (int k = 0; k < 8; ++k) v[k] = 0.0;
-      }
-      split8(v, s_cexp_b[j], Bt, kBTile, j, g);
-    }
-    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-    asm volatile("tcgen05.fence::before_thread_sync;\n");
+  // Pipeline: block b's MMAs run while block b+1 is split; block b+2 is being
+  // copied into the staging buffer meanwhile.
+  if (nblocks > 0) {
+    stage_copy(r_begin);
+    cp_async_wait_all();
     __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;\n");
-    // ---- MMAs of this block (one thread)
-    const bool window_start = (b % kFlushBlocks) == 0;
-    if (tid == 0) {
-#pragma unroll 1
-      for (int t = 0; t < kDigits; ++t) {
-        const uint32_t a_base = smem_u32(At + t * kATile);
-#pragma unroll 1
-        for (int u = 0; t + u < kDigits; ++u) {
-          const uint32_t b_base = smem_u32(Bt + u * kBTile);
-          const uint32_t dcol = tmem + (uint32_t)((t + u) * NBT);
-#pragma unroll
-          for (int kk = 0; kk < kBlockRows / 16; ++kk) {
-            const uint32_t acc = (window_start && t == 0 && kk == 0) ? 0u : 1u;
-            mma_bf16(dcol, desc_sw128(a_base + kk * 32), desc_sw128(b_base + kk * 32), idesc, acc);
-          }
-        }
-      }
-      asm volatile(
-          "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
-              smem_u32(&mbar)));
+    split_block(0);
+    __syncthreads();
+    if (nblocks > 1) stage_copy(r_begin + kBlockRows);
+    fence_smem_to_async();
+    tc_before_sync();
+    __syncthreads();
+    tc_after_sync();
+    if (tid == 0) issue_mma(0);
+  }
+  for (int b = 0; b < nblocks; ++b) {
+    const bool more = b + 1 < nblocks;
+    if (more) {
+      cp_async_wait_all();
+      __syncthreads();
+      split_block((b + 1) & 1);
+      __syncthreads();
+      if (b + 2 < nblocks) stage_copy(r_begin + (int64_t)(b + 2) * kBlockRows);
     }
-    bool ok = false;
-    const long long t_wait = clock64();
-    while (!(ok = mbar_try(smem_u32(&mbar), phase)))
-      if (clock64() - t_wait > kWaitCycles) break;
+    const bool ok = mbar_wait_bounded(&mbar, phase);
     phase ^= 1u;
     if (__syncthreads_or(!ok)) {
       timed_out = true;
       break;
     }
-    asm volatile("tcgen05.fence::after_thread_sync;\n");
-    // ---- read back and fold the level accumulators every kFlushBlocks blocks
-    if ((b % kFlushBlocks) == kFlushBlocks - 1 || b == nblocks - 1) {
-      const uint32_t lane_addr = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)my_j0;
+    tc_after_sync();
+    // read back the exact level sums of block b and fold them
+    const uint32_t lane_addr = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)my_j0;
+    if (reader) {
 #pragma unroll
-      for (int g8 = 0; g8 < kHalf; g8 += 8) {
-        int32_t L[kDigits][8];
+    for (int g8 = 0; g8 < kHalf; g8 += 8) {
+      int32_t L[8][kDigits];
 #pragma unroll
-        for (int l = 0; l < kDigits; ++l) {
-          uint32_t r[8];
-          const uint32_t taddr = lane_addr + (uint32_t)(l * NBT + g8);
-          asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
-                       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
-                         "=r"(r[6]), "=r"(r[7])
-                       : "r"(taddr));
-          asm volatile("tcgen05.wait::ld.sync.aligned;\n");
+      for (int l = 0; l < kDigits; ++l) {
+        uint32_t r[8];
+        tmem_ld8(lane_addr + (uint32_t)(l * NBT + g8), r);
 #pragma unroll
-          for (int j = 0; j < 8; ++j) L[l][j] = __float2int_rn(__uint_as_float(r[j]));
-        }
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          // exact: |L_l| <= (l+1) 64 127^2 < (l+1) 2^20
-          const int32_t c01 = (L[0][j] << 7) + L[1][j];
-          const int32_t c23 = (L[2][j] << 7) + L[3][j];
-          const int32_t c56 = (L[5][j] << 7) + L[6][j];
-          const int32_t c78 = (L[7][j] << 7) + L[8][j];
-          hi[g8 + j] += ((long long)c01 << 21) + ((long long)c23 << 7) + (long long)L[4][j];
-          lo[g8 + j] += ((long long)c56 << 14) + (long long)c78;
-        }
+        for (int j = 0; j < 8; ++j) L[j][l] = __float2int_rn(__uint_as_float(r[j]));
       }
+#pragma unroll
+      for (int j = 0; j < 8; ++j) fold_levels(L[j], hi[g8 + j], lo[g8 + j]);
     }
-    asm volatile("tcgen05.fence::before_thread_sync;\n");
-    __syncthreads();  // tiles and accumulators are free for the next block
+    }
+    fence_smem_to_async();
+    tc_before_sync();
+    __syncthreads();
+    tc_after_sync();
+    if (more && tid == 0) issue_mma((b + 1) & 1);
   }
+  cp_async_wait_all();
 
-  if (!bad && !timed_out) {
-    if (my_i < ncol_a) {
-      double* out = partial + (size_t)chunk * ((size_t)d.na * ldp) + (size_t)(col0 + my_i) * ldp + jb0;
-      const int ea = s_cexp_a[my_i];
+  if (!bad && !timed_out && reader && my_i < ncol_a) {
+    double* out = partial + (size_t)chunk * ((size_t)d.na * ldp) + (size_t)(col0 + my_i) * ldp + jb0;
+    const int ea = s_cexp_a[my_i];
 #pragma unroll
-      for (int j = 0; j < kHalf; ++j) {
-        const int jj = my_j0 + j;
-        if (jj < nb) {
-          const int sc = ea + s_cexp_b[jj] - 2044;  // E_i + E_j
-          out[jj] = ldexp((double)hi[j], sc - 42) + ldexp((double)lo[j], sc - 70);
-        }
-      }
+    for (int j = 0; j < kHalf; ++j) {
+      const int jj = my_j0 + j;
+      if (jj < nb) out[jj] = unfold(hi[j], lo[j], ea, s_cexp_b[jj]);
     }
   }
   if (timed_out && tid == 0) set_failure(st, BCGS_ERR_TIMEOUT, d.block);
-  asm volatile("tcgen05.fence::before_thread_sync;\n");
+  tc_before_sync();
   __syncthreads();
-  if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "n"(kTmemCols));
+  if (warp == 0) tmem_dealloc<kTmemCols>(tmem);
 }
 
 __global__ void zero_u64_kernel(unsigned long long* p, int n) {
@@ -326,7 +324,8 @@ cudaError_t launch_t(const GramDesc& d, double* partial, double* G, int ldg, uns
   dim3 grid(d.nchunks, (unsigned)ceil_div(d.na, kMTile), (unsigned)ceil_div(d.nb, nbt));
 #define BCGS_TC_CASE(NB)                                                                        \
   {                                                                                             \
-    const size_t smem = 1024 + (size_t)kDigits * (kATile + NB * 128);                           \
+    const size_t smem = 1024 + 2 * (size_t)kDigits * (kATile + NB * kBlockRows * 2) +           \
+                        (size_t)(kMTile + NB) * (kBlockRows * sizeof(T) + 16);                  \
     cudaError_t e = ensure_dyn_smem(gram_tc_kernel<T, NB>, smem);                               \
     if (e != cudaSuccess) return e;                                                             \
     gram_tc_kernel<T, NB><<<grid, kThreads, smem, stream>>>(d, cm, amax, partial, st);           \

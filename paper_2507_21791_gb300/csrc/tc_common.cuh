@@ -1,8 +1,17 @@
 // Device helpers shared by the tensor-core kernels (gram_tc.cu, proj_tc.cu):
-// tcgen05 descriptors and MMA issue, bounded mbarrier polling, and the exact
-// splitting of an FP64 value into nine 7-bit digits relative to an exponent
-// (error-free splitting in the manner of Ozaki, Ogita, Oishi and Rump,
-// Numer. Algorithms 59, 2012).
+// tcgen05 descriptors and MMA issue, bounded mbarrier polling, asynchronous
+// copies, and the exact splitting of an FP64 value into eight 8-bit digits
+// relative to an exponent (error-free splitting in the manner of Ozaki, Ogita,
+// Oishi and Rump, Numer. Algorithms 59, 2012).
+//
+// Digits: with E the exponent of the line's maximum (|a| < 2^E),
+// a = sign N 2^(E - 63) with the integer N < 2^63 (truncated), and the digits
+// are the bytes of N: N = sum_t d_t 2^(56 - 8t), t = 0..7 (d_0 < 128).  A
+// signed digit is an integer of magnitude at most 255, exact in bf16.  The
+// product of two digits is below 2^16; a level l = t + u of at most eight digit
+// pairs summed over 32 rows stays below 8 * 32 * 255^2 < 2^24, exact in fp32.
+// Keeping the pairs t + u <= 7 (36 pairs) and truncating N bound the error of
+// one product term by 2^(E_a + E_b - 59.1) <= 2^-57.1 max|a| max|b|.
 #pragma once
 
 #include "bcgs_internal.cuh"
@@ -10,7 +19,7 @@
 namespace bcgs {
 namespace tc {
 
-constexpr int kDigits = 9;
+constexpr int kDigits = 8;
 constexpr long long kWaitCycles = 2000000000LL;  // about one second at GB300 clocks
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -28,12 +37,30 @@ __device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
   return d;
 }
 
+// tcgen05 shared-memory descriptor, K-major without swizzle: 8-row x 16-byte core
+// matrices stored contiguously (128 B each); `lbo` = byte distance between core
+// matrices adjacent along K, `sbo` = between core matrices adjacent along M/N.
+__device__ __forceinline__ uint64_t desc_interleave(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = (uint64_t)((saddr & 0x3FFFF) >> 4);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+  d |= (uint64_t)1 << 46;
+  return d;
+}
+
+// D (tensor memory, fp32) (+)= A B^T for bf16 A (M x K) and B (N x K) in shared
+// memory; `accumulate` = 0 overwrites D.
 __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
                                          uint32_t accumulate) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
       " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
       "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+}
+
+// Instruction descriptor of kind::f16: fp32 D, bf16 A and B, both K-major.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
 __device__ __forceinline__ bool mbar_try(uint32_t mbar, uint32_t phase) {
@@ -51,9 +78,9 @@ __device__ __forceinline__ double ld_elem(const void* base, int64_t idx) {
   return (double)__ldg(reinterpret_cast<const T*>(base) + idx);
 }
 
-// 63-bit fixed-point magnitude of a relative to the column exponent field
-// `cexp` (the biased exponent of the column's max |a|): N = |a| 2^(63 - E),
-// E = cexp - 1022.  neg receives the sign bit.
+// 63-bit fixed-point magnitude of a relative to the exponent field `cexp` (the
+// biased exponent of the line's max |a|): N = |a| 2^(63 - E), E = cexp - 1022,
+// truncated.  neg receives the sign bit.
 __device__ __forceinline__ uint64_t fixed63(double a, int cexp, uint32_t& neg) {
   const uint64_t bits = (uint64_t)__double_as_longlong(a);
   neg = (uint32_t)(bits >> 63);
@@ -65,38 +92,62 @@ __device__ __forceinline__ uint64_t fixed63(double a, int cexp, uint32_t& neg) {
   return -sh < 64 ? (mant >> (-sh)) : 0;
 }
 
-// bf16 bit pattern of the signed integer (neg ? -d : d), 0 <= d < 128:
-// (2^23 + d) - 2^23 in fp32 with the sign folded into both operands.
-__device__ __forceinline__ uint32_t digit_f32(uint32_t d, uint32_t neg) {
-  const float big = __int_as_float((int)(0x4B000000u | d | (neg << 31)));
-  const float off = __int_as_float((int)(0xCB000000u ^ (neg << 31)));
-  return __float_as_uint(big + off);
+// fp32 bits of the signed digit in byte `sel` of x: the byte is placed into the
+// sign-carrying magic word +-2^23 (0x4B000000 / 0xCB000000) and the magic is
+// removed, (+-(2^23 + d)) -/+ 2^23 = +-d exactly: one PRMT and one FADD.
+__device__ __forceinline__ uint32_t digit_byte_f32(uint32_t x, uint32_t magic, float off, uint32_t sel) {
+  return __float_as_uint(__uint_as_float(__byte_perm(x, magic, 0x7650u | sel)) + off);
 }
 
-// Split 8 consecutive rows of one column into the 9 digit tiles: tile t gets
-// the 16 bytes (8 bf16) at row `row` (the MMA M/N index), 16-byte chunk `g`,
-// swizzled as SW128 expects (chunk ^ (row % 8)).
-__device__ __forceinline__ void split8(const double (&v)[8], int cexp, uint8_t* tiles, int tile_bytes,
-                                       int row, int g) {
-  uint64_t N[8];
-  uint32_t ng[8];
+// Split 8 consecutive K-elements into the 8 digit tiles, 16 bytes (8 bf16) at
+// byte offset `off` of each tile.
+__device__ __forceinline__ void split8_at(const double (&v)[8], int cexp, uint8_t* tiles, int tile_bytes,
+                                          int off) {
+  uint32_t lo[8], hi[8], mg[8];
+  float ofs[8];
 #pragma unroll
-  for (int e = 0; e < 8; ++e) N[e] = fixed63(v[e], cexp, ng[e]);
-  const int off = row * 128 + ((g ^ (row & 7)) << 4);
+  for (int e = 0; e < 8; ++e) {
+    uint32_t neg;
+    const uint64_t N = fixed63(v[e], cexp, neg);
+    lo[e] = (uint32_t)N;
+    hi[e] = (uint32_t)(N >> 32);
+    mg[e] = 0x4B000000u | (neg << 31);
+    ofs[e] = __uint_as_float(0xCB000000u ^ (neg << 31));
+  }
 #pragma unroll
   for (int t = 0; t < kDigits; ++t) {
-    const int sh = 56 - 7 * t;
+    const uint32_t sel = 3u - (uint32_t)(t & 3);  // digit t is byte 7 - t of N
     uint32_t w[4];
 #pragma unroll
     for (int p = 0; p < 4; ++p) {
-      const uint32_t d0 = (uint32_t)(N[2 * p] >> sh) & 0x7Fu;
-      const uint32_t d1 = (uint32_t)(N[2 * p + 1] >> sh) & 0x7Fu;
-      w[p] = __byte_perm(digit_f32(d0, ng[2 * p]), digit_f32(d1, ng[2 * p + 1]), 0x7632);
+      const uint32_t x0 = t < 4 ? hi[2 * p] : lo[2 * p];
+      const uint32_t x1 = t < 4 ? hi[2 * p + 1] : lo[2 * p + 1];
+      w[p] = __byte_perm(digit_byte_f32(x0, mg[2 * p], ofs[2 * p], sel),
+                         digit_byte_f32(x1, mg[2 * p + 1], ofs[2 * p + 1], sel), 0x7632);
     }
     *reinterpret_cast<uint4*>(tiles + t * tile_bytes + off) = make_uint4(w[0], w[1], w[2], w[3]);
   }
 }
 
+// K-major, non-swizzled digit tiles with `kc` 16-byte chunks per 8-row group:
+// row `row`, chunk `g` lives at ((row / 8) kc + g) 128 + (row % 8) 16.
+__device__ __forceinline__ void split8_interleave(const double (&v)[8], int cexp, uint8_t* tiles,
+                                                  int tile_bytes, int row, int g, int kc) {
+  split8_at(v, cexp, tiles, tile_bytes, ((row >> 3) * kc + g) * 128 + (row & 7) * 16);
+}
+
+// 4- and 8-byte asynchronous global -> shared copies; `valid` = false writes
+// zeros and reads nothing.
+__device__ __forceinline__ void cp_async8(void* dst_smem, const void* src, bool valid) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(smem_u32(dst_smem)), "l"(src),
+               "r"(valid ? 8 : 0));
+}
+__device__ __forceinline__ void cp_async4(void* dst_smem, const void* src, bool valid) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(smem_u32(dst_smem)), "l"(src),
+               "r"(valid ? 4 : 0));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
   asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
@@ -106,21 +157,19 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;\n");
 }
 
-// Fold nine exact level sums L_l (|L_l| <= (l+1) 64 127^2 < (l+1) 2^20) into the
-// two int64 accumulators: hi += sum_{l<=4} L_l 2^(7(4-l)), lo += sum_{l>=5} L_l 2^(7(8-l)).
+// Fold the eight exact level sums L_l (|L_l| <= (l+1) 32 255^2 < 2^24) into two
+// int64 accumulators: hi += sum_{l<=3} L_l 2^(8(3-l)), lo += sum_{l>=4} L_l 2^(8(7-l)).
 __device__ __forceinline__ void fold_levels(const int32_t (&L)[kDigits], long long& hi, long long& lo) {
-  const int32_t c01 = (L[0] << 7) + L[1];
-  const int32_t c23 = (L[2] << 7) + L[3];
-  const int32_t c56 = (L[5] << 7) + L[6];
-  const int32_t c78 = (L[7] << 7) + L[8];
-  hi += ((long long)c01 << 21) + ((long long)c23 << 7) + (long long)L[4];
-  lo += ((long long)c56 << 14) + (long long)c78;
+  const int32_t c01 = (L[0] << 8) + L[1];  // |L0| <= 32 255^2 < 2^21: no overflow
+  const int32_t c23 = (L[2] << 8) + L[3];  // |L2| <= 3 32 255^2: 256 |L2| < 2^31
+  hi += ((long long)c01 << 16) + (long long)c23;
+  lo += ((long long)L[4] << 24) + ((long long)L[5] << 16) + ((long long)L[6] << 8) + (long long)L[7];
 }
 
-// The value 2^(E_a + E_b - 70) (hi 2^28 + lo), with E = cexp - 1022.
+// The value 2^(E_a + E_b - 70) (hi 2^32 + lo), with E = cexp - 1022.
 __device__ __forceinline__ double unfold(long long hi, long long lo, int cexp_a, int cexp_b) {
   const int sc = cexp_a + cexp_b - 2044;
-  return ldexp((double)hi, sc - 42) + ldexp((double)lo, sc - 70);
+  return ldexp((double)hi, sc - 38) + ldexp((double)lo, sc - 70);
 }
 
 // Tensor-memory allocation of NCOLS (power of two, 32..512) columns by one warp.

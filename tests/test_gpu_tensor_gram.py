@@ -1,12 +1,12 @@
 """The tensor-core Gram engine (bcgs_set_option(BCGS_OPT_GRAM_ENGINE, 2)).
 
-Each operand entry is split exactly into nine 7-bit digits relative to its
+Each operand entry is split exactly into eight 8-bit digits relative to its
 column maximum (error-free splitting, Ozaki et al. 2012) and digit pairs with
-t + u <= 8 are multiplied on the bf16 tensor cores with exact integer sums; the
-error of one product term is at most 2^-57.5 max|a_i| max|b_j| and each chunk
+t + u <= 7 are multiplied on the bf16 tensor cores with exact integer sums; the
+error of one product term is at most 2^-57.1 max|a_i| max|b_j| and each chunk
 partial is rounded once to FP64, then the partials are added in chunk order.
 Derived bound used below, per entry:
-    m max|a_i| max|b_j| 2^-57.5 + 2 (nchunks + 2) u (|A|^T |B|)_ij.
+    m max|a_i| max|b_j| 2^-57.1 + 2 (nchunks + 2) u (|A|^T |B|)_ij.
 """
 import numpy as np
 import pytest
@@ -56,7 +56,7 @@ def test_tensor_gram_parity(tensor, m, ka, kb):
     Co = oracle.gram([A], [B])
     amax_a = np.abs(A).max(axis=0)
     amax_b = np.abs(B).max(axis=0)
-    bound = m * np.outer(amax_a, amax_b) * 2.0 ** -57.5 + 2 * (nchunks(m) + 2) * U64 * (np.abs(A).T @ np.abs(B))
+    bound = m * np.outer(amax_a, amax_b) * 2.0 ** -57.1 + 2 * (nchunks(m) + 2) * U64 * (np.abs(A).T @ np.abs(B))
     assert np.all(np.abs(C1 - Co) <= bound)
 
 
@@ -120,7 +120,7 @@ def test_row_scaled_heavy_tails_meet_the_gates(cuda):
 def test_tensor_project_parity(tensor, m, c, s, with_t):
     """(V - Q C) T^{-1} with Q C on the tensor cores (row exponents of Q, column
     exponents of C) against the oracle; same derived FP64 tolerance as the
-    FP64-pipe kernel (the digit error c 2^-57.5 max|q_r| max|c_j| is below it)."""
+    FP64-pipe kernel (the digit error c 2^-57.1 max|q_r| max|c_j| is below it)."""
     rng = np.random.default_rng(m + c + s)
     V = rng.standard_normal((m, s))
     Q = np.linalg.qr(rng.standard_normal((m, c)))[0]
