@@ -17,7 +17,7 @@
 // (an explicit inverse would add a kappa(T) u residual); the division by
 // t_jj is a multiplication by its reciprocal, formed once per CTA.
 //
-// One CTA (512 threads) per 128-row tile: a first pass over the tile finds the
+// One CTA (256 threads) per 128-row tile: a first pass over the tile finds the
 // row exponents (the tile stays in L2 for the second pass); then, pipelined over
 // 32-column chunks of Q, cp.async stages chunk k+2, all threads split chunk k+1
 // (and the matching 32 rows of C) into K-major bf16 digit tiles while the tensor
@@ -31,7 +31,7 @@ namespace bcgs {
 namespace {
 using namespace tc;
 
-constexpr int kThreads = 512;
+constexpr int kThreads = 256;
 constexpr int kRows = 128;                // rows of Q per CTA (MMA M)
 constexpr int kKChunk = 32;               // columns of Q per MMA stage
 constexpr int kChunks = kKChunk / 8;      // 16-byte chunks of K per operand row in a digit tile
@@ -46,14 +46,23 @@ __device__ __forceinline__ unsigned long long abs_bits(double v) {
   return (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFull;
 }
 
+// Buffers of digit tiles: one for s <= 16 (two CTAs per SM overlap each other's
+// phases), two for s <= 32 (one CTA per SM pipelines its own chunks).
+template <int NBT>
+struct ProjCfg {
+  static constexpr int kBuf = NBT <= 16 ? 1 : 2;
+  static constexpr int kCtasPerSm = NBT <= 16 ? 2 : 1;
+};
+
 template <typename T, int NBT>
-__global__ void __launch_bounds__(kThreads, 1) proj_tc_kernel(ProjDesc d, DevStatus* st) {
+__global__ void __launch_bounds__(kThreads, ProjCfg<NBT>::kCtasPerSm) proj_tc_kernel(ProjDesc d, DevStatus* st) {
   static_assert(NBT == 16 || NBT == 32, "N tile");
+  constexpr int kBuf = ProjCfg<NBT>::kBuf;
   constexpr int kBTile = NBT * kKChunk * 2;            // bytes of one digit tile of C
   constexpr int kStage = kDigits * (kATile + kBTile);
-  constexpr int kTmemCols = kDigits * NBT <= 256 ? 256 : 512;
-  constexpr int kHalf = 8;                 // output columns per thread in the read-back
-  constexpr int kGroups = NBT / kHalf;      // column groups (warps w / 4 < kGroups read back)
+  constexpr int kTmemCols = kDigits * NBT <= 128 ? 128 : (kDigits * NBT <= 256 ? 256 : 512);
+  constexpr int kGroups = kThreads / 128;    // column groups (warp / 4)
+  constexpr int kHalf = NBT / kGroups;       // output columns per thread in the read-back
   if (block_failed(st)) return;
   extern __shared__ uint8_t dyn[];
   __shared__ __align__(8) uint64_t mbar;
@@ -62,13 +71,13 @@ __global__ void __launch_bounds__(kThreads, 1) proj_tc_kernel(ProjDesc d, DevSta
   __shared__ int s_cexp_b[NBT];
   __shared__ unsigned long long s_rowmax[kThreads / kRows][kRows];
   __shared__ double s_inv[32];
-  __shared__ double s_T[32 * 32];
+  __shared__ double s_T[NBT * NBT];
   __shared__ int s_bad;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   uint8_t* digits = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(dyn) + 1023) & ~uintptr_t(1023));
-  T* staging = reinterpret_cast<T*>(digits + 2 * kStage);       // kKChunk columns x kRows rows
-  double* P = reinterpret_cast<double*>(digits + 2 * kStage);   // reuses staging: kRows x NBT
+  T* staging = reinterpret_cast<T*>(digits + kBuf * kStage);       // kKChunk columns x kRows rows
+  double* P = reinterpret_cast<double*>(digits + kBuf * kStage);   // reuses staging: kRows x NBT
 
   const int s = d.s, c = d.q.ncols;
   const int64_t r0 = (int64_t)blockIdx.x * kRows;
@@ -119,7 +128,7 @@ __global__ void __launch_bounds__(kThreads, 1) proj_tc_kernel(ProjDesc d, DevSta
   }
   for (int e = tid; e < s * s; e += kThreads) {
     const int i = e % s, j = e / s;
-    s_T[i * 32 + j] = d.T ? d.T[i + (int64_t)j * d.ldt] : (i == j ? 1.0 : 0.0);
+    s_T[i * NBT + j] = d.T ? d.T[i + (int64_t)j * d.ldt] : (i == j ? 1.0 : 0.0);
   }
   if (warp == 0) tmem_alloc<kTmemCols>(&tmem_base_s);
   if (tid == 0) mbar_init(&mbar);
@@ -136,7 +145,7 @@ __global__ void __launch_bounds__(kThreads, 1) proj_tc_kernel(ProjDesc d, DevSta
   }
   for (int j = tid; j < s; j += kThreads) {
     if (s_cexp_b[j] == 0x7FF) s_bad = 1;
-    s_inv[j] = 1.0 / s_T[j * 32 + j];  // one division per diagonal entry per CTA
+    s_inv[j] = 1.0 / s_T[j * NBT + j];  // one division per diagonal entry per CTA
   }
   __syncthreads();
   const uint32_t tmem = tmem_base_s;
@@ -213,37 +222,8 @@ __global__ void __launch_bounds__(kThreads, 1) proj_tc_kernel(ProjDesc d, DevSta
   uint32_t phase = 0;
   bool timed_out = false;
   const int nchunks = bad ? 0 : (c + kKChunk - 1) / kKChunk;
-  if (nchunks > 0) {
-    stage_copy(0);
-    cp_async_wait_all();
-    __syncthreads();
-    split_chunk(0, 0);
-    __syncthreads();
-    if (nchunks > 1) stage_copy(kKChunk);
-    fence_smem_to_async();
-    tc_before_sync();
-    __syncthreads();
-    tc_after_sync();
-    if (tid == 0) issue_mma(0);
-  }
-  for (int kc = 0; kc < nchunks; ++kc) {
-    const bool more = kc + 1 < nchunks;
-    if (more) {
-      cp_async_wait_all();
-      __syncthreads();
-      split_chunk((kc + 1) & 1, (kc + 1) * kKChunk);
-      __syncthreads();
-      if (kc + 2 < nchunks) stage_copy((kc + 2) * kKChunk);
-    }
-    const bool ok = mbar_wait_bounded(&mbar, phase);
-    phase ^= 1u;
-    if (__syncthreads_or(!ok)) {
-      timed_out = true;
-      break;
-    }
-    tc_after_sync();
+  auto read_back = [&]() {
     const uint32_t lane_addr = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)my_j0;
-    if (reader) {
 #pragma unroll
     for (int g8 = 0; g8 < kHalf; g8 += 8) {
       int32_t L[8][kDigits];
@@ -257,12 +237,71 @@ __global__ void __launch_bounds__(kThreads, 1) proj_tc_kernel(ProjDesc d, DevSta
 #pragma unroll
       for (int j = 0; j < 8; ++j) fold_levels(L[j], hi[g8 + j], lo[g8 + j]);
     }
+  };
+  if constexpr (kBuf == 2) {
+    // chunk k's MMAs run while chunk k+1 is split; chunk k+2 is being staged
+    if (nchunks > 0) {
+      stage_copy(0);
+      cp_async_wait_all();
+      __syncthreads();
+      split_chunk(0, 0);
+      __syncthreads();
+      if (nchunks > 1) stage_copy(kKChunk);
+      fence_smem_to_async();
+      tc_before_sync();
+      __syncthreads();
+      tc_after_sync();
+      if (tid == 0) issue_mma(0);
     }
-    fence_smem_to_async();
-    tc_before_sync();
-    __syncthreads();
-    tc_after_sync();
-    if (more && tid == 0) issue_mma((kc + 1) & 1);
+    for (int kc = 0; kc < nchunks; ++kc) {
+      const bool more = kc + 1 < nchunks;
+      if (more) {
+        cp_async_wait_all();
+        __syncthreads();
+        split_chunk((kc + 1) & 1, (kc + 1) * kKChunk);
+        __syncthreads();
+        if (kc + 2 < nchunks) stage_copy((kc + 2) * kKChunk);
+      }
+      const bool ok = mbar_wait_bounded(&mbar, phase);
+      phase ^= 1u;
+      if (__syncthreads_or(!ok)) {
+        timed_out = true;
+        break;
+      }
+      tc_after_sync();
+      read_back();
+      fence_smem_to_async();
+      tc_before_sync();
+      __syncthreads();
+      tc_after_sync();
+      if (more && tid == 0) issue_mma((kc + 1) & 1);
+    }
+  } else {
+    // one buffer: chunk k+1 is staged while chunk k is split, multiplied and
+    // read back; the other CTA on the SM fills the gaps
+    if (nchunks > 0) stage_copy(0);
+    for (int kc = 0; kc < nchunks; ++kc) {
+      cp_async_wait_all();
+      __syncthreads();
+      split_chunk(0, kc * kKChunk);
+      __syncthreads();
+      if (kc + 1 < nchunks) stage_copy((kc + 1) * kKChunk);
+      fence_smem_to_async();
+      tc_before_sync();
+      __syncthreads();
+      tc_after_sync();
+      if (tid == 0) issue_mma(0);
+      const bool ok = mbar_wait_bounded(&mbar, phase);
+      phase ^= 1u;
+      if (__syncthreads_or(!ok)) {
+        timed_out = true;
+        break;
+      }
+      tc_after_sync();
+      read_back();
+      tc_before_sync();
+      __syncthreads();
+    }
   }
   cp_async_wait_all();
   __syncthreads();  // staging is free: reuse it for the products
@@ -289,7 +328,7 @@ __global__ void __launch_bounds__(kThreads, 1) proj_tc_kernel(ProjDesc d, DevSta
           double x = w[j];
 #pragma unroll
           for (int l = 0; l < NBT; ++l)
-            if (l < j) x = fma(-w[l], s_T[l * 32 + j], x);
+            if (l < j) x = fma(-w[l], s_T[l * NBT + j], x);
           w[j] = x * s_inv[j];
         }
       }
@@ -311,7 +350,7 @@ cudaError_t launch_t(const ProjDesc& d, DevStatus* st, cudaStream_t stream) {
   const int slot = prof_begin(stream);
 #define BCGS_PTC_CASE(NB)                                                                          \
   {                                                                                                \
-    const size_t smem = 1024 + 2 * (size_t)kDigits * (kATile + NB * kKChunk * 2) +               \
+    const size_t smem = 1024 + (size_t)ProjCfg<NB>::kBuf * kDigits * (kATile + NB * kKChunk * 2) + \
                         (size_t)kKChunk * kRows * 8;                                               \
     cudaError_t e = ensure_dyn_smem(proj_tc_kernel<T, NB>, smem);                                  \
     if (e != cudaSuccess) return e;                                                                \

@@ -85,11 +85,11 @@ __device__ __forceinline__ uint64_t fixed63(double a, int cexp, uint32_t& neg) {
   const uint64_t bits = (uint64_t)__double_as_longlong(a);
   neg = (uint32_t)(bits >> 63);
   const int e = (int)((bits >> 52) & 0x7FF);
-  if (e == 0) return 0;  // zero or subnormal
+  // N = mant 2^(e - cexp + 10): mant < 2^53, so mant 2^10 < 2^63, then shift right
+  // by cexp - e >= 0 (|a| <= max).  A zero exponent field (zero, subnormal) gives 0.
   const uint64_t mant = (bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-  const int sh = e - cexp + 10;  // <= 10 because |a| <= max
-  if (sh >= 0) return mant << (sh > 10 ? 10 : sh);
-  return -sh < 64 ? (mant >> (-sh)) : 0;
+  const int d = cexp - e;
+  return (e != 0 && d < 64) ? ((mant << 10) >> (d > 0 ? d : 0)) : 0ull;
 }
 
 // fp32 bits of the signed digit in byte `sel` of x: the byte is placed into the
