@@ -21,7 +21,8 @@ constexpr int kMaxS = 64;
 constexpr int kMaxN = 2048;
 
 struct Layout {
-  size_t status, S[2], Sd[2], Yd, Rt1, Rt2, G, G2, partial, amax, U, V, tsqr, total;
+  size_t status, S[2], Sd[2], Yd, Rt1, Rt2, G, G2, partial, amax, amaxQ, amaxU, rowmaxQ, U, V, tsqr,
+      total;
   int ldg;      // leading dimension of G, G2 (= n_max)
   int64_t ldu;  // leading dimension of U, V
   TsqrPlan tp;
@@ -53,6 +54,10 @@ void make_layout(int64_t m, int32_t n_max, int32_t s, int variant, int precision
   L->G2 = take((size_t)n_max * 2 * s * sizeof(double));
   L->partial = take(gram_partial_doubles(m, n_max, 2 * s) * sizeof(double));
   L->amax = take(((size_t)n_max + 4 * (size_t)s) * sizeof(unsigned long long));
+  // maxima kept by the writers: per column of Q, per column of U, per row of Q
+  L->amaxQ = take((size_t)n_max * sizeof(unsigned long long));
+  L->amaxU = take((size_t)s * sizeof(unsigned long long));
+  L->rowmaxQ = take((size_t)m * sizeof(unsigned long long));
   L->ldu = round_up(m, 64);
   L->U = take((size_t)L->ldu * s * esz);
   L->V = variant == BCGS_BCGSI_PLUS_P_1S ? off : take((size_t)L->ldu * s * esz);
@@ -61,12 +66,13 @@ void make_layout(int64_t m, int32_t n_max, int32_t s, int variant, int precision
   L->total = off;
 }
 
-Seg seg(const void* p, int64_t ld, int ncols, int fp32) {
+Seg seg(const void* p, int64_t ld, int ncols, int fp32, const unsigned long long* amax = nullptr) {
   Seg g;
   g.p = p;
   g.ld = ld;
   g.ncols = ncols;
   g.fp32 = fp32;
+  g.amax = amax;
   return g;
 }
 
@@ -115,9 +121,16 @@ struct bcgs_qr_s {
   void* V() { return ws + L.V; }
   // column block k (1-based) of Q
   char* Qblk(int k) { return Q + (size_t)(k - 1) * s * ldq * esz; }
-  Seg Qseg(int ncols) { return seg(Q, ldq, ncols, fp32); }
-  Seg Useg() { return seg(U(), L.ldu, s, fp32); }
+  unsigned long long* amaxQ() { return reinterpret_cast<unsigned long long*>(ws + L.amaxQ); }
+  unsigned long long* amaxU() { return reinterpret_cast<unsigned long long*>(ws + L.amaxU); }
+  unsigned long long* rowmaxQ() { return reinterpret_cast<unsigned long long*>(ws + L.rowmaxQ); }
+  // Q and U carry the column maxima their writers kept
+  Seg Qseg(int ncols) { return seg(Q, ldq, ncols, fp32, amaxQ()); }
+  Seg Useg() { return seg(U(), L.ldu, s, fp32, amaxU()); }
   Seg Vseg() { return seg(V(), L.ldu, s, fp32); }
+  // maxima to keep when writing block k of Q, or U
+  MaxOut Qmax(int k) { return MaxOut{amaxQ() + (size_t)(k - 1) * s, rowmaxQ()}; }
+  MaxOut Umax() { return MaxOut{amaxU(), nullptr}; }
 };
 
 namespace {
@@ -164,8 +177,11 @@ cudaError_t gram(bcgs_qr_s* h, std::initializer_list<Seg> A, std::initializer_li
 }
 
 cudaError_t project(bcgs_qr_s* h, Seg v, int c, const double* C, int ldc, const double* T,
-                    void* w, int64_t ldw) {
+                    void* w, int64_t ldw, MaxOut wmax = MaxOut{nullptr, nullptr}) {
   ProjDesc d;
+  memset(&d, 0, sizeof(d));
+  d.q_rowmax = h->rowmaxQ();
+  d.wmax = wmax;
   d.v = v;
   d.q = h->Qseg(c);
   d.C = C;
@@ -181,10 +197,12 @@ cudaError_t project(bcgs_qr_s* h, Seg v, int c, const double* C, int ldc, const 
   return launch_project(d, h->st(), h->stream);
 }
 
-cudaError_t tsqr(bcgs_qr_s* h, Seg a, void* q, int64_t ldq, double* R, int ldr, int block) {
+cudaError_t tsqr(bcgs_qr_s* h, Seg a, void* q, int64_t ldq, double* R, int ldr, int block,
+                 MaxOut qmax = MaxOut{nullptr, nullptr}) {
   return launch_tsqr(h->L.tp, a, q, ldq, h->fp32, R, ldr, h->buf(h->L.tsqr), h->st(), block,
-                     h->stream);
+                     h->stream, qmax);
 }
+cudaError_t zero_umax(bcgs_qr_s* h) { return launch_zero_u64(h->amaxU(), h->s, h->stream); }
 
 // Last-block branch of Alg. 2 (shared by BCGSI+P-1S and -2S):
 // [Y_{1:q-1,q}; Omega_q] = [Q_{q-1} U_q]^T U_q, Y_qq, R column block q, Q_q.
@@ -213,7 +231,7 @@ int finish_p(bcgs_qr_s* h) {
   t.block = q;
   t.ldsm = h->n_max;
   TRY(launch_tail_1s2s(t, h->st(), h->stream));
-  TRY(project(h, h->Useg(), c, G, ldg, h->buf(h->L.Yd), h->Qblk(q), h->ldq));
+  TRY(project(h, h->Useg(), c, G, ldg, h->buf(h->L.Yd), h->Qblk(q), h->ldq, h->Qmax(q)));
   return BCGS_OK;
 }
 
@@ -257,15 +275,16 @@ int step_p(bcgs_qr_s* h, const void* X, int64_t ldx) {
   t.ldsm = h->n_max;
   TRY(launch_tail_1s2s(t, h->st(), h->stream));
   // Q_k = (U_k - Q_{1:k-1} Y_{1:k-1,k}) Y_kk^{-1}
-  TRY(project(h, h->Useg(), c, G, ldg, h->buf(h->L.Yd), h->Qblk(k), h->ldq));
+  TRY(project(h, h->Useg(), c, G, ldg, h->buf(h->L.Yd), h->Qblk(k), h->ldq, h->Qmax(k)));
+  TRY(zero_umax(h));
   if (one_sync) {
     // U_{k+1} = (X_{k+1} - Q_{1:k} S_{1:k,k+1}) S_{k+1,k+1}^{-1}
     TRY(project(h, Xs, c + s, h->buf(h->L.S[nxt]), h->n_max, h->buf(h->L.Sd[nxt]), h->U(),
-                h->L.ldu));
+                h->L.ldu, h->Umax()));
   } else {
     // [U_{k+1}, S_{k+1,k+1}] = TSQR(X_{k+1} - Q_{1:k} S_{1:k,k+1})
     TRY(project(h, Xs, c + s, h->buf(h->L.S[nxt]), h->n_max, nullptr, h->V(), h->L.ldu));
-    TRY(tsqr(h, h->Vseg(), h->U(), h->L.ldu, h->buf(h->L.Sd[nxt]), s, k + 1));
+    TRY(tsqr(h, h->Vseg(), h->U(), h->L.ldu, h->buf(h->L.Sd[nxt]), s, k + 1, h->Umax()));
   }
   h->cur = nxt;
   return BCGS_OK;
@@ -278,7 +297,7 @@ int do_step(bcgs_qr_s* h, const void* X, int64_t ldx) {
   const int ldg = h->L.ldg;
   if (j == 1) {
     // [Q_1, R_11] = TSQR(X_1)
-    TRY(tsqr(h, Xs, h->Qblk(1), h->ldq, h->R, h->ldr, 1));
+    TRY(tsqr(h, Xs, h->Qblk(1), h->ldq, h->R, h->ldr, 1, h->Qmax(1)));
     return BCGS_OK;
   }
   switch (h->variant) {
@@ -288,11 +307,12 @@ int do_step(bcgs_qr_s* h, const void* X, int64_t ldx) {
       // S = Q_k^T X_{k+1};  [U, S_kk] = TSQR(X_{k+1} - Q_k S)
       TRY(gram(h, {h->Qseg(c)}, {Xs}, G));
       TRY(project(h, Xs, c, G, ldg, nullptr, h->V(), h->L.ldu));
-      TRY(tsqr(h, h->Vseg(), h->U(), h->L.ldu, h->buf(h->L.Rt1), s, j));
+      TRY(zero_umax(h));
+      TRY(tsqr(h, h->Vseg(), h->U(), h->L.ldu, h->buf(h->L.Rt1), s, j, h->Umax()));
       // Y = Q_k^T U;  [Q_{k+1}, Y_kk] = TSQR(U - Q_k Y)
       TRY(gram(h, {h->Qseg(c)}, {h->Useg()}, G2));
       TRY(project(h, h->Useg(), c, G2, ldg, nullptr, h->V(), h->L.ldu));
-      TRY(tsqr(h, h->Vseg(), h->Qblk(j), h->ldq, h->buf(h->L.Rt2), s, j));
+      TRY(tsqr(h, h->Vseg(), h->Qblk(j), h->ldq, h->buf(h->L.Rt2), s, j, h->Qmax(j)));
       TRY(launch_r_assemble(c, s, G, ldg, G2, ldg, h->buf(h->L.Rt1), h->buf(h->L.Rt2), h->R,
                             h->ldr, c, h->st(), h->stream));
       return BCGS_OK;
@@ -303,8 +323,9 @@ int do_step(bcgs_qr_s* h, const void* X, int64_t ldx) {
         TRY(gram(h, {h->Qseg(s), Xs}, {Xs}, G));
         TRY(launch_tail_start_1s(s, G, ldg, h->buf(h->L.S[h->cur]), h->n_max,
                                  h->buf(h->L.Sd[h->cur]), 2, h->st(), h->stream));
+        TRY(zero_umax(h));
         TRY(project(h, Xs, s, h->buf(h->L.S[h->cur]), h->n_max, h->buf(h->L.Sd[h->cur]), h->U(),
-                    h->L.ldu));
+                    h->L.ldu, h->Umax()));
         return BCGS_OK;
       }
       return step_p(h, X, ldx);
@@ -314,7 +335,8 @@ int do_step(bcgs_qr_s* h, const void* X, int64_t ldx) {
         TRY(gram(h, {h->Qseg(s)}, {Xs}, G));
         TRY(launch_copy_small(s, s, G, ldg, h->buf(h->L.S[h->cur]), h->n_max, h->st(), h->stream));
         TRY(project(h, Xs, s, G, ldg, nullptr, h->V(), h->L.ldu));
-        TRY(tsqr(h, h->Vseg(), h->U(), h->L.ldu, h->buf(h->L.Sd[h->cur]), s, 2));
+        TRY(zero_umax(h));
+        TRY(tsqr(h, h->Vseg(), h->U(), h->L.ldu, h->buf(h->L.Sd[h->cur]), s, 2, h->Umax()));
         return BCGS_OK;
       }
       return step_p(h, X, ldx);
@@ -352,6 +374,8 @@ int init_handle(bcgs_qr_s* h, int64_t m, int32_t n_max, int32_t s, int variant, 
   h->finished = 0;
   TRY(launch_reset_status(h->st(), h->stream));
   TRY(launch_zero_lower(n_max, R, ldr, h->stream));
+  TRY(launch_zero_u64(h->amaxQ(), n_max, h->stream));
+  TRY(launch_zero_u64(h->rowmaxQ(), m, h->stream));
   return BCGS_OK;
 }
 
@@ -598,6 +622,7 @@ int bcgs_project(int64_t m, int32_t c, int32_t s, const double* V, int64_t ldv, 
   if (c > 0 && (!Q || !C || ldq < m || ldc < c)) return BCGS_ERR_INVALID_ARG;
   if (T && ldt < s) return BCGS_ERR_INVALID_ARG;
   ProjDesc d;
+  memset(&d, 0, sizeof(d));
   d.v = seg(V, ldv, s, 0);
   d.q = seg(Q, ldq, c, 0);
   d.C = C;

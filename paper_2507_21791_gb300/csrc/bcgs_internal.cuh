@@ -45,7 +45,32 @@ struct Seg {
   int64_t ld;
   int32_t ncols;
   int32_t fp32;
+  // Optional per-column max |x| of this segment (bit patterns of non-negative
+  // doubles, unsigned order = value order), kept by the kernel that wrote it;
+  // null means the tensor-core Gram computes it.
+  const unsigned long long* amax;
 };
+
+// Running maxima of |x| over what a kernel writes, as above.  `col` gets one
+// atomicMax per written column (may be null); `row[r]` is raised to the max of
+// the written row r by the thread that owns the row (may be null).
+struct MaxOut {
+  unsigned long long* col;
+  unsigned long long* row;
+};
+
+__device__ __forceinline__ unsigned long long abs_bits64(double v) {
+  return (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFull;
+}
+__device__ __forceinline__ unsigned long long umax64(unsigned long long a, unsigned long long b) {
+  return a > b ? a : b;
+}
+// Warp-wide max of v; lane 0 adds it to *dst.
+__device__ __forceinline__ void warp_max_to(unsigned long long v, unsigned long long* dst) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = umax64(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if ((threadIdx.x & 31) == 0 && v != 0ull) atomicMax(dst, v);
+}
 
 constexpr int kMaxSegA = 4;
 constexpr int kMaxSegB = 3;
@@ -100,6 +125,10 @@ struct ProjDesc {
   const double* T; int32_t ldt;
   void* w; int64_t ldw; int32_t w_fp32;
   int64_t m; int32_t s;
+  // Optional max |q_rk| over k < c per row r of Q (bit patterns); null makes
+  // the tensor-core kernel find the row maxima itself.
+  const unsigned long long* q_rowmax;
+  MaxOut wmax;      // maxima of the written W
 };
 cudaError_t launch_project(const ProjDesc& d, DevStatus* st, cudaStream_t stream);
 // Tensor-core form (proj_tc.cu): s <= 32 and c >= 1.
@@ -123,7 +152,7 @@ struct TsqrPlan {
 void tsqr_plan(int64_t m, int32_t s, TsqrPlan* plan);
 cudaError_t launch_tsqr(const TsqrPlan& plan, Seg a, void* q, int64_t ldq, int32_t q_fp32,
                         double* R, int32_t ldr, double* work, DevStatus* st, int32_t block,
-                        cudaStream_t stream);
+                        cudaStream_t stream, MaxOut qmax = MaxOut{nullptr, nullptr});
 
 // Small FP64 tails (one CTA each); see tail.cu for the exact formulas.
 struct TailDesc {
@@ -153,6 +182,7 @@ cudaError_t launch_r_assemble(int32_t c, int32_t s, const double* S, int32_t lds
 cudaError_t launch_chol(int32_t s, const double* A, int32_t lda, double* R, int32_t ldr,
                         int32_t block, DevStatus* st, cudaStream_t stream);
 cudaError_t launch_zero_lower(int32_t n, double* R, int32_t ldr, cudaStream_t stream);
+cudaError_t launch_zero_u64(unsigned long long* p, int64_t n, cudaStream_t stream);
 cudaError_t launch_reset_status(DevStatus* st, cudaStream_t stream);
 
 // ---------------------------------------------------------------- instrumentation

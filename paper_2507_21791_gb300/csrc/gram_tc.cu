@@ -7,7 +7,8 @@
 // 59, 2012):
 //
 //   * every column i of A (and j of B) gets the exponent E_i with
-//     max_r |a_ri| < 2^E_i (a column-max pass precedes the kernel);
+//     max_r |a_ri| < 2^E_i (kept by the kernel that wrote the column, or found
+//     by a column-max pass before the kernel);
 //   * each entry becomes eight signed 8-bit digits relative to E_i, exact bf16
 //     integers (tc_common.cuh);
 //   * the 36 digit pairs t + u <= 7 run as bf16 tcgen05.mma with fp32
@@ -49,6 +50,9 @@ constexpr int kATile = kMTile * kBlockRows * 2;  // bytes of one digit tile of A
 struct TcCols {
   int32_t a_off[kMaxSegA + 1];
   int32_t b_off[kMaxSegB + 1];
+  // per-column max |x| of each segment: kept by its writer or computed here
+  const unsigned long long* a_amax[kMaxSegA];
+  const unsigned long long* b_amax[kMaxSegB];
 };
 
 template <int MAXS>
@@ -60,32 +64,19 @@ __device__ __forceinline__ int find_seg(const int32_t* off, int nseg, int col) {
   return s;
 }
 
-// Column max |x| of every column of A (first na) and B (next nb), kept as the
-// bit pattern of |x|: for non-negative doubles unsigned order is value order,
-// and Inf (0x7FF0...) and NaN (0x7FF8... and above) compare above every
-// finite value, so a non-finite column shows as exponent field 0x7FF.
+// Column max |x| of every column of one segment, kept as the bit pattern of
+// |x|: for non-negative doubles unsigned order is value order, and Inf
+// (0x7FF0...) and NaN (0x7FF8... and above) compare above every finite value,
+// so a non-finite column shows as exponent field 0x7FF.
 template <typename T>
-__global__ void colmax_kernel(GramDesc d, TcCols cm, unsigned long long* amax) {
+__global__ void colmax_kernel(Seg S, int64_t m, unsigned long long* amax) {
   const int col = blockIdx.y;
-  const bool is_a = col < d.na;
-  const int c = is_a ? col : col - d.na;
-  const int sg = is_a ? find_seg<kMaxSegA>(cm.a_off, d.nsa, c) : find_seg<kMaxSegB>(cm.b_off, d.nsb, c);
-  const Seg& S = is_a ? d.a[sg] : d.b[sg];
-  const int cc = c - (is_a ? cm.a_off[sg] : cm.b_off[sg]);
-  const int64_t off = (int64_t)cc * S.ld;
+  const int64_t off = (int64_t)col * S.ld;
   unsigned long long mx = 0ull;
-  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < d.m;
-       r += (int64_t)gridDim.x * blockDim.x) {
-    const unsigned long long bits =
-        (unsigned long long)__double_as_longlong(ld_elem<T>(S.p, off + r)) & 0x7FFFFFFFFFFFFFFFull;
-    mx = bits > mx ? bits : mx;
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const unsigned long long y = __shfl_xor_sync(0xffffffffu, mx, o);
-    mx = y > mx ? y : mx;
-  }
-  if ((threadIdx.x & 31) == 0) atomicMax(amax + col, mx);
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < m;
+       r += (int64_t)gridDim.x * blockDim.x)
+    mx = umax64(mx, abs_bits64(ld_elem<T>(S.p, off + r)));
+  warp_max_to(mx, amax + col);
 }
 
 __device__ __forceinline__ int cexp_of(unsigned long long b) { return (int)((b >> 52) & 0x7FF); }
@@ -131,9 +122,9 @@ gram_tc_kernel(GramDesc d, TcCols cm, const unsigned long long* __restrict__ ama
     const T* p = nullptr;
     if (i < ncol_a) {
       const int ca = col0 + i;
-      e = cexp_of(amax[ca]);
-      if (e == 0x7FF) s_bad = 1;
       const int sg = find_seg<kMaxSegA>(cm.a_off, d.nsa, ca);
+      e = cexp_of(cm.a_amax[sg][ca - cm.a_off[sg]]);
+      if (e == 0x7FF) s_bad = 1;
       p = reinterpret_cast<const T*>(d.a[sg].p) + (int64_t)(ca - cm.a_off[sg]) * d.a[sg].ld;
     }
     s_cexp_a[i] = e;
@@ -144,9 +135,9 @@ gram_tc_kernel(GramDesc d, TcCols cm, const unsigned long long* __restrict__ ama
     const T* p = nullptr;
     if (j < nb) {
       const int cb = jb0 + j;
-      e = cexp_of(amax[d.na + cb]);
-      if (e == 0x7FF) s_bad = 1;
       const int sg = find_seg<kMaxSegB>(cm.b_off, d.nsb, cb);
+      e = cexp_of(cm.b_amax[sg][cb - cm.b_off[sg]]);
+      if (e == 0x7FF) s_bad = 1;
       p = reinterpret_cast<const T*>(d.b[sg].p) + (int64_t)(cb - cm.b_off[sg]) * d.b[sg].ld;
     }
     s_cexp_b[j] = e;
@@ -299,9 +290,6 @@ gram_tc_kernel(GramDesc d, TcCols cm, const unsigned long long* __restrict__ ama
   if (warp == 0) tmem_dealloc<kTmemCols>(tmem);
 }
 
-__global__ void zero_u64_kernel(unsigned long long* p, int n) {
-  for (int i = threadIdx.x + blockIdx.x * blockDim.x; i < n; i += blockDim.x * gridDim.x) p[i] = 0ull;
-}
 
 template <typename T>
 cudaError_t launch_t(const GramDesc& d, double* partial, double* G, int ldg, unsigned long long* amax,
@@ -311,13 +299,40 @@ cudaError_t launch_t(const GramDesc& d, double* partial, double* G, int ldg, uns
   for (int k = 0; k < kMaxSegA; ++k) cm.a_off[k + 1] = cm.a_off[k] + (k < d.nsa ? d.a[k].ncols : 0);
   cm.b_off[0] = 0;
   for (int k = 0; k < kMaxSegB; ++k) cm.b_off[k + 1] = cm.b_off[k] + (k < d.nsb ? d.b[k].ncols : 0);
-  const int ncols = d.na + d.nb;
-  zero_u64_kernel<<<(ncols + 255) / 256, 256, 0, stream>>>(amax, ncols);
+  // column maxima: segments whose writer kept them are used as they are; the
+  // others (at most once per distinct segment) are computed into `amax`
   {
+    int64_t off = 0;
     int gx = (int)ceil_div(d.m, 256 * 64);
     if (gx > 16) gx = 16;
     if (gx < 1) gx = 1;
-    colmax_kernel<T><<<dim3(gx, ncols), 256, 0, stream>>>(d, cm, amax);
+    const Seg* segs[kMaxSegA + kMaxSegB];
+    const unsigned long long** dst[kMaxSegA + kMaxSegB];
+    int ns = 0;
+    for (int k = 0; k < d.nsa; ++k) { segs[ns] = &d.a[k]; dst[ns++] = &cm.a_amax[k]; }
+    for (int k = 0; k < d.nsb; ++k) { segs[ns] = &d.b[k]; dst[ns++] = &cm.b_amax[k]; }
+    for (int k = 0; k < ns; ++k) {
+      const Seg& S = *segs[k];
+      if (S.amax != nullptr) {
+        *dst[k] = S.amax;
+        continue;
+      }
+      const unsigned long long* same = nullptr;
+      for (int q = 0; q < k; ++q)
+        if (segs[q]->p == S.p && segs[q]->ld == S.ld && segs[q]->ncols >= S.ncols && segs[q]->amax == nullptr)
+          same = *dst[q];
+      if (same != nullptr) {
+        *dst[k] = same;
+        continue;
+      }
+      unsigned long long* out = amax + off;
+      off += S.ncols;
+      cudaError_t e = launch_zero_u64(out, S.ncols, stream);
+      if (e != cudaSuccess) return e;
+      colmax_kernel<T><<<dim3(gx, S.ncols), 256, 0, stream>>>(S, d.m, out);
+      note_launch(1);
+      *dst[k] = out;
+    }
   }
   const int slot = prof_begin(stream);
   const int nbt = d.nb <= 16 ? 16 : 32;
@@ -335,7 +350,7 @@ cudaError_t launch_t(const GramDesc& d, double* partial, double* G, int ldg, uns
 #undef BCGS_TC_CASE
   prof_end(slot, kProfGramPartial, stream, 2.0 * (double)d.m * d.na * d.nb,
            (double)d.m * (d.na + d.nb) * sizeof(T) + (double)d.nchunks * d.na * d.nb * 8.0);
-  note_launch(3);
+  note_launch(1);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   return launch_gram_reduce(partial, d.nchunks, d.na, d.nb, G, ldg, st, stream);

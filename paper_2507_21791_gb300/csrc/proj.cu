@@ -24,6 +24,15 @@ __device__ __forceinline__ void stv(void* p, int64_t i, double v) {
   reinterpret_cast<T*>(p)[i] = (T)v;
 }
 
+// Column maxima of the written W (one warp max and atomic per column and warp).
+template <typename T, int S>
+__device__ __forceinline__ void column_max_out(const ProjDesc& d, const double* w, bool live) {
+  if (d.wmax.col == nullptr) return;
+#pragma unroll
+  for (int j = 0; j < S; ++j)
+    if (j < d.s) warp_max_to(live ? abs_bits64((double)(T)w[j]) : 0ull, d.wmax.col + j);
+}
+
 template <typename T, int S>
 __global__ void __launch_bounds__(kProjThreads)
 project_kernel(ProjDesc d, const DevStatus* st) {
@@ -66,28 +75,38 @@ project_kernel(ProjDesc d, const DevStatus* st) {
     }
     __syncthreads();
   }
-  if (!live) return;
   double* w = acc;  // reuse the registers: w_j = v_j - (Q C)_j
-#pragma unroll
-  for (int j = 0; j < S; ++j) {
-    if (j < s) w[j] = ldv<T>(d.v.p, r + (int64_t)j * d.v.ld) - acc[j];
-  }
-  if (d.T != nullptr) {
-    // w T^{-1}: w_j = (v_j - sum_{l<j} w_l t_lj) / t_jj
+  if (live) {
 #pragma unroll
     for (int j = 0; j < S; ++j) {
-      if (j < s) {
-        double x = w[j];
+      if (j < s) w[j] = ldv<T>(d.v.p, r + (int64_t)j * d.v.ld) - acc[j];
+    }
+    if (d.T != nullptr) {
+      // w T^{-1}: w_j = (v_j - sum_{l<j} w_l t_lj) / t_jj
 #pragma unroll
-        for (int l = 0; l < S; ++l)
-          if (l < j) x = fma(-w[l], Ts[l * S + j], x);
-        w[j] = x / Ts[j * S + j];
+      for (int j = 0; j < S; ++j) {
+        if (j < s) {
+          double x = w[j];
+#pragma unroll
+          for (int l = 0; l < S; ++l)
+            if (l < j) x = fma(-w[l], Ts[l * S + j], x);
+          w[j] = x / Ts[j * S + j];
+        }
       }
     }
-  }
 #pragma unroll
-  for (int j = 0; j < S; ++j)
-    if (j < s) stv<T>(d.w, r + (int64_t)j * d.ldw, w[j]);
+    for (int j = 0; j < S; ++j)
+      if (j < s) stv<T>(d.w, r + (int64_t)j * d.ldw, w[j]);
+    if (d.wmax.row != nullptr) {
+      unsigned long long mx = 0ull;
+#pragma unroll
+      for (int j = 0; j < S; ++j)
+        if (j < s) mx = umax64(mx, abs_bits64((double)(T)w[j]));
+      d.wmax.row[r] = umax64(d.wmax.row[r], mx);
+    }
+  }
+  // every thread of the warp takes part in the column maxima (dead rows give 0)
+  column_max_out<T, S>(d, w, live);
 }
 
 template <typename T>

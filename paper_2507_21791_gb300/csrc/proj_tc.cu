@@ -101,9 +101,14 @@ __global__ void __launch_bounds__(kThreads, ProjCfg<NBT>::kCtasPerSm) proj_tc_ke
     }
     if (lane == 0) s_cexp_b[j] = (int)((mx >> 52) & 0x7FF);
   }
-  // exponents of the rows of the Q tile (two halves of the columns per row)
-  {
-    constexpr int kParts = kThreads / kRows;  // threads per row
+  // exponents of the rows of the Q tile: kept by the writers of Q, or found by
+  // a pass over the tile (which then stays in L2 for the chunks)
+  constexpr int kParts = kThreads / kRows;  // threads per row
+  if (d.q_rowmax != nullptr) {
+    for (int i = tid; i < kRows; i += kThreads) s_rowmax[0][i] = i < rows_here ? d.q_rowmax[r0 + i] : 0ull;
+    for (int h = 1; h < kParts; ++h)
+      for (int i = tid; i < kRows; i += kThreads) s_rowmax[h][i] = 0ull;
+  } else {
     const int i = tid & (kRows - 1), h = tid / kRows;
     unsigned long long mx = 0ull;
     if (i < rows_here) {
@@ -314,28 +319,45 @@ __global__ void __launch_bounds__(kThreads, ProjCfg<NBT>::kCtasPerSm) proj_tc_ke
     }
   }
   __syncthreads();
-  if (!bad && !timed_out && tid < kRows && tid < rows_here) {
+  if (!bad && !timed_out && tid < kRows) {  // warps 0..3, one row per thread
+    const bool live = tid < rows_here;
     const int64_t r = r0 + tid;
     double w[NBT];
 #pragma unroll
-    for (int j = 0; j < NBT; ++j)
-      if (j < s) w[j] = (double)__ldg(reinterpret_cast<const T*>(d.v.p) + r + (int64_t)j * d.v.ld) -
-                        P[tid * NBT + j];
-    if (d.T != nullptr) {
+    for (int j = 0; j < NBT; ++j) w[j] = 0.0;
+    if (live) {
 #pragma unroll
-      for (int j = 0; j < NBT; ++j) {
-        if (j < s) {
-          double x = w[j];
+      for (int j = 0; j < NBT; ++j)
+        if (j < s) w[j] = (double)__ldg(reinterpret_cast<const T*>(d.v.p) + r + (int64_t)j * d.v.ld) -
+                          P[tid * NBT + j];
+      if (d.T != nullptr) {
 #pragma unroll
-          for (int l = 0; l < NBT; ++l)
-            if (l < j) x = fma(-w[l], s_T[l * NBT + j], x);
-          w[j] = x * s_inv[j];
+        for (int j = 0; j < NBT; ++j) {
+          if (j < s) {
+            double x = w[j];
+#pragma unroll
+            for (int l = 0; l < NBT; ++l)
+              if (l < j) x = fma(-w[l], s_T[l * NBT + j], x);
+            w[j] = x * s_inv[j];
+          }
         }
       }
-    }
 #pragma unroll
-    for (int j = 0; j < NBT; ++j)
-      if (j < s) st_elem<T>(d.w, r + (int64_t)j * d.ldw, w[j]);
+      for (int j = 0; j < NBT; ++j)
+        if (j < s) st_elem<T>(d.w, r + (int64_t)j * d.ldw, w[j]);
+      if (d.wmax.row != nullptr) {
+        unsigned long long mx = 0ull;
+#pragma unroll
+        for (int j = 0; j < NBT; ++j)
+          if (j < s) mx = umax64(mx, abs_bits64((double)(T)w[j]));
+        d.wmax.row[r] = umax64(d.wmax.row[r], mx);
+      }
+    }
+    if (d.wmax.col != nullptr) {
+#pragma unroll
+      for (int j = 0; j < NBT; ++j)
+        if (j < s) warp_max_to(live ? abs_bits64((double)(T)w[j]) : 0ull, d.wmax.col + j);
+    }
   }
   if (timed_out && tid == 0) set_failure(st, BCGS_ERR_TIMEOUT, 0);
   tc_before_sync();

@@ -244,6 +244,11 @@ __global__ void zero_kernel(int32_t n, double* R, int32_t ldr) {
   }
 }
 
+__global__ void zero_u64_words(unsigned long long* p, int64_t n) {
+  for (int64_t i = threadIdx.x + (int64_t)blockIdx.x * blockDim.x; i < n; i += (int64_t)blockDim.x * gridDim.x)
+    p[i] = 0ull;
+}
+
 __global__ void reset_status_kernel(DevStatus* st) {
   if (threadIdx.x == 0) {
     st->code = 0;
@@ -310,6 +315,15 @@ cudaError_t launch_zero_lower(int32_t n, double* R, int32_t ldr, cudaStream_t st
   if (grid > 1024) grid = 1024;
   if (grid < 1) grid = 1;
   zero_kernel<<<grid, 256, 0, stream>>>(n, R, ldr);
+  note_launch(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_zero_u64(unsigned long long* p, int64_t n, cudaStream_t stream) {
+  if (n <= 0) return cudaSuccess;
+  int64_t grid = (n + 255) / 256;
+  if (grid > 1024) grid = 1024;
+  zero_u64_words<<<(unsigned)grid, 256, 0, stream>>>(p, n);
   note_launch(1);
   return cudaGetLastError();
 }

@@ -218,7 +218,7 @@ tsqr_node_apply(TsqrPlan p, int32_t level, double* work, const DevStatus* st) {
 
 template <typename T>
 __global__ void __launch_bounds__(kTsqrThreads)
-tsqr_leaf_apply(TsqrPlan p, const double* work, void* q, int64_t ldq, const DevStatus* st) {
+tsqr_leaf_apply(TsqrPlan p, const double* work, void* q, int64_t ldq, const DevStatus* st, MaxOut qmax) {
   if (failed(st)) return;
   extern __shared__ double sm[];
   __shared__ double tau[64];
@@ -243,11 +243,27 @@ tsqr_leaf_apply(TsqrPlan p, const double* work, void* q, int64_t ldq, const DevS
     const int r = e % mt, j = e / mt;
     if (r < rows_here) dst[row0 + r + (int64_t)j * ldq] = (T)E[e];
   }
+  // maxima of the written Q block (of the stored values)
+  if (qmax.col != nullptr) {
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    for (int j = warp; j < s; j += kWarps) {
+      unsigned long long mx = 0ull;
+      for (int r = lane; r < rows_here; r += 32) mx = umax64(mx, abs_bits64((double)(T)E[r + (size_t)j * mt]));
+      warp_max_to(mx, qmax.col + j);
+    }
+  }
+  if (qmax.row != nullptr) {
+    for (int r = threadIdx.x; r < rows_here; r += kTsqrThreads) {
+      unsigned long long mx = 0ull;
+      for (int j = 0; j < s; ++j) mx = umax64(mx, abs_bits64((double)(T)E[r + (size_t)j * mt]));
+      qmax.row[row0 + r] = umax64(qmax.row[row0 + r], mx);
+    }
+  }
 }
 
 template <typename T>
 cudaError_t launch_tsqr_t(const TsqrPlan& p, Seg a, void* q, int64_t ldq, double* R, int32_t ldr,
-                          double* work, DevStatus* st, int32_t block, cudaStream_t stream) {
+                          double* work, DevStatus* st, int32_t block, cudaStream_t stream, MaxOut qmax) {
   const size_t leaf_f = (size_t)p.mt * p.s * sizeof(double);
   const size_t node_f = (size_t)p.fan * p.s * p.s * sizeof(double);
   cudaError_t e;
@@ -265,7 +281,7 @@ cudaError_t launch_tsqr_t(const TsqrPlan& p, Seg a, void* q, int64_t ldq, double
     tsqr_node_factor<<<p.nodes[l], kTsqrThreads, node_f, stream>>>(p, l, work, R, ldr, st, block);
   for (int l = p.nlevels - 1; l >= 1; --l)
     tsqr_node_apply<<<p.nodes[l], kTsqrThreads, 2 * node_f, stream>>>(p, l, work, st);
-  tsqr_leaf_apply<T><<<p.nodes[0], kTsqrThreads, 2 * leaf_f, stream>>>(p, work, q, ldq, st);
+  tsqr_leaf_apply<T><<<p.nodes[0], kTsqrThreads, 2 * leaf_f, stream>>>(p, work, q, ldq, st, qmax);
   // Householder QR and explicit Q of the m x s block: 2 m s^2 flops each.
   prof_end(slot, kProfTsqr, stream, 4.0 * (double)p.m * p.s * p.s,
            2.0 * (double)p.m * p.s * sizeof(T) + 2.0 * (double)p.nodes[0] * p.mt * p.s * 8.0);
@@ -314,11 +330,11 @@ void tsqr_plan(int64_t m, int32_t s, TsqrPlan* p) {
 
 cudaError_t launch_tsqr(const TsqrPlan& p, Seg a, void* q, int64_t ldq, int32_t q_fp32, double* R,
                         int32_t ldr, double* work, DevStatus* st, int32_t block,
-                        cudaStream_t stream) {
+                        cudaStream_t stream, MaxOut qmax) {
   if (p.m <= 0) return cudaSuccess;
   (void)q_fp32;
-  return a.fp32 ? launch_tsqr_t<float>(p, a, q, ldq, R, ldr, work, st, block, stream)
-                : launch_tsqr_t<double>(p, a, q, ldq, R, ldr, work, st, block, stream);
+  return a.fp32 ? launch_tsqr_t<float>(p, a, q, ldq, R, ldr, work, st, block, stream, qmax)
+                : launch_tsqr_t<double>(p, a, q, ldq, R, ldr, work, st, block, stream, qmax);
 }
 
 }  // namespace bcgs
