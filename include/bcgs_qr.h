@@ -263,17 +263,19 @@ BCGS_API int64_t bcgs_get_option(int option);
 /* Number of CUDA kernels this library has launched since it was loaded. */
 BCGS_API int64_t bcgs_launch_count(void);
 
-/* enable != 0: bracket every Gram-partial, Gram-reduce, projection, TSQR and
- * tail launch with CUDA events recorded on its stream (cudaEventCreate is the
- * only resource used).  Adds a few microseconds per launch. */
+/* enable != 0: bracket every Gram-partial, Gram-reduce, projection, TSQR,
+ * tail and digit-store split launch with CUDA events recorded on its stream
+ * (cudaEventCreate is the only resource used).  Adds a few microseconds per
+ * launch. */
 BCGS_API int bcgs_profile_enable(int enable);
 
 /* Drop recorded events and totals. */
 BCGS_API int bcgs_profile_reset(void);
 
 /* Totals for a kernel class (0 Gram partial, 1 Gram reduce, 2 projection,
- * 3 TSQR, 4 tail) over the recorded launches: count, summed event time in ms,
- * algorithmic flops and bytes.  Waits for the recorded events. */
+ * 3 TSQR, 4 tail, 5 digit-store split of Q) over the recorded launches: count,
+ * summed event time in ms, algorithmic flops and bytes.  Waits for the recorded
+ * events. */
 BCGS_API int bcgs_profile_read(int kernel_class, int64_t* launches, double* total_ms,
                                double* flops, double* bytes);
 

@@ -69,7 +69,8 @@ SIGNATURES = [
                                          ctypes.POINTER(ctypes.c_double)]),
 ]
 
-PROFILE_CLASSES = {"gram_partial": 0, "gram_reduce": 1, "project": 2, "tsqr": 3, "tail": 4}
+PROFILE_CLASSES = {"gram_partial": 0, "gram_reduce": 1, "project": 2, "tsqr": 3, "tail": 4,
+                   "store_split": 5}
 
 _lib = None
 

@@ -4,6 +4,7 @@
 // Every step is a fixed sequence of stream-ordered launches; nothing here
 // synchronizes except bcgs_qr_sync / *_status.  All device memory is the
 // caller's: the workspace is carved into the buffers below.
+#include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -21,8 +22,9 @@ constexpr int kMaxS = 64;
 constexpr int kMaxN = 2048;
 
 struct Layout {
-  size_t status, S[2], Sd[2], Yd, Rt1, Rt2, G, G2, partial, amax, amaxQ, amaxU, rowmaxQ, U, V, tsqr,
-      total;
+  size_t status, S[2], Sd[2], Yd, Rt1, Rt2, G, G2, Bp, partial, amax, amaxQ, amaxU, rowmaxQ, U, V, tsqr,
+      qstore, total;
+  int store;    // the digit store of Q is part of the workspace
   int ldg;      // leading dimension of G, G2 (= n_max)
   int64_t ldu;  // leading dimension of U, V
   TsqrPlan tp;
@@ -34,7 +36,15 @@ bool valid_shape(int64_t m, int32_t n, int32_t s) {
   return s >= 1 && s <= kMaxS && m >= n && n >= s && n % s == 0 && n <= kMaxN;
 }
 
-void make_layout(int64_t m, int32_t n_max, int32_t s, int variant, int precision, Layout* L) {
+// The digit store of Q pays for itself where the projections run on the tensor
+// cores: FP64 storage, s <= 32, and the row count the engine option selects.
+bool want_store(int64_t m, int32_t s, int precision) {
+  const int e = gram_engine();
+  return precision == BCGS_FP64 && s <= 32 && e != 0 && (e == 2 || m >= gram_tc_min_rows());
+}
+
+void make_layout(int64_t m, int32_t n_max, int32_t s, int variant, int precision, int store,
+                 Layout* L) {
   const size_t esz = precision == BCGS_FP32_STORAGE ? 4 : 8;
   size_t off = 0;
   auto take = [&](size_t bytes) {
@@ -52,6 +62,8 @@ void make_layout(int64_t m, int32_t n_max, int32_t s, int variant, int precision
   L->ldg = n_max;
   L->G = take((size_t)n_max * 2 * s * sizeof(double));
   L->G2 = take((size_t)n_max * 2 * s * sizeof(double));
+  // (c + s) x 2s coefficients of the paired projection (BCGSI+P-1S / -2S)
+  L->Bp = variant == BCGS_BCGSI_PLUS ? off : take((size_t)n_max * 2 * s * sizeof(double));
   L->partial = take(gram_partial_doubles(m, n_max, 2 * s) * sizeof(double));
   L->amax = take(((size_t)n_max + 4 * (size_t)s) * sizeof(unsigned long long));
   // maxima kept by the writers: per column of Q, per column of U, per row of Q
@@ -63,6 +75,8 @@ void make_layout(int64_t m, int32_t n_max, int32_t s, int variant, int precision
   L->V = variant == BCGS_BCGSI_PLUS_P_1S ? off : take((size_t)L->ldu * s * esz);
   tsqr_plan(m, s, &L->tp);
   L->tsqr = take(L->tp.doubles * sizeof(double));
+  L->store = store;
+  L->qstore = store ? take(qstore_bytes(m, n_max)) : off;
   L->total = off;
 }
 
@@ -131,22 +145,35 @@ struct bcgs_qr_s {
   // maxima to keep when writing block k of Q, or U
   MaxOut Qmax(int k) { return MaxOut{amaxQ() + (size_t)(k - 1) * s, rowmaxQ()}; }
   MaxOut Umax() { return MaxOut{amaxU(), nullptr}; }
+  QStore qs() { return qstore_at(ws + L.qstore, m, n_max); }
 };
 
 namespace {
 
-int check(bcgs_qr_s* h, cudaError_t e) {
+// BCGS_DEBUG_SYNC=1 in the environment: synchronize after every launch and name
+// the launch that failed on stderr (diagnostics only; off by default).
+bool debug_sync() {
+  static const bool on = [] {
+    const char* v = getenv("BCGS_DEBUG_SYNC");
+    return v != nullptr && v[0] != '\0' && v[0] != '0';
+  }();
+  return on;
+}
+
+int check(bcgs_qr_s* h, cudaError_t e, const char* what, int line) {
+  if (e == cudaSuccess && debug_sync()) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) {
     h->last_cuda = e;
+    if (debug_sync()) fprintf(stderr, "bcgs: %s (bcgs_api.cu:%d): %s\n", what, line, cudaGetErrorString(e));
     return BCGS_ERR_CUDA;
   }
   return BCGS_OK;
 }
 
-#define TRY(expr)                      \
-  do {                                 \
-    int rc_ = check(h, (expr));        \
-    if (rc_ != BCGS_OK) return rc_;    \
+#define TRY(expr)                                    \
+  do {                                               \
+    int rc_ = check(h, (expr), #expr, __LINE__);     \
+    if (rc_ != BCGS_OK) return rc_;                  \
   } while (0)
 
 cudaError_t gram(bcgs_qr_s* h, std::initializer_list<Seg> A, std::initializer_list<Seg> B,
@@ -193,8 +220,30 @@ cudaError_t project(bcgs_qr_s* h, Seg v, int c, const double* C, int ldc, const 
   d.w_fp32 = h->fp32;
   d.m = h->m;
   d.s = h->s;
+  if (h->L.store && use_tensor_project(d) && project_store_supported(h->s, 1, 0)) {
+    StoreProjDesc p;
+    memset(&p, 0, sizeof(p));
+    p.qs = h->qs();
+    p.c = c;
+    p.B = C;
+    p.ldb = ldc;
+    p.s = h->s;
+    p.nouts = 1;
+    p.out[0] = ProjOut{reinterpret_cast<const double*>(v.p), v.ld, T, h->s, reinterpret_cast<double*>(w),
+                       ldw, wmax};
+    p.m = h->m;
+    p.block = h->j + 1;
+    return launch_project_store(p, h->st(), h->stream);
+  }
   if (use_tensor_project(d)) return launch_project_tc(d, h->st(), h->stream);
   return launch_project(d, h->st(), h->stream);
+}
+
+// Digits of the freshly written block column k of Q into the store.
+cudaError_t wrote_q(bcgs_qr_s* h, int k) {
+  if (!h->L.store) return cudaSuccess;
+  return launch_qsplit(h->qs(), reinterpret_cast<const double*>(h->Q), h->ldq, h->m, (k - 1) * h->s, h->s,
+                       h->st(), k, h->stream);
 }
 
 cudaError_t tsqr(bcgs_qr_s* h, Seg a, void* q, int64_t ldq, double* R, int ldr, int block,
@@ -230,8 +279,38 @@ int finish_p(bcgs_qr_s* h) {
   t.has_next = 0;
   t.block = q;
   t.ldsm = h->n_max;
+  ProjDesc probe;
+  memset(&probe, 0, sizeof(probe));
+  probe.q = h->Qseg(c);
+  probe.m = h->m;
+  probe.s = s;
+  const bool folded = h->L.store && use_tensor_project(probe) && project_store_supported(s, 1, s);
+  if (folded) {
+    t.Bpair = h->buf(h->L.Bp);
+    t.ldb = h->n_max;
+  }
   TRY(launch_tail_1s2s(t, h->st(), h->stream));
-  TRY(project(h, h->Useg(), c, G, ldg, h->buf(h->L.Yd), h->Qblk(q), h->ldq, h->Qmax(q)));
+  if (folded) {
+    // Q_q = [Q_{1:q-1} U_q] [-Y Y_qq^{-1}; Y_qq^{-1}] from the digit store
+    StoreProjDesc p;
+    memset(&p, 0, sizeof(p));
+    p.qs = h->qs();
+    p.c = c;
+    p.ext = reinterpret_cast<const double*>(h->U());
+    p.ld_ext = h->L.ldu;
+    p.next = s;
+    p.B = h->buf(h->L.Bp);
+    p.ldb = h->n_max;
+    p.s = s;
+    p.nouts = 1;
+    p.out[0] = ProjOut{nullptr, 0, nullptr, 0, reinterpret_cast<double*>(h->Qblk(q)), h->ldq, h->Qmax(q)};
+    p.m = h->m;
+    p.block = q;
+    TRY(launch_project_store(p, h->st(), h->stream));
+  } else {
+    TRY(project(h, h->Useg(), c, G, ldg, h->buf(h->L.Yd), h->Qblk(q), h->ldq, h->Qmax(q)));
+  }
+  TRY(wrote_q(h, q));
   return BCGS_OK;
 }
 
@@ -273,9 +352,51 @@ int step_p(bcgs_qr_s* h, const void* X, int64_t ldx) {
   t.chol_next = one_sync ? 1 : 0;
   t.block = k;
   t.ldsm = h->n_max;
+  // Paired projection from the digit store: Q_k and the next block in one pass
+  // over [Q_{1:k-1} U_k] (qstore.cu); the tail supplies its coefficients.
+  ProjDesc probe;
+  memset(&probe, 0, sizeof(probe));
+  probe.q = h->Qseg(c);
+  probe.m = h->m;
+  probe.s = s;
+  const bool paired = h->L.store && use_tensor_project(probe) && project_store_supported(s, 2, s);
+  if (paired) {
+    t.Bpair = h->buf(h->L.Bp);
+    t.ldb = h->n_max;
+  }
   TRY(launch_tail_1s2s(t, h->st(), h->stream));
+  if (paired) {
+    TRY(zero_umax(h));
+    StoreProjDesc p;
+    memset(&p, 0, sizeof(p));
+    p.qs = h->qs();
+    p.c = c;
+    p.ext = reinterpret_cast<const double*>(h->U());
+    p.ld_ext = h->L.ldu;
+    p.next = s;
+    p.B = h->buf(h->L.Bp);
+    p.ldb = h->n_max;
+    p.s = s;
+    p.nouts = 2;
+    // Q_k from the folded coefficients [-Y Y_kk^{-1}; Y_kk^{-1}]: no FP64 epilogue
+    p.out[0] = ProjOut{nullptr, 0, nullptr, 0, reinterpret_cast<double*>(h->Qblk(k)), h->ldq, h->Qmax(k)};
+    if (one_sync)
+      p.out[1] = ProjOut{reinterpret_cast<const double*>(X), ldx, h->buf(h->L.Sd[nxt]), s,
+                         reinterpret_cast<double*>(h->U()), h->L.ldu, h->Umax()};
+    else
+      p.out[1] = ProjOut{reinterpret_cast<const double*>(X), ldx, nullptr, s,
+                         reinterpret_cast<double*>(h->V()), h->L.ldu, MaxOut{nullptr, nullptr}};
+    p.m = h->m;
+    p.block = k;
+    TRY(launch_project_store(p, h->st(), h->stream));
+    TRY(wrote_q(h, k));
+    if (!one_sync) TRY(tsqr(h, h->Vseg(), h->U(), h->L.ldu, h->buf(h->L.Sd[nxt]), s, k + 1, h->Umax()));
+    h->cur = nxt;
+    return BCGS_OK;
+  }
   // Q_k = (U_k - Q_{1:k-1} Y_{1:k-1,k}) Y_kk^{-1}
   TRY(project(h, h->Useg(), c, G, ldg, h->buf(h->L.Yd), h->Qblk(k), h->ldq, h->Qmax(k)));
+  TRY(wrote_q(h, k));
   TRY(zero_umax(h));
   if (one_sync) {
     // U_{k+1} = (X_{k+1} - Q_{1:k} S_{1:k,k+1}) S_{k+1,k+1}^{-1}
@@ -298,6 +419,7 @@ int do_step(bcgs_qr_s* h, const void* X, int64_t ldx) {
   if (j == 1) {
     // [Q_1, R_11] = TSQR(X_1)
     TRY(tsqr(h, Xs, h->Qblk(1), h->ldq, h->R, h->ldr, 1, h->Qmax(1)));
+    TRY(wrote_q(h, 1));
     return BCGS_OK;
   }
   switch (h->variant) {
@@ -313,6 +435,7 @@ int do_step(bcgs_qr_s* h, const void* X, int64_t ldx) {
       TRY(gram(h, {h->Qseg(c)}, {h->Useg()}, G2));
       TRY(project(h, h->Useg(), c, G2, ldg, nullptr, h->V(), h->L.ldu));
       TRY(tsqr(h, h->Vseg(), h->Qblk(j), h->ldq, h->buf(h->L.Rt2), s, j, h->Qmax(j)));
+      TRY(wrote_q(h, j));
       TRY(launch_r_assemble(c, s, G, ldg, G2, ldg, h->buf(h->L.Rt1), h->buf(h->L.Rt2), h->R,
                             h->ldr, c, h->st(), h->stream));
       return BCGS_OK;
@@ -353,7 +476,9 @@ int init_handle(bcgs_qr_s* h, int64_t m, int32_t n_max, int32_t s, int variant, 
   if (ldq < m || ldr < n_max) return BCGS_ERR_INVALID_ARG;
   if (((uintptr_t)workspace) % 256 != 0) return BCGS_ERR_WORKSPACE;
   memset(h, 0, sizeof(*h));
-  make_layout(m, n_max, s, variant, precision, &h->L);
+  make_layout(m, n_max, s, variant, precision, want_store(m, s, precision), &h->L);
+  if (ws_bytes < h->L.total && h->L.store)  // sized without the store: run without it
+    make_layout(m, n_max, s, variant, precision, 0, &h->L);
   if (ws_bytes < h->L.total) return BCGS_ERR_WORKSPACE;
   h->m = m;
   h->n_max = n_max;
@@ -489,7 +614,7 @@ int bcgs_qr_workspace_size(int64_t m, int32_t n_max, int32_t s, int variant, int
   if (bytes == nullptr || !valid_shape(m, n_max, s)) return BCGS_ERR_INVALID_ARG;
   if (variant < 0 || variant > 2 || precision < 0 || precision > 1) return BCGS_ERR_INVALID_ARG;
   Layout L;
-  make_layout(m, n_max, s, variant, precision, &L);
+  make_layout(m, n_max, s, variant, precision, want_store(m, s, precision), &L);
   *bytes = L.total;
   return BCGS_OK;
 }

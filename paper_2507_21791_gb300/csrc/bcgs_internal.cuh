@@ -136,6 +136,57 @@ bool project_tc_supported(const ProjDesc& d);
 cudaError_t launch_project_tc(const ProjDesc& d, DevStatus* st, cudaStream_t stream);
 bool use_tensor_project(const ProjDesc& d);
 
+// ---------------------------------------------------------------- resident digit store of Q
+// With FP64 storage, Q is kept a second time as exact digit tiles ready for the
+// tensor cores (qstore.cu).  Per 128-row block b and column k: the exponent field
+// exps[b][k] of max_{i in b} |q_ik|, and the eight balanced 8-bit digits
+// (tc_common.cuh) of every q_ik relative to it, as f16.  Tiles of 128 rows x 128
+// columns per (b, column group G), 256 KB each:
+//   [t: digit 0..7][g: 8-column group 0..15][r: 8-row group 0..15][8 rows x 16 B]
+// so a 16-column chunk of one digit is 4 KB of contiguous bytes.
+constexpr int kStoreRows = 128;
+constexpr int kStoreCols = 128;
+constexpr size_t kStoreTileBytes = (size_t)8 * kStoreRows * kStoreCols * 2;
+struct QStore {
+  uint8_t* dig;
+  int32_t* exps;
+  int64_t nblk;      // row blocks
+  int32_t ngroups;   // column groups
+  int32_t ld_exp;    // ngroups * 128
+};
+size_t qstore_bytes(int64_t m, int32_t n_max);
+QStore qstore_at(void* base, int64_t m, int32_t n_max);
+// Digits and exponents of columns [k0, k0 + s) of Q (FP64, ld ldq).  The rest of
+// the 16-column chunk holding column k0 + s - 1 is written as zeros, and columns
+// of the 8-column group before k0 are rewritten from Q (same exponents).
+cudaError_t launch_qsplit(const QStore& qs, const double* Q, int64_t ldq, int64_t m, int32_t k0,
+                          int32_t s, DevStatus* st, int32_t block, cudaStream_t stream);
+
+// One output of the store projection: W = (V - P_o) T^{-1}; V null means W = P_o T^{-1},
+// T null means no solve.
+struct ProjOut {
+  const double* v; int64_t ldv;
+  const double* T; int32_t ldt;
+  double* w; int64_t ldw;
+  MaxOut wmax;
+};
+// P = [Q_{1:c} E] B with Q from the store, the optional extra segment E (m x
+// next, FP64, split on the fly) and B ((c + next) x nouts s, column-major, ldb);
+// output o takes columns [o s, o s + s) of P; only the last output may have a
+// triangle T.  Every V_o is read before any W_o is written, so W_1 may overwrite
+// E or V_0.
+struct StoreProjDesc {
+  QStore qs; int32_t c;
+  const double* ext; int64_t ld_ext; int32_t next;
+  const double* B; int32_t ldb;
+  int32_t s, nouts;
+  ProjOut out[2];
+  int64_t m;
+  int32_t block;
+};
+bool project_store_supported(int32_t s, int32_t nouts, int32_t next);
+cudaError_t launch_project_store(const StoreProjDesc& d, DevStatus* st, cudaStream_t stream);
+
 // TSQR of an m x s block.
 struct TsqrPlan {
   int64_t m; int32_t s;
@@ -167,6 +218,11 @@ struct TailDesc {
   double* R; int32_t ldr; int32_t r_row0, r_col0; // R block column destination
   int32_t has_next, chol_next, block;
   int32_t ldsm;          // leading dim of S/Y buffers (n_max)
+  // Optional: coefficients of the projections from the digit store, (c+s) rows,
+  // leading dimension ldb.  Columns [0, s): [-Y Y_kk^{-1}; Y_kk^{-1}], so that
+  // Q_k = [Q_{1:k-1} U_k] B[:, 0:s].  With has_next also columns [s, 2s):
+  // [Z - Y M; M] with M = Y_kk^{-1} W (W the bottom s rows of S_{1:k,k+1}).
+  double* Bpair; int32_t ldb;
 };
 cudaError_t launch_tail_1s2s(const TailDesc& d, DevStatus* st, cudaStream_t stream);
 // S22 = chol(T2 - S12^T S12) from the startup Gram [Q1 X2]^T X2 (1S only).
@@ -188,7 +244,7 @@ cudaError_t launch_reset_status(DevStatus* st, cudaStream_t stream);
 // ---------------------------------------------------------------- instrumentation
 // Kernel classes timed by the optional profiler (bcgs_profile_read).
 enum ProfClass { kProfGramPartial = 0, kProfGramReduce = 1, kProfProject = 2, kProfTsqr = 3,
-                 kProfTail = 4, kProfClasses = 5 };
+                 kProfTail = 4, kProfStoreSplit = 5, kProfClasses = 6 };
 void note_launch(int n);
 int prof_begin(cudaStream_t stream);  // -1 when profiling is off
 void prof_end(int slot, int cls, cudaStream_t stream, double flops, double bytes);

@@ -144,8 +144,7 @@ cudaError_t launch_gram_t(const GramDesc& d, double* partial, double* G, int ldg
 #define BCGS_GRAM_CASE(NPT)                                                                    \
   if (npt_need <= NPT) {                                                                       \
     auto kern = gram_partial_kernel<T, NPT>;                                                   \
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,    \
-                                         (int)smem);                                           \
+    cudaError_t e = ensure_dyn_smem(kern, smem);                                               \
     if (e != cudaSuccess) return e;                                                            \
     kern<<<grid, kThreads, smem, stream>>>(d, cm, na_g, tr, partial, st);                      \
   } else

@@ -48,27 +48,37 @@ namespace {
 struct SmemEntry {
   const void* kernel;
   int dev;
-  size_t bytes;
+  size_t bytes;  // dynamic shared memory the kernel may launch with now
 };
 std::mutex g_smem_mu;
 std::vector<SmemEntry> g_smem;
 }  // namespace
 
+// Without the opt-in a kernel may take 48 KB minus its static shared memory of
+// dynamic shared memory; above that, raise MaxDynamicSharedMemorySize once.
 cudaError_t ensure_dyn_smem_ptr(const void* kernel, size_t bytes) {
-  if (bytes <= 48 * 1024) return cudaSuccess;
+  if (bytes == 0) return cudaSuccess;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) dev = -1;
   std::lock_guard<std::mutex> lk(g_smem_mu);
-  for (auto& e : g_smem)
-    if (e.kernel == kernel && e.dev == dev && e.bytes >= bytes) return cudaSuccess;
-  cudaError_t err = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-  if (err != cudaSuccess) return err;
+  SmemEntry* hit = nullptr;
   for (auto& e : g_smem)
     if (e.kernel == kernel && e.dev == dev) {
-      e.bytes = bytes;
-      return cudaSuccess;
+      hit = &e;
+      break;
     }
-  g_smem.push_back({kernel, dev, bytes});
+  if (hit == nullptr) {
+    cudaFuncAttributes a;
+    cudaError_t err = cudaFuncGetAttributes(&a, kernel);
+    if (err != cudaSuccess) return err;
+    const size_t def = a.sharedSizeBytes < 48 * 1024 ? 48 * 1024 - a.sharedSizeBytes : 0;
+    g_smem.push_back({kernel, dev, def});
+    hit = &g_smem.back();
+  }
+  if (hit->bytes >= bytes) return cudaSuccess;
+  cudaError_t err = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (err != cudaSuccess) return err;
+  hit->bytes = bytes;
   return cudaSuccess;
 }
 

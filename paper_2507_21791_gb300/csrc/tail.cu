@@ -110,6 +110,33 @@ __device__ void tail_1s2s_body(const TailDesc& d, DevStatus* st, double* dyn) {
     }
     d.R[(d.r_row0 + i) + (size_t)(d.r_col0 + j) * d.ldr] = v;
   }
+  if (d.Bpair != nullptr) {
+    // Q_k = (U_k - Q_{1:k-1} Y) Y_kk^{-1} = [Q_{1:k-1} U_k] [-Y Yi; Yi], Yi = Y_kk^{-1}
+    // (upper triangular, by back substitution; Y_kk is close to the identity
+    // once U_k has been normalized, so the explicit inverse costs no accuracy).
+    __syncthreads();
+    double* Yi = Sd;  // S_kk is no longer needed
+    for (int j = threadIdx.x; j < s; j += blockDim.x) {
+      for (int i = s - 1; i >= 0; --i) {
+        double x = i == j ? 1.0 : 0.0;
+        for (int l = i + 1; l <= j; ++l) x = fma(-Yd[i + l * s], Yi[l + j * s], x);
+        Yi[i + j * s] = i > j ? 0.0 : x / Yd[i + i * s];
+      }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < (c + s) * s; e += blockDim.x) {
+      const int i = e % (c + s), j = e / (c + s);
+      double v;
+      if (i < c) {
+        double t = 0.0;
+        for (int l = 0; l <= j; ++l) t = fma(Yg[i + (size_t)l * ldg], Yi[l + j * s], t);
+        v = -t;
+      } else {
+        v = Yi[(i - c) + j * s];
+      }
+      d.Bpair[i + (size_t)j * d.ldb] = v;
+    }
+  }
   if (!d.has_next) return;
   // S_{1:k,k+1} = [Z; Y_kk^{-T} (P - Y^T Z)]
   small_tn(c, s, Yg, ldg, Zg, ldg, Ms);
@@ -131,6 +158,35 @@ __device__ void tail_1s2s_body(const TailDesc& d, DevStatus* st, double* dyn) {
   for (int e = threadIdx.x; e < (c + s) * s; e += blockDim.x) {
     const int i = e % (c + s), j = e / (c + s);
     d.S_next[i + (size_t)j * d.ldsm] = i < c ? Zg[i + (size_t)j * ldg] : Wb[(i - c) + j * s];
+  }
+  if (d.Bpair != nullptr) {
+    // Coefficients of the paired projection (Q_k and the next block in one pass
+    // over [Q_{1:k-1} U_k]): Q_{1:k} S_{1:k,k+1} = Q_{1:k-1} Z + Q_k W
+    //   = Q_{1:k-1} (Z - Y M) + U_k M  with  M = Y_kk^{-1} W, since
+    // Q_k = (U_k - Q_{1:k-1} Y) Y_kk^{-1}.
+    __syncthreads();
+    // M = Y_kk^{-1} W by back substitution (into Ms), column by column
+    for (int j = threadIdx.x; j < s; j += blockDim.x) {
+      for (int i = s - 1; i >= 0; --i) {
+        double x = Wb[i + j * s];
+        for (int l = i + 1; l < s; ++l) x = fma(-Yd[i + l * s], Ms[l + j * s], x);
+        Ms[i + j * s] = x / Yd[i + i * s];
+      }
+    }
+    __syncthreads();
+    double* B = d.Bpair + (size_t)s * d.ldb;
+    for (int e = threadIdx.x; e < (c + s) * s; e += blockDim.x) {
+      const int i = e % (c + s), jj = e / (c + s);
+      double v;
+      if (i < c) {
+        double t = 0.0;
+        for (int l = 0; l < s; ++l) t = fma(Yg[i + (size_t)l * ldg], Ms[l + jj * s], t);
+        v = Zg[i + (size_t)jj * ldg] - t;
+      } else {
+        v = Ms[(i - c) + jj * s];
+      }
+      B[i + (size_t)jj * d.ldb] = v;
+    }
   }
   if (!d.chol_next) return;
   __syncthreads();

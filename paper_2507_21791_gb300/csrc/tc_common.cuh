@@ -172,6 +172,141 @@ __device__ __forceinline__ double unfold(long long hi, long long lo, int cexp_a,
   return ldexp((double)hi, sc - 38) + ldexp((double)lo, sc - 70);
 }
 
+// ---------------------------------------------------------------- balanced digits
+// Second digit form, used by the resident digit store of Q (qstore.cu): a is
+// written as the signed integer N = trunc(a 2^(62 - E)) (|N| < 2^62), and N is
+// expanded in balanced base-256 digits d_t in [-128, 127]:
+//     N = sum_t d_t 2^(56 - 8t),   d_t = byte_(7-t)(N + 0x8080808080808080) - 128,
+// (adding 128 to every byte turns the balanced expansion into the unsigned one;
+// |N| < 2^62 keeps the sum clear of the wrap-around).  |d_t| <= 128 (|d_0| <= 64),
+// so a digit product is at most 2^14 and a level of at most eight pairs summed
+// over 128 K-values is at most 7 2^21 < 2^24: exact in fp32 for 128 K-values
+// between read-backs.  Digits are stored as f16 (integers up to 2048 are exact).
+
+// N + 0x8080808080808080 for a with biased exponent `e`, magnitude bits `mant`
+// (implicit bit included) and sign `neg`, relative to the exponent field `cexp`
+// (cexp >= e; |a| < 2^(cexp - 1022)): N = (mant 2^9) >> (cexp - e).
+__device__ __forceinline__ uint64_t fixed62_offset(uint64_t mant, int e, int cexp, uint32_t neg) {
+  const int d = cexp - e;
+  const uint64_t mag = (e > 0 && d < 63) ? ((mant << 9) >> (d > 0 ? d : 0)) : 0ull;
+  const uint64_t n = neg ? (0ull - mag) : mag;
+  return n + 0x8080808080808080ull;
+}
+__device__ __forceinline__ uint64_t fixed62_offset(double a, int cexp) {
+  const uint64_t bits = (uint64_t)__double_as_longlong(a);
+  return fixed62_offset((bits & 0xFFFFFFFFFFFFFull) | (1ull << 52), (int)((bits >> 52) & 0x7FF), cexp,
+                        (uint32_t)(bits >> 63));
+}
+
+// f16x2 of two offset-binary digit bytes of `w` (bytes 0 and 2 for SEL 0x4240,
+// bytes 1 and 3 for SEL 0x4341): each byte b becomes the low mantissa bits of
+// the f16 1024 + b, and 1152 = 1024 + 128 is taken off (exact).
+template <uint32_t SEL>
+__device__ __forceinline__ uint32_t f16x2_digits(uint32_t w) {
+  const uint32_t h = __byte_perm(w, 0x64646464u, SEL);
+  uint32_t r;
+  asm("sub.rn.f16x2 %0, %1, %2;\n" : "=r"(r) : "r"(h), "r"(0x64806480u));
+  return r;
+}
+
+// For two consecutive K-elements x, y with offset words (hi, lo) = (xh, xl) and
+// (yh, yl): out[t] = f16x2 (digit t of x, digit t of y), t = 0..7; digit t is
+// byte 3 - t of hi for t < 4 and byte 7 - t of lo otherwise.
+__device__ __forceinline__ void digits_pair_f16(uint32_t xh, uint32_t xl, uint32_t yh, uint32_t yl,
+                                                uint32_t (&out)[8]) {
+  const uint32_t h3 = __byte_perm(xh, yh, 0x6723u);  // [x.b3, x.b2, y.b3, y.b2]
+  const uint32_t h1 = __byte_perm(xh, yh, 0x4501u);  // [x.b1, x.b0, y.b1, y.b0]
+  const uint32_t l3 = __byte_perm(xl, yl, 0x6723u);
+  const uint32_t l1 = __byte_perm(xl, yl, 0x4501u);
+  out[0] = f16x2_digits<0x4240u>(h3);
+  out[1] = f16x2_digits<0x4341u>(h3);
+  out[2] = f16x2_digits<0x4240u>(h1);
+  out[3] = f16x2_digits<0x4341u>(h1);
+  out[4] = f16x2_digits<0x4240u>(l3);
+  out[5] = f16x2_digits<0x4341u>(l3);
+  out[6] = f16x2_digits<0x4240u>(l1);
+  out[7] = f16x2_digits<0x4341u>(l1);
+}
+
+// Instruction descriptor of kind::f16 with f16 A and B (fp32 D, both K-major).
+__host__ __device__ constexpr uint32_t idesc_f16(int M, int N) {
+  return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// Bulk (non-tensor) global -> shared copy completing on an mbarrier's
+// transaction count; sizes and addresses multiples of 16 bytes.
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* mbar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(mbar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst_smem, const void* src, uint32_t bytes, uint64_t* mbar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+          smem_u32(dst_smem)),
+      "l"(src), "r"(bytes), "r"(smem_u32(mbar))
+      : "memory");
+}
+
+// tcgen05.ld without the wait (several loads in flight, then tmem_wait_ld).
+__device__ __forceinline__ void tmem_ld8_nowait(uint32_t taddr, uint32_t (&r)[8]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+                 "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory"); }
+
+// The value of the folded levels of the balanced form, 2^(F - 1022 - 36) hi +
+// 2^(F - 1022 - 68) lo, for the column exponent field F of the B operand
+// (the exponents of A cancel against the scaling of B, see qstore.cu).
+__device__ __forceinline__ double unfold62(long long hi, long long lo, int F) {
+  return ldexp((double)hi, F - 1058) + ldexp((double)lo, F - 1090);
+}
+
+// The double nearest to (hi 2^32 + lo) 2^(F - 1090) (round to nearest, ties to
+// even), built from the exact integer with integer operations only (no FP64
+// pipe work; GB300's FP64 rate is low).  Results outside the normal range take
+// the ldexp route.
+__device__ __forceinline__ double fixed_to_double(long long hi, long long lo, int F) {
+  // v = hi 2^32 + lo as a 128-bit two's complement integer (vh, vl)
+  const unsigned long long a = (unsigned long long)hi << 32;
+  const unsigned long long vl0 = a + (unsigned long long)lo;
+  long long vh = (hi >> 32) + (lo >> 63) + (vl0 < a ? 1 : 0);
+  unsigned long long vl = vl0;
+  const bool neg = vh < 0;
+  if (neg) {
+    vl = ~vl + 1ull;
+    vh = (long long)(~(unsigned long long)vh + (vl == 0ull ? 1ull : 0ull));
+  }
+  const unsigned long long uh = (unsigned long long)vh;
+  if (uh == 0ull && vl == 0ull) return 0.0;
+  const int lz = uh != 0ull ? __clzll((long long)uh) : 64 + __clzll((long long)vl);
+  unsigned long long th, tl;  // v << lz: leading one at bit 127
+  if (lz >= 64) {
+    th = vl << (lz - 64);
+    tl = 0ull;
+  } else if (lz == 0) {
+    th = uh;
+    tl = vl;
+  } else {
+    th = (uh << lz) | (vl >> (64 - lz));
+    tl = vl << lz;
+  }
+  unsigned long long mant = th >> 11;  // 53 bits
+  const bool rnd = (th >> 10) & 1ull;
+  const bool sticky = (th & 0x3FFull) != 0ull || tl != 0ull;
+  mant += (rnd && (sticky || (mant & 1ull))) ? 1ull : 0ull;
+  int p = 127 - lz;
+  if (mant >> 53) {
+    mant >>= 1;
+    ++p;
+  }
+  const int be = p + F - 1090 + 1023;
+  if (be <= 0 || be >= 2047) return ldexp((double)hi, F - 1058) + ldexp((double)lo, F - 1090);
+  return __longlong_as_double((long long)(((unsigned long long)neg << 63) | ((unsigned long long)be << 52) |
+                                          (mant & 0xFFFFFFFFFFFFFull)));
+}
+
 // Tensor-memory allocation of NCOLS (power of two, 32..512) columns by one warp.
 template <int NCOLS>
 __device__ __forceinline__ void tmem_alloc(uint32_t* dst_smem) {

@@ -52,8 +52,22 @@ def test_workspace_size_queries():
     # 1S needs no separate projected block V; the others do
     assert sizes["bcgsi+p-1s"] < sizes["bcgsi+p-2s"]
     assert bcgs.workspace_size(m, n, s, "bcgsi+p-1s", "fp32") < sizes["bcgsi+p-1s"]
-    big = bcgs.workspace_size(2 ** 22, 256, 16, "bcgsi+p-1s")
-    assert 2 ** 22 * 16 * 8 < big < 2 ** 22 * 16 * 8 * 3
+    # FP64 engine: U, the TSQR tree and the row maxima, a few m x s blocks
+    old = bcgs.get_gram_engine()
+    try:
+        bcgs.set_gram_engine("fp64")
+        small = bcgs.workspace_size(2 ** 22, 256, 16, "bcgsi+p-1s")
+        bcgs.set_gram_engine("tensor")
+        big = bcgs.workspace_size(2 ** 22, 256, 16, "bcgsi+p-1s")
+        # the tensor engine adds the digit store of Q: 16 bytes per element
+        # plus one exponent per 128 rows and column
+        fp32 = bcgs.workspace_size(2 ** 22, 256, 16, "bcgsi+p-1s", "fp32")
+    finally:
+        bcgs.set_gram_engine(old)
+    assert 2 ** 22 * 16 * 8 < small < 2 ** 22 * 16 * 8 * 3
+    store = 2 ** 22 * 256 * 16 + (2 ** 22 // 128) * 256 * 4
+    assert big - small == pytest.approx(store, abs=2 ** 12)
+    assert fp32 < small   # no store with FP32 storage
 
 
 @pytest.mark.parametrize("m,n,s", [(100, 30, 8), (100, 16, 0), (4, 8, 8), (100, 64, 65),
