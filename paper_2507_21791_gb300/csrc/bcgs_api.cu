@@ -127,6 +127,7 @@ struct bcgs_qr_s {
   int32_t finished;
   int32_t esz;
   int32_t fp32;
+  int32_t sgram;  // Grams read the digit store (the current U and X blocks are split into it)
   cudaError_t last_cuda;
 
   DevStatus* st() { return reinterpret_cast<DevStatus*>(ws + L.status); }
@@ -242,8 +243,35 @@ cudaError_t project(bcgs_qr_s* h, Seg v, int c, const double* C, int ldc, const 
 // Digits of the freshly written block column k of Q into the store.
 cudaError_t wrote_q(bcgs_qr_s* h, int k) {
   if (!h->L.store) return cudaSuccess;
-  return launch_qsplit(h->qs(), reinterpret_cast<const double*>(h->Q), h->ldq, h->m, (k - 1) * h->s, h->s,
-                       h->st(), k, h->stream);
+  const double* Q = reinterpret_cast<const double*>(h->Q);
+  return launch_qsplit(h->qs(), Q + (size_t)(k - 1) * h->s * h->ldq, h->ldq, Q, h->ldq, h->m, (k - 1) * h->s,
+                       h->s, h->st(), k, h->stream);
+}
+
+// With store Grams: digits of an m x s block (X or U) into store columns
+// [k0, k0 + s), the columns Q fills next.
+cudaError_t store_put(bcgs_qr_s* h, const void* src, int64_t ld, int k0) {
+  if (!h->sgram) return cudaSuccess;
+  const double* Q = reinterpret_cast<const double*>(h->Q);
+  return launch_qsplit(h->qs(), reinterpret_cast<const double*>(src), ld, Q, h->ldq, h->m, k0, h->s, h->st(),
+                       h->j + 1, h->stream);
+}
+
+// G = A^T B: from the store (A = store columns [0, na), B = [b0, b0 + nb)) when
+// the factorization keeps its Grams there, else from the segments.
+cudaError_t gram_cols(bcgs_qr_s* h, int na, int b0, int nb, std::initializer_list<Seg> A,
+                      std::initializer_list<Seg> B, double* G) {
+  if (!h->sgram) return gram(h, A, B, G);
+  GramStoreDesc d;
+  memset(&d, 0, sizeof(d));
+  d.qs = h->qs();
+  d.na = na;
+  d.b0 = b0;
+  d.nb = nb;
+  gram_store_partition(h->m, &d.nchunks, &d.bpc);
+  d.m = h->m;
+  d.block = h->j + 1;
+  return launch_gram_store(d, h->buf(h->L.partial), G, h->L.ldg, h->st(), h->stream);
 }
 
 cudaError_t tsqr(bcgs_qr_s* h, Seg a, void* q, int64_t ldq, double* R, int ldr, int block,
@@ -260,7 +288,7 @@ int finish_p(bcgs_qr_s* h) {
   const int c = (q - 1) * s;
   double* G = h->buf(h->L.G);
   const int ldg = h->L.ldg;
-  TRY(gram(h, {h->Qseg(c), h->Useg()}, {h->Useg()}, G));
+  TRY(gram_cols(h, c + s, c, s, {h->Qseg(c), h->Useg()}, {h->Useg()}, G));
   TailDesc t;
   memset(&t, 0, sizeof(t));
   t.s = s;
@@ -323,10 +351,11 @@ int step_p(bcgs_qr_s* h, const void* X, int64_t ldx) {
   const Seg Xs = seg(X, ldx, s, h->fp32);
   double* G = h->buf(h->L.G);
   const int ldg = h->L.ldg;
+  TRY(store_put(h, X, ldx, c + s));
   if (one_sync)
-    TRY(gram(h, {h->Qseg(c), h->Useg(), Xs}, {h->Useg(), Xs}, G));
+    TRY(gram_cols(h, c + 2 * s, c, 2 * s, {h->Qseg(c), h->Useg(), Xs}, {h->Useg(), Xs}, G));
   else
-    TRY(gram(h, {h->Qseg(c), h->Useg()}, {h->Useg(), Xs}, G));
+    TRY(gram_cols(h, c + s, c, 2 * s, {h->Qseg(c), h->Useg()}, {h->Useg(), Xs}, G));
   const int nxt = 1 - h->cur;
   TailDesc t;
   memset(&t, 0, sizeof(t));
@@ -391,6 +420,7 @@ int step_p(bcgs_qr_s* h, const void* X, int64_t ldx) {
     TRY(launch_project_store(p, h->st(), h->stream));
     TRY(wrote_q(h, k));
     if (!one_sync) TRY(tsqr(h, h->Vseg(), h->U(), h->L.ldu, h->buf(h->L.Sd[nxt]), s, k + 1, h->Umax()));
+    TRY(store_put(h, h->U(), h->L.ldu, k * s));
     h->cur = nxt;
     return BCGS_OK;
   }
@@ -407,6 +437,7 @@ int step_p(bcgs_qr_s* h, const void* X, int64_t ldx) {
     TRY(project(h, Xs, c + s, h->buf(h->L.S[nxt]), h->n_max, nullptr, h->V(), h->L.ldu));
     TRY(tsqr(h, h->Vseg(), h->U(), h->L.ldu, h->buf(h->L.Sd[nxt]), s, k + 1, h->Umax()));
   }
+  TRY(store_put(h, h->U(), h->L.ldu, k * s));
   h->cur = nxt;
   return BCGS_OK;
 }
@@ -427,12 +458,14 @@ int do_step(bcgs_qr_s* h, const void* X, int64_t ldx) {
       const int k = j - 1, c = k * s;
       double* G2 = h->buf(h->L.G2);
       // S = Q_k^T X_{k+1};  [U, S_kk] = TSQR(X_{k+1} - Q_k S)
-      TRY(gram(h, {h->Qseg(c)}, {Xs}, G));
+      TRY(store_put(h, X, ldx, c));
+      TRY(gram_cols(h, c, c, s, {h->Qseg(c)}, {Xs}, G));
       TRY(project(h, Xs, c, G, ldg, nullptr, h->V(), h->L.ldu));
       TRY(zero_umax(h));
       TRY(tsqr(h, h->Vseg(), h->U(), h->L.ldu, h->buf(h->L.Rt1), s, j, h->Umax()));
       // Y = Q_k^T U;  [Q_{k+1}, Y_kk] = TSQR(U - Q_k Y)
-      TRY(gram(h, {h->Qseg(c)}, {h->Useg()}, G2));
+      TRY(store_put(h, h->U(), h->L.ldu, c));
+      TRY(gram_cols(h, c, c, s, {h->Qseg(c)}, {h->Useg()}, G2));
       TRY(project(h, h->Useg(), c, G2, ldg, nullptr, h->V(), h->L.ldu));
       TRY(tsqr(h, h->Vseg(), h->Qblk(j), h->ldq, h->buf(h->L.Rt2), s, j, h->Qmax(j)));
       TRY(wrote_q(h, j));
@@ -443,23 +476,27 @@ int do_step(bcgs_qr_s* h, const void* X, int64_t ldx) {
     case BCGS_BCGSI_PLUS_P_1S:
       if (j == 2) {
         // [S_12; T_2] = [Q_1 X_2]^T X_2, S_22 = chol(T_2 - S_12^T S_12), U_2
-        TRY(gram(h, {h->Qseg(s), Xs}, {Xs}, G));
+        TRY(store_put(h, X, ldx, s));
+        TRY(gram_cols(h, 2 * s, s, s, {h->Qseg(s), Xs}, {Xs}, G));
         TRY(launch_tail_start_1s(s, G, ldg, h->buf(h->L.S[h->cur]), h->n_max,
                                  h->buf(h->L.Sd[h->cur]), 2, h->st(), h->stream));
         TRY(zero_umax(h));
         TRY(project(h, Xs, s, h->buf(h->L.S[h->cur]), h->n_max, h->buf(h->L.Sd[h->cur]), h->U(),
                     h->L.ldu, h->Umax()));
+        TRY(store_put(h, h->U(), h->L.ldu, s));
         return BCGS_OK;
       }
       return step_p(h, X, ldx);
     case BCGS_BCGSI_PLUS_P_2S:
       if (j == 2) {
         // S_12 = Q_1^T X_2, [U_2, S_22] = TSQR(X_2 - Q_1 S_12)
-        TRY(gram(h, {h->Qseg(s)}, {Xs}, G));
+        TRY(store_put(h, X, ldx, s));
+        TRY(gram_cols(h, s, s, s, {h->Qseg(s)}, {Xs}, G));
         TRY(launch_copy_small(s, s, G, ldg, h->buf(h->L.S[h->cur]), h->n_max, h->st(), h->stream));
         TRY(project(h, Xs, s, G, ldg, nullptr, h->V(), h->L.ldu));
         TRY(zero_umax(h));
         TRY(tsqr(h, h->Vseg(), h->U(), h->L.ldu, h->buf(h->L.Sd[h->cur]), s, 2, h->Umax()));
+        TRY(store_put(h, h->U(), h->L.ldu, s));
         return BCGS_OK;
       }
       return step_p(h, X, ldx);
@@ -494,6 +531,8 @@ int init_handle(bcgs_qr_s* h, int64_t m, int32_t n_max, int32_t s, int variant, 
   h->stream = reinterpret_cast<cudaStream_t>(stream);
   h->fp32 = precision == BCGS_FP32_STORAGE ? 1 : 0;
   h->esz = h->fp32 ? 4 : 8;
+  // Grams from the store need whole 8-column groups per block and nb <= 32
+  h->sgram = h->L.store && s % 8 == 0 && (variant == BCGS_BCGSI_PLUS ? s <= 32 : s <= 16);
   h->j = 0;
   h->cur = 0;
   h->finished = 0;

@@ -156,11 +156,29 @@ struct QStore {
 };
 size_t qstore_bytes(int64_t m, int32_t n_max);
 QStore qstore_at(void* base, int64_t m, int32_t n_max);
-// Digits and exponents of columns [k0, k0 + s) of Q (FP64, ld ldq).  The rest of
-// the 16-column chunk holding column k0 + s - 1 is written as zeros, and columns
-// of the 8-column group before k0 are rewritten from Q (same exponents).
-cudaError_t launch_qsplit(const QStore& qs, const double* Q, int64_t ldq, int64_t m, int32_t k0,
-                          int32_t s, DevStatus* st, int32_t block, cudaStream_t stream);
+// Digits and exponents of store columns [k0, k0 + s) from the s columns of src
+// (FP64, ld lds).  The rest of the 16-column chunk holding column k0 + s - 1 is
+// written as zeros, and columns of the 8-column group before k0 are rewritten
+// from Q (ld ldq) with their unchanged exponents.
+cudaError_t launch_qsplit(const QStore& qs, const double* src, int64_t lds, const double* Q, int64_t ldq,
+                          int64_t m, int32_t k0, int32_t s, DevStatus* st, int32_t block,
+                          cudaStream_t stream);
+
+// Gram from the store (gram_store.cu): G = A^T B with A = store columns [0, na)
+// and B = store columns [b0, b0 + nb), b0 a multiple of 8, nb <= 32.  Chunks of
+// whole 128-row blocks (gram_store_partition); partials in the layout of
+// launch_gram_reduce, which it calls.
+struct GramStoreDesc {
+  QStore qs;
+  int32_t na, b0, nb;
+  int32_t nchunks, bpc;   // chunks of bpc blocks
+  int64_t m;
+  int32_t block;
+};
+void gram_store_partition(int64_t m, int32_t* nchunks, int32_t* bpc);
+bool gram_store_supported(int32_t na, int32_t b0, int32_t nb);
+cudaError_t launch_gram_store(const GramStoreDesc& d, double* partial, double* G, int32_t ldg, DevStatus* st,
+                              cudaStream_t stream);
 
 // One output of the store projection: W = (V - P_o) T^{-1}; V null means W = P_o T^{-1},
 // T null means no solve.

@@ -56,9 +56,10 @@ __device__ __forceinline__ int exp_field(double v) {
 }
 
 // One CTA per 128-row block, one thread per row.
-__global__ void __launch_bounds__(kStoreRows) qsplit_kernel(QStore qs, const double* Q, int64_t ldq,
-                                                            int64_t m, int32_t k0, int32_t s,
-                                                            DevStatus* st, int32_t block) {
+__global__ void __launch_bounds__(kStoreRows) qsplit_kernel(QStore qs, const double* src, int64_t lds,
+                                                            const double* Q, int64_t ldq, int64_t m,
+                                                            int32_t k0, int32_t s, DevStatus* st,
+                                                            int32_t block) {
   if (block_failed(st)) return;
   __shared__ int s_wmax[kStoreRows / 32][kQsplitMaxCols];
   __shared__ int s_e[kQsplitMaxCols];
@@ -67,8 +68,10 @@ __global__ void __launch_bounds__(kStoreRows) qsplit_kernel(QStore qs, const dou
   const bool live = r < m;
   const int klo = k0 & ~7, kend = k0 + s;
   const int kwr = (kend + 15) & ~15;
+  // column k of the store: src column k - k0, or (k < k0) column k of Q
+  auto at = [&](int k) { return k >= k0 ? src[r + (int64_t)(k - k0) * lds] : Q[r + (int64_t)k * ldq]; };
   for (int k = klo; k < kend; ++k) {
-    const int e = live ? exp_field(Q[r + (int64_t)k * ldq]) : 0;
+    const int e = live ? exp_field(at(k)) : 0;
     const int mx = __reduce_max_sync(0xffffffffu, e);
     if (lane == 0) s_wmax[warp][k - klo] = mx;
   }
@@ -87,7 +90,7 @@ __global__ void __launch_bounds__(kStoreRows) qsplit_kernel(QStore qs, const dou
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
       const int k = g8 + u;
-      const double v = (live && k < kend) ? Q[r + (int64_t)k * ldq] : 0.0;
+      const double v = (live && k < kend) ? at(k) : 0.0;
       N[u] = fixed62_offset(v, k < kend ? s_e[k - klo] : 0);
     }
     uint32_t w[4][8];
@@ -517,11 +520,12 @@ cudaError_t launch_sp(const StoreProjDesc& d, DevStatus* st, cudaStream_t stream
 
 }  // namespace
 
-cudaError_t launch_qsplit(const QStore& qs, const double* Q, int64_t ldq, int64_t m, int32_t k0,
-                          int32_t s, DevStatus* st, int32_t block, cudaStream_t stream) {
-  if (s < 1 || s > 64 || qs.nblk <= 0) return cudaErrorInvalidValue;
+cudaError_t launch_qsplit(const QStore& qs, const double* src, int64_t lds, const double* Q, int64_t ldq,
+                          int64_t m, int32_t k0, int32_t s, DevStatus* st, int32_t block,
+                          cudaStream_t stream) {
+  if (s < 1 || s > 64 || qs.nblk <= 0 || k0 < 0 || k0 + s > qs.ld_exp) return cudaErrorInvalidValue;
   const int slot = prof_begin(stream);
-  qsplit_kernel<<<(unsigned)qs.nblk, kStoreRows, 0, stream>>>(qs, Q, ldq, m, k0, s, st, block);
+  qsplit_kernel<<<(unsigned)qs.nblk, kStoreRows, 0, stream>>>(qs, src, lds, Q, ldq, m, k0, s, st, block);
   // reads the s new columns, writes 16 bytes of digits per element
   prof_end(slot, kProfStoreSplit, stream, 0.0, (double)m * s * (8.0 + 16.0));
   note_launch(1);

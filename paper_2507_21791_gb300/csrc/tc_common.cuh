@@ -326,6 +326,13 @@ __device__ __forceinline__ void mbar_init(uint64_t* mbar) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(mbar)));
   asm volatile("fence.mbarrier_init.release.cluster;\n");
 }
+__device__ __forceinline__ void mbar_init_count(uint64_t* mbar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(mbar)), "r"(count));
+  asm volatile("fence.mbarrier_init.release.cluster;\n");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* mbar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(mbar)) : "memory");
+}
 // Poll the barrier's phase `phase` for at most kWaitCycles; true when it completed.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* mbar, uint32_t phase) {
   const long long t0 = clock64();
