@@ -23,7 +23,7 @@ constexpr int kMaxN = 2048;
 
 struct Layout {
   size_t status, S[2], Sd[2], Yd, Rt1, Rt2, G, G2, Bp, partial, amax, amaxQ, amaxU, rowmaxQ, U, V, tsqr,
-      qstore, total;
+      qstore, fexp, total;
   int store;    // the digit store of Q is part of the workspace
   int ldg;      // leading dimension of G, G2 (= n_max)
   int64_t ldu;  // leading dimension of U, V
@@ -77,6 +77,7 @@ void make_layout(int64_t m, int32_t n_max, int32_t s, int variant, int precision
   L->tsqr = take(L->tp.doubles * sizeof(double));
   L->store = store;
   L->qstore = store ? take(qstore_bytes(m, n_max)) : off;
+  L->fexp = store ? take((size_t)ceil_div(m, kStoreRows) * 32 * sizeof(int32_t)) : off;
   L->total = off;
 }
 
@@ -143,9 +144,14 @@ struct bcgs_qr_s {
   Seg Qseg(int ncols) { return seg(Q, ldq, ncols, fp32, amaxQ()); }
   Seg Useg() { return seg(U(), L.ldu, s, fp32, amaxU()); }
   Seg Vseg() { return seg(V(), L.ldu, s, fp32); }
-  // maxima to keep when writing block k of Q, or U
-  MaxOut Qmax(int k) { return MaxOut{amaxQ() + (size_t)(k - 1) * s, rowmaxQ()}; }
-  MaxOut Umax() { return MaxOut{amaxU(), nullptr}; }
+  // maxima to keep when writing block k of Q, or U: the column maxima feed the
+  // on-the-fly Gram (not needed when the Grams read the store), the row maxima
+  // of Q the on-the-fly projection (not needed with the store)
+  MaxOut Qmax(int k) {
+    return MaxOut{sgram ? nullptr : amaxQ() + (size_t)(k - 1) * s, L.store ? nullptr : rowmaxQ()};
+  }
+  MaxOut Umax() { return MaxOut{sgram ? nullptr : amaxU(), nullptr}; }
+  int32_t* fexp() { return reinterpret_cast<int32_t*>(ws + L.fexp); }
   QStore qs() { return qstore_at(ws + L.qstore, m, n_max); }
 };
 
@@ -221,7 +227,7 @@ cudaError_t project(bcgs_qr_s* h, Seg v, int c, const double* C, int ldc, const 
   d.w_fp32 = h->fp32;
   d.m = h->m;
   d.s = h->s;
-  if (h->L.store && use_tensor_project(d) && project_store_supported(h->s, 1, 0)) {
+  if (h->L.store && use_tensor_project(d) && project_store_supported(h->s, 1)) {
     StoreProjDesc p;
     memset(&p, 0, sizeof(p));
     p.qs = h->qs();
@@ -234,6 +240,7 @@ cudaError_t project(bcgs_qr_s* h, Seg v, int c, const double* C, int ldc, const 
                        ldw, wmax};
     p.m = h->m;
     p.block = h->j + 1;
+    p.fexp = h->fexp();
     return launch_project_store(p, h->st(), h->stream);
   }
   if (use_tensor_project(d)) return launch_project_tc(d, h->st(), h->stream);
@@ -312,7 +319,8 @@ int finish_p(bcgs_qr_s* h) {
   probe.q = h->Qseg(c);
   probe.m = h->m;
   probe.s = s;
-  const bool folded = h->L.store && use_tensor_project(probe) && project_store_supported(s, 1, s);
+  // U_q is in the store (columns [c, c + s)) when the Grams use it
+  const bool folded = h->sgram && use_tensor_project(probe) && project_store_supported(s, 1);
   if (folded) {
     t.Bpair = h->buf(h->L.Bp);
     t.ldb = h->n_max;
@@ -323,10 +331,7 @@ int finish_p(bcgs_qr_s* h) {
     StoreProjDesc p;
     memset(&p, 0, sizeof(p));
     p.qs = h->qs();
-    p.c = c;
-    p.ext = reinterpret_cast<const double*>(h->U());
-    p.ld_ext = h->L.ldu;
-    p.next = s;
+    p.c = c + s;
     p.B = h->buf(h->L.Bp);
     p.ldb = h->n_max;
     p.s = s;
@@ -334,6 +339,7 @@ int finish_p(bcgs_qr_s* h) {
     p.out[0] = ProjOut{nullptr, 0, nullptr, 0, reinterpret_cast<double*>(h->Qblk(q)), h->ldq, h->Qmax(q)};
     p.m = h->m;
     p.block = q;
+    p.fexp = h->fexp();
     TRY(launch_project_store(p, h->st(), h->stream));
   } else {
     TRY(project(h, h->Useg(), c, G, ldg, h->buf(h->L.Yd), h->Qblk(q), h->ldq, h->Qmax(q)));
@@ -388,7 +394,8 @@ int step_p(bcgs_qr_s* h, const void* X, int64_t ldx) {
   probe.q = h->Qseg(c);
   probe.m = h->m;
   probe.s = s;
-  const bool paired = h->L.store && use_tensor_project(probe) && project_store_supported(s, 2, s);
+  // [Q_{1:k-1} U_k] from the store: U_k is there when the Grams use it
+  const bool paired = h->sgram && use_tensor_project(probe) && project_store_supported(s, 2);
   if (paired) {
     t.Bpair = h->buf(h->L.Bp);
     t.ldb = h->n_max;
@@ -399,10 +406,7 @@ int step_p(bcgs_qr_s* h, const void* X, int64_t ldx) {
     StoreProjDesc p;
     memset(&p, 0, sizeof(p));
     p.qs = h->qs();
-    p.c = c;
-    p.ext = reinterpret_cast<const double*>(h->U());
-    p.ld_ext = h->L.ldu;
-    p.next = s;
+    p.c = c + s;
     p.B = h->buf(h->L.Bp);
     p.ldb = h->n_max;
     p.s = s;
@@ -417,6 +421,7 @@ int step_p(bcgs_qr_s* h, const void* X, int64_t ldx) {
                          reinterpret_cast<double*>(h->V()), h->L.ldu, MaxOut{nullptr, nullptr}};
     p.m = h->m;
     p.block = k;
+    p.fexp = h->fexp();
     TRY(launch_project_store(p, h->st(), h->stream));
     TRY(wrote_q(h, k));
     if (!one_sync) TRY(tsqr(h, h->Vseg(), h->U(), h->L.ldu, h->buf(h->L.Sd[nxt]), s, k + 1, h->Umax()));

@@ -188,21 +188,20 @@ struct ProjOut {
   double* w; int64_t ldw;
   MaxOut wmax;
 };
-// P = [Q_{1:c} E] B with Q from the store, the optional extra segment E (m x
-// next, FP64, split on the fly) and B ((c + next) x nouts s, column-major, ldb);
-// output o takes columns [o s, o s + s) of P; only the last output may have a
-// triangle T.  Every V_o is read before any W_o is written, so W_1 may overwrite
-// E or V_0.
+// P = Q_{1:c} B with the first c store columns (Q, and the current U block when
+// the Grams use the store) and B (c x nouts s, column-major, ldb); output o takes
+// columns [o s, o s + s) of P; only the last output may have a triangle T.  A V
+// is read before the W of the same row is written, so W may overwrite V.
 struct StoreProjDesc {
   QStore qs; int32_t c;
-  const double* ext; int64_t ld_ext; int32_t next;
   const double* B; int32_t ldb;
   int32_t s, nouts;
   ProjOut out[2];
   int64_t m;
   int32_t block;
+  int32_t* fexp;  // scratch: 32 ints per row block (column exponents of B')
 };
-bool project_store_supported(int32_t s, int32_t nouts, int32_t next);
+bool project_store_supported(int32_t s, int32_t nouts);
 cudaError_t launch_project_store(const StoreProjDesc& d, DevStatus* st, cudaStream_t stream);
 
 // TSQR of an m x s block.

@@ -109,412 +109,500 @@ __global__ void __launch_bounds__(kStoreRows) qsplit_kernel(QStore qs, const dou
 }
 
 // ---------------------------------------------------------------- projection
-// Two CTAs per SM (one accumulator set of tensor memory and half the shared
-// memory each): the prologue, the read-backs and the FP64 epilogue of one CTA
-// overlap the digit stream of the other.
-constexpr int kThreads = 256;
-constexpr int kRows = 128;                       // rows per CTA (MMA M) = one store block
+// Persistent, one CTA per SM, warp-specialized:
+//   warp 0      bulk copies of the A digit chunks and the MMAs (one thread);
+//   warps 1..3  per row block: its exponents, the column exponents F_j of B',
+//               and the B' digits of every chunk;
+//   warps 4..11 read-back of the accumulators and the FP64 epilogue.
+// Chunks, B' splits, read-backs and epilogues of consecutive row blocks overlap
+// through mbarriers; two accumulator sets in tensor memory alternate per group
+// of 128 K-values.
+constexpr int kRows = 128;                       // rows per block (MMA M)
 constexpr int kK = 16;                           // K-values per chunk (one MMA K step)
-constexpr int kStages = 2;                       // chunks in flight per CTA
+constexpr int kStages = 3;                       // chunks in flight
 constexpr int kATileT = kRows * kK * 2;          // one digit of one chunk: 4 KB
 constexpr int kAStage = kDigits * kATileT;       // 32 KB
 constexpr int kGroupChunks = 8;                  // 128 K-values between read-backs
-constexpr int kExpInts = 2048 + 64;              // s_exp: c + next <= 2048 + 16
-constexpr int kTBytes = 32 * 32 * 8;             // one s x s triangle (s <= 32)
+constexpr int kExpInts = 2048 + 64;              // s_exp: K <= 2048 + 16
 constexpr size_t kDigTile = (size_t)kStoreRows * kStoreCols * 2;  // one digit of a store tile
+constexpr int kCtl = 0;                          // warp roles
+constexpr int kSplit0 = 1, kSplitWarps = 3;
+constexpr int kRead0 = 4, kReadWarps = 8;
+constexpr int kThreads = 32 * (kRead0 + kReadWarps);
 
-// NBT: columns of B (all outputs); NOUT: outputs; EXT: an extra A segment of at
-// most 16 columns split on the fly, taken as chunk 0 of the contraction.
-template <int NBT, int NOUT, bool EXT>
+// Output o occupies tile columns [o SMAX, o SMAX + s) (B column o s + jj); with
+// two outputs each read-back thread holds one output of its row, so the
+// epilogue runs from registers and only the single form stages products in P.
+// B itself is staged in shared memory when it fits (kSmemLimit).
+template <int NBT, int NOUT>
 struct SPCfg {
   static constexpr int kBTileT = NBT * kK * 2;   // one digit of one B chunk
   static constexpr int kBStage = kDigits * kBTileT;
-  static constexpr int kTmem = kDigits * NBT;    // TMEM columns: the eight levels
+  static constexpr int kBRing = 4;               // B chunks in the ring (>= kStages)
+  static constexpr int kAcc = kDigits * NBT;     // TMEM columns of one accumulator set
+  static constexpr int kTmem = 2 * kAcc;
   static constexpr int kSmax = NBT / NOUT;       // columns per output
-  static constexpr size_t kSmem =
-      1024 + (size_t)kStages * kAStage + (size_t)kStages * kBStage + kExpInts * 4 + kTBytes;
+  static constexpr size_t kPBytes = NOUT == 1 ? (size_t)kRows * NBT * 8 : 0;
+  static constexpr size_t kFixed = 1024 + (size_t)kStages * kAStage + (size_t)kBRing * kBStage + kExpInts * 4 +
+                                   kPBytes + 32 * 32 * 8;
 };
+constexpr size_t kSmemLimit = 232448 - 4096;     // dynamic shared memory we ask for at most
 
-// Raw B' operands of one thread for one chunk (loaded a chunk ahead).
-struct BPair {
-  double x, y;
-  int kx, ky;  // rows of B (and of s_exp), -1 for none
-};
+// Column exponents of B' = diag(2^E_b) B for every row block b:
+//     F_bj = max_k (e(B_k,bcol(j)) + E_bk) - 1022   (exponent fields; 0 for none)
+// one warp per block, the exponent fields of B staged once per CTA.  A
+// non-finite entry of B or of the block exponents raises BCGS_ERR_NONFINITE.
+template <int NBT, int NOUT>
+__global__ void __launch_bounds__(256) proj_fexp_kernel(StoreProjDesc d, DevStatus* st) {
+  constexpr int SMAX = NBT / NOUT;
+  if (block_failed(st)) return;
+  extern __shared__ int16_t eB[];  // K x NBT, tile columns
+  const int K = d.c, s = d.s;
+  for (int e = threadIdx.x; e < K * NBT; e += blockDim.x) {
+    const int j = e / K, k = e - j * K;  // consecutive threads: consecutive rows of one column
+    const int o = j / SMAX, jj = j - o * SMAX;
+    eB[k * NBT + j] = (int16_t)((o < NOUT && jj < s) ? exp_field(d.B[k + (int64_t)(o * s + jj) * d.ldb]) : 0);
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  bool nf = false;
+  for (int64_t b = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; b < d.qs.nblk; b += nw) {
+    const int32_t* ex = d.qs.exps + b * d.qs.ld_exp;
+    int F = INT_MIN;
+    for (int k0 = 0; k0 < K; k0 += 32) {
+      const int E = k0 + lane < K ? ex[k0 + lane] : 0;
+      nf |= E == 0x7FF;
+      const int kn = K - k0 < 32 ? K - k0 : 32;
+      for (int u = 0; u < kn; ++u) {
+        const int Eu = __shfl_sync(0xffffffffu, E, u);
+        const int eb = lane < NBT ? eB[(k0 + u) * NBT + lane] : 0;
+        nf |= eb == 0x7FF;
+        if (eb != 0 && Eu != 0 && Eu != 0x7FF && eb != 0x7FF) F = max(F, eb + Eu - 1022);
+      }
+    }
+    if (lane < NBT) d.fexp[b * NBT + lane] = F == INT_MIN ? 0 : F;
+  }
+  if (__any_sync(0xffffffffu, nf) && lane == 0) set_failure(st, BCGS_ERR_NONFINITE, d.block);
+}
 
-template <int NBT, int NOUT, bool EXT>
-__global__ void __launch_bounds__(kThreads, 2) proj_store_kernel(StoreProjDesc d, DevStatus* st) {
-  using C = SPCfg<NBT, NOUT, EXT>;
+// Poll `mbar` for phase `parity` until it completes, *abort is raised, or the
+// bound runs out (then *abort is raised): true when the phase completed.
+__device__ __forceinline__ bool wait_or_abort(uint64_t* mbar, uint32_t parity, volatile int* abort) {
+  const long long t0 = clock64();
+  while (!mbar_try(smem_u32(mbar), parity)) {
+    if (*abort) return false;
+    if (clock64() - t0 > kWaitCycles) {
+      *abort = 1;
+      return false;
+    }
+  }
+  return true;
+}
+
+template <int NBT, int NOUT>
+__global__ void __launch_bounds__(kThreads, 1) proj_store_kernel(StoreProjDesc d, int32_t b_staged,
+                                                                  DevStatus* st) {
+  using C = SPCfg<NBT, NOUT>;
   static_assert(NBT == 16 || NBT == 32, "N tile");
   constexpr int kHalf = NBT / 2;                 // read-back columns per thread
   constexpr int SMAX = C::kSmax;
-  constexpr int X0 = EXT ? 1 : 0;                // chunk index of the first Q chunk
   if (block_failed(st)) return;
   extern __shared__ uint8_t dyn[];
-  __shared__ __align__(8) uint64_t full[kStages];
-  __shared__ __align__(8) uint64_t done[kStages];
+  __shared__ __align__(8) uint64_t fullA[kStages];    // A chunk landed (copy)
+  __shared__ __align__(8) uint64_t done[kStages];     // MMAs of the chunk in the slot done
+  __shared__ __align__(8) uint64_t bready[C::kBRing]; // B' digits of the chunk written (splitter warps)
+  __shared__ __align__(8) uint64_t bdone[C::kBRing];  // MMAs that read the B slot done
+  __shared__ __align__(8) uint64_t accdone[2];        // accumulator set complete
+  __shared__ __align__(8) uint64_t accfree[2];        // accumulator set read (8 warps)
+  __shared__ __align__(8) uint64_t fready[2];         // F_j of a block written
+  __shared__ __align__(8) uint64_t ffree[2];          // F_j of a block used
   __shared__ uint32_t tmem_base_s;
-  __shared__ int s_F[NBT];
-  __shared__ int s_wmax[8][8];
+  __shared__ int s_F[2][NBT];
   __shared__ double s_inv[32];
+  __shared__ volatile int s_abort;
   __shared__ int s_bad;
 
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(dyn) + 1023) & ~uintptr_t(1023));
   uint8_t* Aring = base;
   uint8_t* Bring = Aring + kStages * kAStage;
-  int* s_exp = reinterpret_cast<int*>(Bring + kStages * C::kBStage);
-  double* s_T = reinterpret_cast<double*>(reinterpret_cast<uint8_t*>(s_exp) + kExpInts * 4);
-  double* P = reinterpret_cast<double*>(Aring);  // after the last MMA: kRows x NBT products
+  int* s_exp = reinterpret_cast<int*>(Bring + C::kBRing * C::kBStage);
+  double* P = reinterpret_cast<double*>(reinterpret_cast<uint8_t*>(s_exp) + kExpInts * 4);
+  double* s_T = reinterpret_cast<double*>(reinterpret_cast<uint8_t*>(P) + C::kPBytes);
+  // staged B (b_staged != 0), row-major by tile column: B'_(k, j) at Bsm[k * kLdj + j]; a pitch
+  // of NBT + 4 doubles keeps the column-per-lane and pair-per-lane reads at two wavefronts
+  constexpr int kLdj = NBT + 4;
+  double* Bsm = s_T + 32 * 32;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int c = d.c, s = d.s;
-  const int next = EXT ? d.next : 0;
+  const int K = d.c, s = d.s;
   const int ncolsB = NOUT * s;
-  const int64_t b = blockIdx.x, r0 = b * kRows;
-  const int nq = (c + kK - 1) / kK;
-  const int nch = nq + X0;
-  const uint8_t* qblk = d.qs.dig + (size_t)b * d.qs.ngroups * kStoreTileBytes;
+  const int nch = (K + kK - 1) / kK;
+  const int ngrp = (nch + kGroupChunks - 1) / kGroupChunks;
+  const int64_t nblk = d.qs.nblk;
+  const int nbl = blockIdx.x < nblk ? (int)((nblk - 1 - blockIdx.x) / gridDim.x + 1) : 0;
+  const int total = nbl * nch;
   const ProjOut& tri = d.out[NOUT - 1];  // only the last output may have a solve
   const bool has_t = tri.T != nullptr;
+  auto blk_of = [&](int bi) { return (int64_t)blockIdx.x + (int64_t)bi * gridDim.x; };
 
-  // chunk kc >= X0 holds columns [16 q, 16 q + 16) of Q, q = kc - X0: digit bytes
-  // (q % 8) * 4 KB of column group q / 8, for each digit t
-  auto issue_copy = [&](int kc) {
-    const int slot = kc % kStages, q = kc - X0;
-    mbar_arrive_expect_tx(&full[slot], kAStage);
-    const uint8_t* src = qblk + (size_t)(q >> 3) * kStoreTileBytes + (size_t)(q & 7) * kATileT;
-#pragma unroll
-    for (int t = 0; t < kDigits; ++t)
-      bulk_g2s(Aring + slot * kAStage + t * kATileT, src + (size_t)t * kDigTile, kATileT, &full[slot]);
-  };
-
-  // phase of full[slot] for the copy of chunk kc: the copies into its slot before
-  // it (chunk 0 of an extra segment is split in place, not copied)
-  auto full_parity = [&](int kc) -> uint32_t {
-    return (uint32_t)((kc / kStages) - ((X0 > 0 && kc % kStages == 0) ? 1 : 0)) & 1u;
-  };
-  int issued = X0;  // chunks whose A operand is on its way (thread 0)
   if (tid == 0) {
+    s_abort = 0;
     s_bad = 0;
     for (int i = 0; i < kStages; ++i) {
-      mbar_init(&full[i]);
+      mbar_init(&fullA[i]);
       mbar_init(&done[i]);
     }
+    for (int i = 0; i < C::kBRing; ++i) {
+      mbar_init_count(&bready[i], kSplitWarps);
+      mbar_init(&bdone[i]);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&accdone[i]);
+      mbar_init_count(&accfree[i], kReadWarps);
+      mbar_init(&fready[i]);
+      mbar_init(&ffree[i]);
+    }
   }
-  for (int k = tid; k < c; k += kThreads) s_exp[k] = d.qs.exps[b * d.qs.ld_exp + k];
-  if (has_t)
+  if (has_t) {
     for (int e = tid; e < s * s; e += kThreads) {
       const int i = e % s, j = e / s;
       s_T[i * 32 + j] = tri.T[i + (int64_t)j * tri.ldt];
     }
-  // extra segment: this thread's row, 8 columns
-  double ev[8];
-  if constexpr (EXT) {
-    const int i = tid & (kRows - 1), h = tid >> 7;
-    const int64_t r = r0 + i;
-    const bool live = r < d.m;
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int col = 8 * h + u;
-      ev[u] = (live && col < next) ? d.ext[r + (int64_t)col * d.ld_ext] : 0.0;
-      const int mx = __reduce_max_sync(0xffffffffu, exp_field(ev[u]));
-      if (lane == 0) s_wmax[warp][u] = mx;
-    }
   }
-  if (warp == 0) tmem_alloc<C::kTmem>(&tmem_base_s);
+  // B column of tile column j, -1 for a padding column
+  auto bcol = [&](int j) { const int o = j / SMAX, jj = j - o * SMAX; return (o < NOUT && jj < s) ? o * s + jj : -1; };
+  // B: staged once per CTA (it is the same for every row block) when it fits
+  if (b_staged)
+    for (int e = tid; e < NBT * K; e += kThreads) {
+      const int j = e / K, k = e - j * K;
+      const int bc = bcol(j);
+      Bsm[k * kLdj + j] = bc >= 0 ? d.B[k + (int64_t)bc * d.ldb] : 0.0;
+    }
+  // element (k, tile column j) of B
+  auto bval = [&](int k, int j) -> double {
+    if (b_staged) return Bsm[k * kLdj + j];
+    const int bc = bcol(j);
+    return bc >= 0 ? d.B[k + (int64_t)bc * d.ldb] : 0.0;
+  };
+  if (warp == kCtl) tmem_alloc<C::kTmem>(&tmem_base_s);
   tc_before_sync();
   __syncthreads();
   tc_after_sync();
-  const uint32_t tmem = tmem_base_s;
-  if (tid == 0)  // the first Q chunks stream in while the coefficients are prepared
-    for (; issued < kStages && issued < nch; ++issued) issue_copy(issued);
-  if constexpr (EXT) {
-    if (tid < 16) {
-      const int h = tid >> 3;
-      int e = 0;
-#pragma unroll
-      for (int w = 0; w < 4; ++w) e = max(e, s_wmax[4 * h + w][tid & 7]);
-      s_exp[c + tid] = e;
-      if (e == 0x7FF) s_bad = 1;
-    }
-  }
   if (has_t)
     for (int j = tid; j < s; j += kThreads) s_inv[j] = 1.0 / s_T[j * 32 + j];
   __syncthreads();
-  // column exponents of B' = diag(2^E_k) B over k < c + next (eight independent
-  // loads in flight per thread)
-  {
-    const int j = tid >> 3, p = tid & 7;
-    int F = INT_MIN;
-    bool nf = false;
-    if (j < ncolsB) {
-      const int K = c + next;
-      const double* bj = d.B + (int64_t)j * d.ldb;
-      for (int k0 = p; k0 < K; k0 += 64) {
-        double v[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) v[u] = k0 + 8 * u < K ? bj[k0 + 8 * u] : 0.0;
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          const int k = k0 + 8 * u;
-          const int ex = k < K ? s_exp[k] : 0;
-          const int e = exp_field(v[u]);
-          if (e == 0x7FF || ex == 0x7FF) nf = true;
-          else if (e != 0 && ex != 0) F = max(F, e + ex - 1022);
-        }
-      }
-    }
-#pragma unroll
-    for (int o = 1; o < 8; o <<= 1) F = max(F, __shfl_xor_sync(0xffffffffu, F, o));
-    if (__any_sync(0xffffffffu, nf) && lane == 0) s_bad = 1;
-    if (p == 0 && j < NBT) s_F[j] = F == INT_MIN ? 0 : F;
-  }
-  if constexpr (EXT) {
-    // digits of the extra segment: chunk 0, ring slot 0 (no copy goes there first)
-    const int i = tid & (kRows - 1), h = tid >> 7;
-    uint64_t N[8];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) N[u] = fixed62_offset(ev[u], s_exp[c + 8 * h + u]);
-    uint32_t w[4][8];
-#pragma unroll
-    for (int p = 0; p < 4; ++p)
-      digits_pair_f16((uint32_t)(N[2 * p] >> 32), (uint32_t)N[2 * p], (uint32_t)(N[2 * p + 1] >> 32),
-                      (uint32_t)N[2 * p + 1], w[p]);
-    uint8_t* dst = Aring + h * 2048 + (i >> 3) * 128 + (i & 7) * 16;
-#pragma unroll
-    for (int t = 0; t < kDigits; ++t)
-      *reinterpret_cast<uint4*>(dst + t * kATileT) = make_uint4(w[0][t], w[1][t], w[2][t], w[3][t]);
-  }
-  __syncthreads();
-  const bool bad = s_bad != 0;
+  const uint32_t tmem = tmem_base_s;
 
-  // B' rows of chunk kc -> digit tiles [t][j / 8][g][8 rows x 16 B] (wide-N contiguous).
-  // This thread's pair: column j, K-values kk, kk + 1 of the chunk.
-  const bool bworker = tid < NBT * 8;
-  const int b_jl = lane >> 2, b_pp = lane & 3;
-  const int b_jr = warp % (NBT / 8), b_g = warp / (NBT / 8);
-  const int b_j = b_jr * 8 + b_jl, b_kk = b_g * 8 + 2 * b_pp;
-  const bool b_jv = bworker && b_j < ncolsB;
-  const double* b_col = d.B + (int64_t)(b_jv ? b_j : 0) * d.ldb;
-  auto load_B = [&](int kc) {
-    BPair q;
-    int k;
-    bool v0, v1;
-    if (kc >= X0) {
-      k = (kc - X0) * kK + b_kk;
-      v0 = k < c;
-      v1 = k + 1 < c;
-    } else {
-      k = c + b_kk;
-      v0 = b_kk < next;
-      v1 = b_kk + 1 < next;
-    }
-    v0 = v0 && b_jv;
-    v1 = v1 && b_jv;
-    q.x = v0 ? b_col[k] : 0.0;
-    q.y = v1 ? b_col[k + 1] : 0.0;
-    q.kx = v0 ? k : -1;
-    q.ky = v1 ? k + 1 : -1;
-    return q;
-  };
-  auto split_B = [&](const BPair& q, uint8_t* dst) {
-    if (!bworker) return;
-    const int F = s_F[b_j];
-    const double xy[2] = {q.x, q.y};
-    const int kx[2] = {q.kx, q.ky};
-    uint64_t nxy[2];
+  if (warp == kCtl) {
+    // ------------------------------------------------ copies and MMAs
+    if (lane == 0) {
+      auto issue_copy = [&](int g) {
+        const int slot = g % kStages, kc = g % nch;
+        const int64_t b = blk_of(g / nch);
+        mbar_arrive_expect_tx(&fullA[slot], kAStage);
+        const uint8_t* src = d.qs.dig + (size_t)b * d.qs.ngroups * kStoreTileBytes +
+                             (size_t)(kc >> 3) * kStoreTileBytes + (size_t)(kc & 7) * kATileT;
 #pragma unroll
-    for (int u = 0; u < 2; ++u) {
-      const uint64_t bits = (uint64_t)__double_as_longlong(xy[u]);
-      const int e = (int)((bits >> 52) & 0x7FF);
-      const int ex = kx[u] >= 0 ? s_exp[kx[u]] : 0;
-      const bool nz = e != 0 && ex != 0;
-      const int dd = F - (e + ex - 1022);
-      const uint64_t mant = (bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-      const uint64_t mag = (nz && dd < 63) ? ((mant << 9) >> (dd > 0 ? dd : 0)) : 0ull;
-      nxy[u] = ((bits >> 63) ? (0ull - mag) : mag) + 0x8080808080808080ull;
-    }
-    uint32_t out[8];
-    digits_pair_f16((uint32_t)(nxy[0] >> 32), (uint32_t)nxy[0], (uint32_t)(nxy[1] >> 32), (uint32_t)nxy[1],
-                    out);
-    uint8_t* pp = dst + b_jr * 256 + b_g * 128 + b_jl * 16 + b_pp * 4;
-#pragma unroll
-    for (int t = 0; t < kDigits; ++t) *reinterpret_cast<uint32_t*>(pp + t * C::kBTileT) = out[t];
-  };
-  // digit t of A times digit tiles [B_0 .. B_{7-t}] (one operand of (8 - t) NBT
-  // rows) lands tile u in level t + u: TMEM columns (t + u) NBT.
-  auto issue_mma = [&](int kc) {
-    const int slot = kc % kStages;
-    const uint32_t a0 = smem_u32(Aring + slot * kAStage);
-    const uint32_t b0 = smem_u32(Bring + slot * C::kBStage);
-    const bool first = (kc % kGroupChunks) == 0;
+        for (int t = 0; t < kDigits; ++t)
+          bulk_g2s(Aring + slot * kAStage + t * kATileT, src + (size_t)t * kDigTile, kATileT, &fullA[slot]);
+      };
+      int issued = 0, got = 0;
+      for (; issued < kStages && issued < total; ++issued) issue_copy(issued);
+      bool ok = true;
+      for (int g = 0; g < total && ok; ++g) {
+        const int slot = g % kStages, kc = g % nch, bi = g / nch;
+        const int gg = bi * ngrp + kc / kGroupChunks;
+        const bool first = kc % kGroupChunks == 0;
+        const int bslot = g % C::kBRing;
+        ok = wait_or_abort(&fullA[slot], (g / kStages) & 1, &s_abort);
+        if (ok) got = g + 1;
+        if (ok) ok = wait_or_abort(&bready[bslot], (g / C::kBRing) & 1, &s_abort);
+        if (ok && first && gg >= 2) ok = wait_or_abort(&accfree[gg & 1], ((gg >> 1) - 1) & 1, &s_abort);
+        if (!ok) break;
+        tc_after_sync();
+        const uint32_t a0 = smem_u32(Aring + slot * kAStage);
+        const uint32_t b0 = smem_u32(Bring + bslot * C::kBStage);
+        const uint32_t acc = tmem + (uint32_t)((gg & 1) * C::kAcc);
+        // digit t of A times digit tiles [B_0 .. B_{7-t}]: tile u lands in level t + u
 #pragma unroll 1
-    for (int t = 0; t < kDigits; ++t)
-      mma_bf16(tmem + (uint32_t)(t * NBT), desc_interleave(a0 + t * kATileT, 2048, 128),
-               desc_interleave(b0, 128, 256), idesc_f16(kRows, (kDigits - t) * NBT),
-               (first && t == 0) ? 0u : 1u);
-    mma_commit(&done[slot]);
-  };
-
-  const int my_j0 = (warp >> 2) * kHalf;
-  long long hi[kHalf], lo[kHalf];
-#pragma unroll
-  for (int j = 0; j < kHalf; ++j) hi[j] = lo[j] = 0;
-  // levels 0..3 fold into hi, 4..7 into lo (the fold of fold_levels in two halves)
-  auto read_back = [&]() {
-    const uint32_t addr = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)my_j0;
-#pragma unroll
-    for (int g8 = 0; g8 < kHalf; g8 += 8) {
-#pragma unroll
-      for (int half = 0; half < 2; ++half) {
-        uint32_t r[4][8];
-#pragma unroll
-        for (int l = 0; l < 4; ++l) tmem_ld8_nowait(addr + (uint32_t)((4 * half + l) * NBT + g8), r[l]);
-        tmem_wait_ld();
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const int32_t L0 = __float2int_rn(__uint_as_float(r[0][j]));
-          const int32_t L1 = __float2int_rn(__uint_as_float(r[1][j]));
-          const int32_t L2 = __float2int_rn(__uint_as_float(r[2][j]));
-          const int32_t L3 = __float2int_rn(__uint_as_float(r[3][j]));
-          if (half == 0)
-            hi[g8 + j] += ((long long)((L0 << 8) + L1) << 16) + (long long)((L2 << 8) + L3);
-          else
-            lo[g8 + j] += ((long long)L0 << 24) + ((long long)L1 << 16) + ((long long)L2 << 8) + (long long)L3;
-        }
-      }
-    }
-  };
-
-  bool timed_out = false;
-  int waited = X0;    // chunks whose copies thread 0 saw land
-  bool t0_fail = false;
-  const int nrun = bad ? 0 : nch;
-  BPair cur = load_B(0);
-  for (int kc = 0; kc < nrun; ++kc) {
-    const int slot = kc % kStages;
-    bool ok = true;
-    if (kc >= kStages) ok = mbar_wait_bounded(&done[slot], ((kc / kStages) - 1) & 1);  // B slot free
-    if (ok) split_B(cur, Bring + slot * C::kBStage);
-    if (kc + 1 < nrun) cur = load_B(kc + 1);  // in flight during the barrier and the MMAs
-    fence_smem_to_async();
-    tc_before_sync();
-    if (__syncthreads_or(!ok || t0_fail)) {
-      timed_out = true;
-      break;
-    }
-    tc_after_sync();
-    if (tid == 0) {
-      bool okc = true;
-      if (kc >= X0) {
-        okc = mbar_wait_bounded(&full[slot], full_parity(kc));
-        if (okc) waited = kc + 1;
-      }
-      if (okc) {
-        issue_mma(kc);
-        // refill the slot of chunk kc - 1 (free once its MMAs are done) with chunk kc + 1
-        const int nk = kc + kStages - 1;
-        if (kc >= 1 && nk < nch && nk >= issued) {
-          if (mbar_wait_bounded(&done[(kc - 1) % kStages], ((kc - 1) / kStages) & 1)) {
-            issue_copy(nk);
-            issued = nk + 1;
-          } else {
-            okc = false;
+        for (int t = 0; t < kDigits; ++t)
+          mma_bf16(acc + (uint32_t)(t * NBT), desc_interleave(a0 + t * kATileT, 2048, 128),
+                   desc_interleave(b0, 128, 256), idesc_f16(kRows, (kDigits - t) * NBT),
+                   (first && t == 0) ? 0u : 1u);
+        mma_commit(&done[slot]);
+        mma_commit(&bdone[bslot]);
+        if (kc % kGroupChunks == kGroupChunks - 1 || kc == nch - 1) mma_commit(&accdone[gg & 1]);
+        // refill the slot of chunk g - 1 (free once its MMAs are done) with chunk g + 3
+        const int ng = g + kStages - 1;
+        if (g >= 1 && ng < total && ng >= issued) {
+          ok = wait_or_abort(&done[(g - 1) % kStages], ((g - 1) / kStages) & 1, &s_abort);
+          if (ok) {
+            issue_copy(ng);
+            issued = ng + 1;
           }
         }
       }
-      t0_fail = !okc;
+      // copies still in flight land before the CTA's shared memory goes away
+      for (int g = got; g < issued; ++g) mbar_wait_bounded(&fullA[g % kStages], (g / kStages) & 1);
     }
-    if ((kc + 1) % kGroupChunks == 0 && kc + 1 < nrun) {
-      // the group ends with chunk kc: read it back before the next group overwrites it
-      const bool okr = mbar_wait_bounded(&done[slot], (kc / kStages) & 1);
-      if (__syncthreads_or(!okr || t0_fail)) {
-        timed_out = true;
-        break;
+  } else if (warp < kRead0) {
+    // ------------------------------------------------ per-block exponents and B' digits
+    // (after an abort every wait returns at once and the work is skipped, but the
+    // named barriers are still passed by all splitter threads)
+    constexpr int kSp = 32 * kSplitWarps;
+    const int sp = tid - 32 * kSplit0;          // 0..kSp-1
+    const int sw = warp - kSplit0;
+    // F pass: column j = lane, rows k = sw, sw + kSplitWarps, ...
+    for (int bi = 0; bi < nbl; ++bi) {
+      const int64_t b = blk_of(bi);
+      // this block's exponents (the previous block's splits are all done: same warps)
+      named_bar_sync(1, kSp);
+      if (!s_abort)
+        for (int k = sp; k < K; k += kSp) s_exp[k] = d.qs.exps[b * d.qs.ld_exp + k];
+      named_bar_sync(1, kSp);
+      // F of block bi (proj_fexp_kernel) goes to buffer bi & 1, free once block bi - 2 is unfolded
+      if (bi >= 2) wait_or_abort(&ffree[bi & 1], ((bi >> 1) - 1) & 1, &s_abort);
+      named_bar_sync(1, kSp);
+      if (sp < NBT && !s_abort) s_F[bi & 1][sp] = d.fexp[b * NBT + sp];
+      named_bar_sync(1, kSp);
+      if (sp == 0) mbar_arrive(&fready[bi & 1]);
+      const int* sF = s_F[bi & 1];
+      for (int kc = 0; kc < nch; ++kc) {
+        const int g = bi * nch + kc, slot = g % C::kBRing;
+        bool ok = true;
+        if (g >= C::kBRing)
+          ok = __all_sync(0xffffffffu, wait_or_abort(&bdone[slot], ((g / C::kBRing) - 1) & 1, &s_abort));
+        if (ok && !s_abort) {
+          uint8_t* dst = Bring + slot * C::kBStage;
+          // K-pairs e = sp, sp + kSp, ... -> column j, K-values kk, kk + 1
+#pragma unroll
+          for (int h = 0; h < (NBT * 8 + kSp - 1) / kSp; ++h) {
+            const int e = sp + kSp * h;
+            if (e < NBT * 8) {
+              const int el = e & 31, ew = e >> 5;
+              const int jl = el >> 2, pp = el & 3, jr = ew % (NBT / 8), gq = ew / (NBT / 8);
+              const int j = jr * 8 + jl, kk = gq * 8 + 2 * pp;
+              const int k = kc * kK + kk;
+              const bool jv = bcol(j) >= 0;
+              const bool v0 = jv && k < K, v1 = jv && k + 1 < K;
+              const double xy[2] = {v0 ? bval(k, j) : 0.0, v1 ? bval(k + 1, j) : 0.0};
+              const int exk[2] = {v0 ? s_exp[k] : 0, v1 ? s_exp[k + 1] : 0};
+              const int Fj = sF[j];
+              uint64_t nxy[2];
+#pragma unroll
+              for (int u = 0; u < 2; ++u) {
+                const uint64_t bits = (uint64_t)__double_as_longlong(xy[u]);
+                const int e2 = (int)((bits >> 52) & 0x7FF);
+                const bool nz = e2 != 0 && exk[u] != 0;
+                const int dd = Fj - (e2 + exk[u] - 1022);
+                const uint64_t mant = (bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+                const uint64_t mag = (nz && dd < 63) ? ((mant << 9) >> (dd > 0 ? dd : 0)) : 0ull;
+                nxy[u] = ((bits >> 63) ? (0ull - mag) : mag) + 0x8080808080808080ull;
+              }
+              uint32_t out[8];
+              digits_pair_f16((uint32_t)(nxy[0] >> 32), (uint32_t)nxy[0], (uint32_t)(nxy[1] >> 32),
+                              (uint32_t)nxy[1], out);
+              uint8_t* pp8 = dst + jr * 256 + gq * 128 + jl * 16 + pp * 4;
+#pragma unroll
+              for (int t = 0; t < kDigits; ++t) *reinterpret_cast<uint32_t*>(pp8 + t * C::kBTileT) = out[t];
+            }
+          }
+          fence_smem_to_async();
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&bready[slot]);
       }
-      tc_after_sync();
-      read_back();
-      tc_before_sync();
     }
-  }
-  if (!timed_out && nrun > 0) {
-    const bool okr = mbar_wait_bounded(&done[(nrun - 1) % kStages], ((nrun - 1) / kStages) & 1);
-    if (__syncthreads_or(!okr || t0_fail)) {
-      timed_out = true;
-    } else {
-      tc_after_sync();
-      read_back();
-    }
-  }
-  if (timed_out && tid == 0) {
-    // let the copies still in flight land before the CTA's shared memory goes away
-    for (int kc = waited; kc < issued; ++kc) mbar_wait_bounded(&full[kc % kStages], full_parity(kc));
-  }
-  __syncthreads();
-  const bool run = !bad && !timed_out;
-  if (run) {
-    const int i = 32 * (warp & 3) + lane;
+  } else {
+    // ------------------------------------------------ read-back and epilogue
+    // (same rule: after an abort the work is skipped, the named barriers are not)
+    const int rt = tid - 32 * kRead0;           // 0..255; TMEM quadrant warp % 4
+    const int half = (warp - kRead0) / 4;       // column half of the read-back
+    const int qrow = 32 * (warp & 3) + lane;    // TMEM lane = row of the block
+    const int my_j0 = half * kHalf;
+    for (int bi = 0; bi < nbl; ++bi) {
+      const int64_t b = blk_of(bi), r0 = b * kRows;
+      if constexpr (NOUT == 2) {
+        // this block's rows of V_1 toward L2 while the accumulators fill
+        const ProjOut& o1 = d.out[1];
+        if (half == 1 && o1.v != nullptr && r0 + qrow < d.m)
+          for (int j = 0; j < s; ++j)
+            asm volatile("prefetch.global.L2 [%0];\n" ::"l"(o1.v + r0 + qrow + (int64_t)j * o1.ldv));
+      }
+      long long hi[kHalf], lo[kHalf];
 #pragma unroll
-    for (int j = 0; j < kHalf; ++j) P[i * NBT + my_j0 + j] = fixed_to_double(hi[j], lo[j], s_F[my_j0 + j]);
-  }
-  __syncthreads();
-  // epilogue: one thread per (output, row)
-  const int o = tid >> 7, i = tid & (kRows - 1);
-  const int64_t r = r0 + i;
-  const bool mine = run && o < NOUT;
-  const bool live = mine && r < d.m;
-  const ProjOut& out = d.out[o < NOUT ? o : 0];
-  double w[SMAX];
+      for (int j = 0; j < kHalf; ++j) hi[j] = lo[j] = 0;
+      for (int grp = 0; grp < ngrp; ++grp) {
+        const int gg = bi * ngrp + grp;
+        const bool ok = __all_sync(0xffffffffu, wait_or_abort(&accdone[gg & 1], (gg >> 1) & 1, &s_abort));
+        if (ok && !s_abort) {
+          tc_after_sync();
+          const uint32_t addr =
+              tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)((gg & 1) * C::kAcc + my_j0);
 #pragma unroll
-  for (int j = 0; j < SMAX; ++j) w[j] = 0.0;
-  if (live) {
+          for (int g8 = 0; g8 < kHalf; g8 += 8) {
 #pragma unroll
-    for (int j = 0; j < SMAX; ++j)
-      if (j < s) w[j] = out.v != nullptr ? out.v[r + (int64_t)j * out.ldv] - P[i * NBT + o * s + j]
-                                         : P[i * NBT + o * s + j];
-  }
-  __syncthreads();  // every V (and E) read before any W, which may overwrite them, is written
-  if (live) {
-    if (o == NOUT - 1 && has_t) {
+            for (int hf = 0; hf < 2; ++hf) {
+              uint32_t r[4][8];
 #pragma unroll
-      for (int j = 0; j < SMAX; ++j) {
-        if (j < s) {
-          double x = w[j];
+              for (int l = 0; l < 4; ++l) tmem_ld8_nowait(addr + (uint32_t)((4 * hf + l) * NBT + g8), r[l]);
+              tmem_wait_ld();
 #pragma unroll
-          for (int l = 0; l < SMAX; ++l)
-            if (l < j) x = fma(-w[l], s_T[l * 32 + j], x);
-          w[j] = x * s_inv[j];
+              for (int j = 0; j < 8; ++j) {
+                const int32_t L0 = __float2int_rn(__uint_as_float(r[0][j]));
+                const int32_t L1 = __float2int_rn(__uint_as_float(r[1][j]));
+                const int32_t L2 = __float2int_rn(__uint_as_float(r[2][j]));
+                const int32_t L3 = __float2int_rn(__uint_as_float(r[3][j]));
+                if (hf == 0)
+                  hi[g8 + j] += ((long long)((L0 << 8) + L1) << 16) + (long long)((L2 << 8) + L3);
+                else
+                  lo[g8 + j] +=
+                      ((long long)L0 << 24) + ((long long)L1 << 16) + ((long long)L2 << 8) + (long long)L3;
+              }
+            }
+          }
+          tc_before_sync();
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&accfree[gg & 1]);
+      }
+      const bool fok = __all_sync(0xffffffffu, wait_or_abort(&fready[bi & 1], (bi >> 1) & 1, &s_abort));
+      const int* sF = s_F[bi & 1];
+      if constexpr (NOUT == 2) {
+        // this warp's output (half) of row qrow, straight from the accumulators
+        const int o = half;
+        const int64_t r = r0 + qrow;
+        const bool live = fok && !s_abort && r < d.m;
+        const ProjOut& out = d.out[o];
+        double w[kHalf];
+#pragma unroll
+        for (int j = 0; j < kHalf; ++j)
+          w[j] = (live && j < s) ? fixed_to_double(hi[j], lo[j], sF[my_j0 + j]) : 0.0;
+        named_bar_sync(2, 32 * kReadWarps);
+        if (rt == 0) mbar_arrive(&ffree[bi & 1]);
+        if (live) {
+          if (out.v != nullptr) {
+#pragma unroll
+            for (int j = 0; j < kHalf; ++j)
+              if (j < s) w[j] = out.v[r + (int64_t)j * out.ldv] - w[j];
+          }
+          if (o == NOUT - 1 && has_t) {
+#pragma unroll
+            for (int j = 0; j < kHalf; ++j) {
+              if (j < s) {
+                double x = w[j];
+#pragma unroll
+                for (int l = 0; l < kHalf; ++l)
+                  if (l < j) x = fma(-w[l], s_T[l * 32 + j], x);
+                w[j] = x * s_inv[j];
+              }
+            }
+          }
+#pragma unroll
+          for (int j = 0; j < kHalf; ++j)
+            if (j < s) out.w[r + (int64_t)j * out.ldw] = w[j];
+          if (out.wmax.row != nullptr) {
+            unsigned long long mx = 0ull;
+#pragma unroll
+            for (int j = 0; j < kHalf; ++j)
+              if (j < s) mx = umax64(mx, abs_bits64(w[j]));
+            out.wmax.row[r] = umax64(out.wmax.row[r], mx);
+          }
+        }
+        if (out.wmax.col != nullptr) {  // warp-uniform: o is
+#pragma unroll
+          for (int j = 0; j < kHalf; ++j)
+            if (j < s) warp_max_to(live ? abs_bits64(w[j]) : 0ull, out.wmax.col + j);
+        }
+      } else {
+        // one output: the two halves of a row meet in P, one thread per row
+        if (fok && !s_abort) {
+#pragma unroll
+          for (int j = 0; j < kHalf; ++j)
+            P[qrow * NBT + my_j0 + j] = fixed_to_double(hi[j], lo[j], sF[my_j0 + j]);
+        }
+        named_bar_sync(2, 32 * kReadWarps);
+        if (rt == 0) mbar_arrive(&ffree[bi & 1]);
+        const int i = rt & (kRows - 1);
+        const int64_t r = r0 + i;
+        const bool mine = rt < kRows;
+        const bool live = mine && r < d.m && fok && !s_abort;
+        const ProjOut& out = d.out[0];
+        double w[SMAX];
+#pragma unroll
+        for (int j = 0; j < SMAX; ++j) w[j] = 0.0;
+        if (live) {
+#pragma unroll
+          for (int j = 0; j < SMAX; ++j)
+            if (j < s) w[j] = out.v != nullptr ? out.v[r + (int64_t)j * out.ldv] - P[i * NBT + j] : P[i * NBT + j];
+        }
+        named_bar_sync(2, 32 * kReadWarps);  // P read before the next block writes it
+        if (live) {
+          if (has_t) {
+#pragma unroll
+            for (int j = 0; j < SMAX; ++j) {
+              if (j < s) {
+                double x = w[j];
+#pragma unroll
+                for (int l = 0; l < SMAX; ++l)
+                  if (l < j) x = fma(-w[l], s_T[l * 32 + j], x);
+                w[j] = x * s_inv[j];
+              }
+            }
+          }
+#pragma unroll
+          for (int j = 0; j < SMAX; ++j)
+            if (j < s) out.w[r + (int64_t)j * out.ldw] = w[j];
+          if (out.wmax.row != nullptr) {
+            unsigned long long mx = 0ull;
+#pragma unroll
+            for (int j = 0; j < SMAX; ++j)
+              if (j < s) mx = umax64(mx, abs_bits64(w[j]));
+            out.wmax.row[r] = umax64(out.wmax.row[r], mx);
+          }
+        }
+        if (mine && out.wmax.col != nullptr) {  // warp-uniform: rt < 128 is
+#pragma unroll
+          for (int j = 0; j < SMAX; ++j)
+            if (j < s) warp_max_to(live ? abs_bits64(w[j]) : 0ull, out.wmax.col + j);
         }
       }
     }
-#pragma unroll
-    for (int j = 0; j < SMAX; ++j)
-      if (j < s) out.w[r + (int64_t)j * out.ldw] = w[j];
-    if (out.wmax.row != nullptr) {
-      unsigned long long mx = 0ull;
-#pragma unroll
-      for (int j = 0; j < SMAX; ++j)
-        if (j < s) mx = umax64(mx, abs_bits64(w[j]));
-      out.wmax.row[r] = umax64(out.wmax.row[r], mx);
-    }
   }
-  if (mine && out.wmax.col != nullptr) {  // warp-uniform: o and run are
-#pragma unroll
-    for (int j = 0; j < SMAX; ++j)
-      if (j < s) warp_max_to(live ? abs_bits64(w[j]) : 0ull, out.wmax.col + j);
-  }
-  if (bad && tid == 0) set_failure(st, BCGS_ERR_NONFINITE, d.block);
-  if (timed_out && tid == 0) set_failure(st, BCGS_ERR_TIMEOUT, d.block);
   tc_before_sync();
   __syncthreads();
-  if (warp == 0) tmem_dealloc<C::kTmem>(tmem);
+  if (tid == 0) {
+    if (s_bad) set_failure(st, BCGS_ERR_NONFINITE, d.block);
+    else if (s_abort) set_failure(st, BCGS_ERR_TIMEOUT, d.block);
+  }
+  if (warp == kCtl) tmem_dealloc<C::kTmem>(tmem);
 }
 
-template <int NBT, int NOUT, bool EXT>
+int g_sm_count = 0;
+
+template <int NBT, int NOUT>
 cudaError_t launch_sp(const StoreProjDesc& d, DevStatus* st, cudaStream_t stream) {
-  const size_t smem = SPCfg<NBT, NOUT, EXT>::kSmem;
-  cudaError_t e = ensure_dyn_smem(proj_store_kernel<NBT, NOUT, EXT>, smem);
+  using C = SPCfg<NBT, NOUT>;
+  const size_t bbytes = (size_t)(NBT + 4) * (size_t)d.c * sizeof(double);
+  const int32_t staged = C::kFixed + bbytes <= kSmemLimit ? 1 : 0;
+  const size_t smem = C::kFixed + (staged ? bbytes : 0);
+  cudaError_t e = ensure_dyn_smem(proj_store_kernel<NBT, NOUT>, smem);
   if (e != cudaSuccess) return e;
-  proj_store_kernel<NBT, NOUT, EXT><<<(unsigned)d.qs.nblk, kThreads, smem, stream>>>(d, st);
+  int sms = g_sm_count;
+  if (sms <= 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      sms = 152;
+    g_sm_count = sms;
+  }
+  const size_t fsmem = (size_t)d.c * NBT * sizeof(int16_t);
+  e = ensure_dyn_smem(proj_fexp_kernel<NBT, NOUT>, fsmem);
+  if (e != cudaSuccess) return e;
+  const int64_t fgrid = ceil_div(d.qs.nblk, 8);
+  proj_fexp_kernel<NBT, NOUT><<<(unsigned)(fgrid < 4 * sms ? fgrid : 4 * sms), 256, fsmem, stream>>>(d, st);
+  const unsigned grid = (unsigned)(d.qs.nblk < sms ? d.qs.nblk : (int64_t)sms);
+  proj_store_kernel<NBT, NOUT><<<grid, kThreads, smem, stream>>>(d, staged, st);
   return cudaSuccess;
 }
 
@@ -532,27 +620,26 @@ cudaError_t launch_qsplit(const QStore& qs, const double* src, int64_t lds, cons
   return cudaGetLastError();
 }
 
-bool project_store_supported(int32_t s, int32_t nouts, int32_t next) {
-  if (s < 1 || next < 0 || next > 16) return false;
-  if (nouts == 2) return s <= 16;
-  return nouts == 1 && (next > 0 ? s <= 16 : s <= 32);
+bool project_store_supported(int32_t s, int32_t nouts) {
+  if (s < 1) return false;
+  return nouts == 2 ? s <= 16 : (nouts == 1 && s <= 32);
 }
 
 cudaError_t launch_project_store(const StoreProjDesc& d, DevStatus* st, cudaStream_t stream) {
-  if (!project_store_supported(d.s, d.nouts, d.next) || d.c < 0 || d.c + d.next > kExpInts - 64 ||
-      d.qs.nblk < ceil_div(d.m, kRows))
+  if (!project_store_supported(d.s, d.nouts) || d.c < 0 || d.c > kExpInts - 64 || d.c > d.qs.ld_exp ||
+      d.qs.nblk < ceil_div(d.m, kRows) || d.fexp == nullptr)
     return cudaErrorInvalidValue;
   for (int o = 0; o + 1 < d.nouts; ++o)
     if (d.out[o].T != nullptr) return cudaErrorInvalidValue;  // only the last output has a solve
   if (d.m == 0) return cudaSuccess;
   const int slot = prof_begin(stream);
   cudaError_t e;
-  if (d.nouts == 2) e = launch_sp<32, 2, true>(d, st, stream);
-  else if (d.next > 0) e = launch_sp<16, 1, true>(d, st, stream);
-  else if (d.s <= 16) e = launch_sp<16, 1, false>(d, st, stream);
-  else e = launch_sp<32, 1, false>(d, st, stream);
+  if (d.nouts == 2) e = launch_sp<32, 2>(d, st, stream);
+  else if (d.s <= 16) e = launch_sp<16, 1>(d, st, stream);
+  else e = launch_sp<32, 1>(d, st, stream);
   if (e != cudaSuccess) return e;
-  const double K = (double)d.c + d.next, nw = (double)d.nouts * d.s;
+  note_launch(1);  // the exponent kernel
+  const double K = (double)d.c, nw = (double)d.nouts * d.s;
   double nv = 0;
   for (int o = 0; o < d.nouts; ++o) nv += d.out[o].v != nullptr ? d.s : 0;
   prof_end(slot, kProfProject, stream, 2.0 * (double)d.m * K * nw + (double)d.m * d.s * d.s,

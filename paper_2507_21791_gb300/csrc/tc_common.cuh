@@ -63,13 +63,17 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
+// One bounded wait on the phase: the thread is suspended until the phase
+// completes or about a microsecond has passed (suspend-time hint, in ns), so a
+// waiting warp takes no issue slots from the working warps of its sub-partition.
 __device__ __forceinline__ bool mbar_try(uint32_t mbar, uint32_t phase) {
   uint32_t ok;
   asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
       " selp.u32 %0, 1, 0, p;\n}\n"
       : "=r"(ok)
-      : "r"(mbar), "r"(phase));
+      : "r"(mbar), "r"(phase), "r"(1000u)
+      : "memory");
   return ok != 0;
 }
 
@@ -264,47 +268,42 @@ __device__ __forceinline__ double unfold62(long long hi, long long lo, int F) {
 }
 
 // The double nearest to (hi 2^32 + lo) 2^(F - 1090) (round to nearest, ties to
-// even), built from the exact integer with integer operations only (no FP64
-// pipe work; GB300's FP64 rate is low).  Results outside the normal range take
-// the ldexp route.
+// even), built from the exact integer with integer operations and selects only
+// (no FP64 pipe work, no divergent branches; GB300's FP64 rate is low).  Results
+// outside the normal range take the ldexp route.
 __device__ __forceinline__ double fixed_to_double(long long hi, long long lo, int F) {
-  // v = hi 2^32 + lo as a 128-bit two's complement integer (vh, vl)
-  const unsigned long long a = (unsigned long long)hi << 32;
-  const unsigned long long vl0 = a + (unsigned long long)lo;
-  long long vh = (hi >> 32) + (lo >> 63) + (vl0 < a ? 1 : 0);
-  unsigned long long vl = vl0;
-  const bool neg = vh < 0;
-  if (neg) {
-    vl = ~vl + 1ull;
-    vh = (long long)(~(unsigned long long)vh + (vl == 0ull ? 1ull : 0ull));
-  }
-  const unsigned long long uh = (unsigned long long)vh;
-  if (uh == 0ull && vl == 0ull) return 0.0;
-  const int lz = uh != 0ull ? __clzll((long long)uh) : 64 + __clzll((long long)vl);
-  unsigned long long th, tl;  // v << lz: leading one at bit 127
-  if (lz >= 64) {
-    th = vl << (lz - 64);
-    tl = 0ull;
-  } else if (lz == 0) {
-    th = uh;
-    tl = vl;
-  } else {
-    th = (uh << lz) | (vl >> (64 - lz));
-    tl = vl << lz;
-  }
-  unsigned long long mant = th >> 11;  // 53 bits
-  const bool rnd = (th >> 10) & 1ull;
-  const bool sticky = (th & 0x3FFull) != 0ull || tl != 0ull;
-  mant += (rnd && (sticky || (mant & 1ull))) ? 1ull : 0ull;
-  int p = 127 - lz;
-  if (mant >> 53) {
-    mant >>= 1;
-    ++p;
-  }
-  const int be = p + F - 1090 + 1023;
+  // v = H 2^32 + L with 0 <= L < 2^32, |v| < 2^95, as the 128-bit (vh, vl)
+  const long long H = hi + (lo >> 32);
+  const unsigned long long L = (unsigned long long)lo & 0xFFFFFFFFull;
+  const unsigned long long sgn = (unsigned long long)(H >> 63);  // 0 or all ones
+  unsigned long long vl = ((unsigned long long)H << 32) | L;
+  unsigned long long vh = (unsigned long long)(H >> 32);
+  // |v| = (v ^ sgn) + (sgn & 1)
+  vl ^= sgn;
+  vh ^= sgn;
+  const unsigned long long vl2 = vl + (sgn & 1ull);
+  vh += vl2 < vl ? 1ull : 0ull;
+  vl = vl2;
+  const bool hv = vh != 0ull;
+  const int lzh = __clzll((long long)vh);  // 33..63 when hv
+  const int lzl = __clzll((long long)vl);
+  const int n = hv ? lzh : 33;
+  // the 64 bits from the leading one down, and whether anything below them is set
+  const unsigned long long top = hv ? ((vh << n) | (vl >> (64 - n))) : (vl << (lzl & 63));
+  const unsigned long long rest = hv ? (vl << n) : 0ull;
+  const int lz = hv ? lzh : 64 + lzl;
+  unsigned long long mant = top >> 11;  // 53 bits
+  const unsigned long long rnd = (top >> 10) & 1ull;
+  const unsigned long long sticky = ((top & 0x3FFull) | rest) != 0ull ? 1ull : 0ull;
+  mant += rnd & (sticky | (mant & 1ull));
+  const unsigned long long carry = mant >> 53;
+  mant >>= carry;
+  const int be = 127 - lz + (int)carry + F - 1090 + 1023;
+  const double r = __longlong_as_double((long long)((sgn << 63) | ((unsigned long long)(be & 0x7FF) << 52) |
+                                                    (mant & 0xFFFFFFFFFFFFFull)));
+  if (!hv && vl == 0ull) return 0.0;
   if (be <= 0 || be >= 2047) return ldexp((double)hi, F - 1058) + ldexp((double)lo, F - 1090);
-  return __longlong_as_double((long long)(((unsigned long long)neg << 63) | ((unsigned long long)be << 52) |
-                                          (mant & 0xFFFFFFFFFFFFFull)));
+  return r;
 }
 
 // Tensor-memory allocation of NCOLS (power of two, 32..512) columns by one warp.
@@ -332,6 +331,10 @@ __device__ __forceinline__ void mbar_init_count(uint64_t* mbar, uint32_t count) 
 }
 __device__ __forceinline__ void mbar_arrive(uint64_t* mbar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(mbar)) : "memory");
+}
+// Barrier `id` (1..15) over `count` threads (a multiple of 32) of the CTA.
+__device__ __forceinline__ void named_bar_sync(int id, int count) {
+  asm volatile("bar.sync %0, %1;\n" ::"r"(id), "r"(count) : "memory");
 }
 // Poll the barrier's phase `phase` for at most kWaitCycles; true when it completed.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* mbar, uint32_t phase) {

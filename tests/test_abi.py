@@ -65,7 +65,9 @@ def test_workspace_size_queries():
     finally:
         bcgs.set_gram_engine(old)
     assert 2 ** 22 * 16 * 8 < small < 2 ** 22 * 16 * 8 * 3
-    store = 2 ** 22 * 256 * 16 + (2 ** 22 // 128) * 256 * 4
+    # digits, one exponent per 128 rows and column, and 32 exponents per row
+    # block for the coefficient side of the projections
+    store = 2 ** 22 * 256 * 16 + (2 ** 22 // 128) * 256 * 4 + (2 ** 22 // 128) * 32 * 4
     assert big - small == pytest.approx(store, abs=2 ** 12)
     assert fp32 < small   # no store with FP32 storage
 
