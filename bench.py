@@ -82,6 +82,8 @@ def parse():
     p.add_argument("--kernel", default=None, choices=["gram", "project", "tsqr"],
                    help="time one building block alone (for profiling on small cases)")
     p.add_argument("--m", type=int, default=2 ** 19, help="rows for --kernel")
+    p.add_argument("--rows", type=int, default=None,
+                   help="rows of the factorization (default 2^22; smaller for profiling captures)")
     p.add_argument("--engine", default="auto", choices=["auto", "fp64", "tensor"],
                    help="inner-product engine of the Gram and projection kernels")
     return p.parse_args()
@@ -180,6 +182,7 @@ class ClockSampler:
 # ------------------------------------------------------------------ GPU arm
 
 def main_ours(args):
+    Mr = args.rows if args.rows else M  # rows of the factorization
     import numpy as np
     import torch
     import torch.distributed as dist
@@ -212,13 +215,13 @@ def main_ours(args):
     bcgs.set_gram_engine(args.engine)
     engine = args.engine
     stream = torch.cuda.current_stream(dev)
-    X = synth.make_matrix_torch(M, N, KAPPA, seed=1000 + 1 * 100 + rank, device=str(dev))
+    X = synth.make_matrix_torch(Mr, N, KAPPA, seed=1000 + 1 * 100 + rank, device=str(dev))
     torch.cuda.synchronize()
 
     def run_variant(variant, profile=False):
-        Q = bcgs.empty_colmajor(M, N, torch.float64, dev)
+        Q = bcgs.empty_colmajor(Mr, N, torch.float64, dev)
         R = bcgs.empty_colmajor(N, N, torch.float64, dev)
-        ws = torch.empty(bcgs.workspace_size(M, N, S, variant), dtype=torch.uint8, device=dev)
+        ws = torch.empty(bcgs.workspace_size(Mr, N, S, variant), dtype=torch.uint8, device=dev)
         for _ in range(args.warmup):
             bcgs.factor_async(X, S, variant, "fp64", Q, R, ws)
         code, blk = bcgs.factor_status(ws)
@@ -262,16 +265,16 @@ def main_ours(args):
     if world > 1:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     ms_max = t.item()
-    value = world * alg_bytes_1s(M, N, S) / (ms_max * 1e-3) / 1e9
+    value = world * alg_bytes_1s(Mr, N, S) / (ms_max * 1e-3) / 1e9
 
     # e2e through the public API with pinned host buffers
-    Xh = torch.empty((N, M), dtype=torch.float64, pin_memory=True).T
+    Xh = torch.empty((N, Mr), dtype=torch.float64, pin_memory=True).T
     Xh.copy_(X)
-    Qh = torch.empty((N, M), dtype=torch.float64, pin_memory=True).T
+    Qh = torch.empty((N, Mr), dtype=torch.float64, pin_memory=True).T
     Rh = torch.empty((N, N), dtype=torch.float64, pin_memory=True).T
-    Xd = bcgs.empty_colmajor(M, N, torch.float64, dev)
+    Xd = bcgs.empty_colmajor(Mr, N, torch.float64, dev)
     Qd, Rd = main["Q"], main["R"]
-    ws = torch.empty(bcgs.workspace_size(M, N, S, "bcgsi+p-1s"), dtype=torch.uint8, device=dev)
+    ws = torch.empty(bcgs.workspace_size(Mr, N, S, "bcgsi+p-1s"), dtype=torch.uint8, device=dev)
 
     def e2e_step():
         Xd.copy_(Xh, non_blocking=True)
@@ -292,7 +295,7 @@ def main_ours(args):
     te = torch.tensor([ms_e2e], dtype=torch.float64, device=dev)
     if world > 1:
         dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_value = world * alg_bytes_1s(M, N, S) / (te.item() * 1e-3) / 1e9
+    e2e_value = world * alg_bytes_1s(Mr, N, S) / (te.item() * 1e-3) / 1e9
     del ws, Xd, Xh, Qh, Rh
 
     compare = {}
@@ -319,8 +322,10 @@ def main_ours(args):
     # dominant kernel class of the timed region (by summed event time)
     dom = max(("gram_partial", "project"), key=lambda k: prof[k][1])
     gl, gms, gfl, gby = prof[dom]
-    kernel_name = {"gram_partial": "gram_tc_kernel" if engine != "fp64" else "gram_partial_kernel",
-                   "project": "proj_tc_kernel" if engine != "fp64" else "project_kernel"}[dom]
+    # with the tensor engine at this size the factorization keeps Q as digit tiles
+    # (the store) and both kernel classes read it
+    kernel_name = {"gram_partial": "gram_store_kernel" if engine != "fp64" else "gram_partial_kernel",
+                   "project": "proj_store_kernel" if engine != "fp64" else "project_kernel"}[dom]
     if engine == "fp64":
         achieved = gfl / (gms * 1e-3) / 1e12
         roofline = {"bound": "alu", "kernel": kernel_name + " (FP64 DFMA)", "achieved": achieved,
@@ -328,7 +333,8 @@ def main_ours(args):
                     "peak_source": "FP64 rate of the profiling recipe (nominal; a DFMA probe measured 1.20)"}
     else:
         achieved = gby / (gms * 1e-3) / 1e9
-        roofline = {"bound": "hbm", "kernel": kernel_name + " (exact bf16 digit products on tcgen05)",
+        roofline = {"bound": "hbm", "kernel": kernel_name + " (exact f16 digit products on tcgen05, "
+                                                          "operands from the resident digit store)",
                     "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                     "frac": achieved / peaks["hbm_gbs"], "peak_source": peaks["source"],
                     "fp64_equivalent_tflops": gfl / (gms * 1e-3) / 1e12}
@@ -341,7 +347,7 @@ def main_ours(args):
         "step_hbm_frac_of_measured_copy": value / peaks["hbm_gbs"],
     })
     others = {}
-    for k in ("gram_partial", "project", "tsqr"):
+    for k in ("gram_partial", "project", "tsqr", "store_split"):
         n_, ms_, fl_, by_ = prof[k]
         if ms_ > 0:
             others[k] = {"ms_per_step": ms_ / args.steps, "alg_gbs": by_ / (ms_ * 1e-3) / 1e9,
@@ -354,11 +360,12 @@ def main_ours(args):
         "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "m": M, "n": N, "s": S, "kappa": KAPPA,
+        "config": {"workload": WORKLOAD if Mr == M else WORKLOAD.replace("m=2^22", f"m={Mr}"),
+                   "m": Mr, "n": N, "s": S, "kappa": KAPPA,
                    "variant": "bcgsi+p-1s", "parallelism": "replicas" if world > 1 else "single",
                    "l2": "inputs larger than L2 (X and Q 8.6 GB each); no flush"},
-        "e2e": {"value": e2e_value, "unit": "GB/s", "h2d_bytes_per_step": M * N * 8,
-                "d2h_bytes_per_step": M * N * 8 + N * N * 8, "ms_per_step": te.item()},
+        "e2e": {"value": e2e_value, "unit": "GB/s", "h2d_bytes_per_step": Mr * N * 8,
+                "d2h_bytes_per_step": Mr * N * 8 + N * N * 8, "ms_per_step": te.item()},
         "gpu_launches": main["launches"],
         "roofline": roofline,
         "kernels": others,
