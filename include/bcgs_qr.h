@@ -84,7 +84,12 @@ BCGS_API int bcgs_version(void);
 /* Bytes of device workspace needed by a factorization (or a handle) of an
  * m x n_max matrix with block size s.  Requirements: 1 <= s <= 64, n_max <= m,
  * n_max a multiple of s, n_max <= 2048.  Writes *bytes; returns BCGS_OK or
- * BCGS_ERR_INVALID_ARG. */
+ * BCGS_ERR_INVALID_ARG.  With FP64 storage, s <= 32 and the tensor engine
+ * selected for m rows (BCGS_OPT_GRAM_ENGINE below) the size includes the digit
+ * store of Q: 16 bytes per element of the m x n_max basis (rounded up to 128
+ * columns), one 32-bit exponent per 128 rows and column, and 32 more per 128
+ * rows.  A factorization given a workspace sized without the store (for example
+ * under the FP64 engine) runs without it. */
 BCGS_API int bcgs_qr_workspace_size(int64_t m, int32_t n_max, int32_t s, int variant,
                            int precision, size_t* bytes);
 
@@ -242,10 +247,16 @@ BCGS_API int bcgs_chol(int32_t s, const double* A, int32_t lda, double* R, int32
  *      projection s <= 32): each FP64 (or FP32) operand
  *      is split exactly into eight 8-bit integer digits relative to the
  *      maximum along its contraction line (a column of a Gram operand, a row
- *      of Q), digit pairs are multiplied on the bf16 tensor cores
+ *      of Q), digit pairs are multiplied on the tensor cores
  *      with exact integer sums, and one FP64 rounding per row chunk remains
- *      (error per product term <= 2^-57.1 max|a_i| max|b_j|);
+ *      (error per product term <= 2^-57.1 max|a_i| max|b_j|).  A factorization
+ *      with FP64 storage and s <= 32 keeps Q as such digits (balanced digits in
+ *      [-128, 127], one exponent per 128 rows and column, error per term
+ *      <= 2^-56.8 max|a| max|b| over the 128-row block) and computes its Grams
+ *      (s a multiple of 8) and projections from them;
  *   2  tensor cores whenever the shape allows it.
+ * A factorization reads the engine when it is initialized (bcgs_qr_init,
+ * bcgs_qr_factor): that fixes whether it keeps the digit store.
  * BCGS_OPT_TC_MIN_ROWS is the row threshold of engine 1 (default 16384).
  * Both engines use the same row partition, so each is deterministic; they
  * differ by rounding.  Returns BCGS_ERR_INVALID_ARG for an unknown option or
