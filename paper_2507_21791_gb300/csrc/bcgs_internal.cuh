@@ -212,6 +212,7 @@ struct TsqrPlan {
   int32_t nlevels;       // leaf level + node levels (root has 1 node)
   int32_t nodes[32];     // nodes per level (level 0 = leaf tiles)
   size_t off_h;          // leaf reflectors: nodes[0] * mt * s doubles
+  size_t off_t0;         // leaf WY triangles T (H_0 ... H_{s-1} = I - V T V^T): nodes[0] * s * s
   size_t off_tau[32];    // taus per level: nodes * s
   size_t off_lvl[32];    // node-level stacked matrices (level >= 1): nodes * (fan*s) * s
   size_t off_b[32];      // apply-phase coefficient blocks per level: nodes * s * s

@@ -30,6 +30,21 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
+// sum over r = r0, r0 + 32, ... < rows of a[r] b[r], in four interleaved
+// accumulators (a fixed order: the result depends on the shape only)
+__device__ __forceinline__ double dot4(const double* a, const double* b, int r0, int rows) {
+  double w0 = 0.0, w1 = 0.0, w2 = 0.0, w3 = 0.0;
+  int r = r0;
+  for (; r + 96 < rows; r += 128) {
+    w0 = fma(a[r], b[r], w0);
+    w1 = fma(a[r + 32], b[r + 32], w1);
+    w2 = fma(a[r + 64], b[r + 64], w2);
+    w3 = fma(a[r + 96], b[r + 96], w3);
+  }
+  for (; r < rows; r += 32) w0 = fma(a[r], b[r], w0);
+  return (w0 + w1) + (w2 + w3);
+}
+
 // In-place Householder QR of the rows x s column-major matrix A (ld = rows) in
 // shared memory.  On return A holds R in its upper triangle and v_j below the
 // diagonal (v_j has an implicit 1 at row j); tau[j] the reflector scalars.
@@ -38,9 +53,7 @@ __device__ void block_householder(double* A, int rows, int s, double* tau) {
   for (int j = 0; j < s; ++j) {
     double* aj = A + (size_t)j * rows;
     if (warp == 0) {
-      double sum = 0.0;
-      for (int r = j + 1 + lane; r < rows; r += 32) sum = fma(aj[r], aj[r], sum);
-      sum = warp_sum(sum);
+      const double sum = warp_sum(dot4(aj, aj, j + 1 + lane, rows));
       const double x0 = aj[j];
       const double alpha = sqrt(fma(x0, x0, sum));
       double t = 0.0, beta = 0.0, denom = 1.0;
@@ -49,8 +62,10 @@ __device__ void block_householder(double* A, int rows, int s, double* tau) {
         denom = x0 - beta;
         t = (beta - x0) / beta;
       }
-      if (alpha != 0.0)
-        for (int r = j + 1 + lane; r < rows; r += 32) aj[r] = aj[r] / denom;
+      if (alpha != 0.0) {
+        const double rden = 1.0 / denom;  // one FP64 division per column
+        for (int r = j + 1 + lane; r < rows; r += 32) aj[r] *= rden;
+      }
       __syncwarp();
       if (lane == 0) {
         tau[j] = t;
@@ -62,9 +77,7 @@ __device__ void block_householder(double* A, int rows, int s, double* tau) {
     if (t != 0.0) {
       for (int l = j + 1 + warp; l < s; l += kWarps) {
         double* al = A + (size_t)l * rows;
-        double w = 0.0;
-        for (int r = j + 1 + lane; r < rows; r += 32) w = fma(aj[r], al[r], w);
-        w = warp_sum(w) + al[j];
+        double w = warp_sum(dot4(aj, al, j + 1 + lane, rows)) + al[j];
         w *= t;
         __syncwarp();  // every lane has read al[j] before lane 0 updates it
         if (lane == 0) al[j] -= w;
@@ -84,9 +97,7 @@ __device__ void block_apply_q(const double* V, const double* tau, double* E, int
       const double* vj = V + (size_t)j * rows;
       for (int c = warp; c < s; c += kWarps) {
         double* ec = E + (size_t)c * rows;
-        double w = 0.0;
-        for (int r = j + 1 + lane; r < rows; r += 32) w = fma(vj[r], ec[r], w);
-        w = warp_sum(w) + ec[j];
+        double w = warp_sum(dot4(vj, ec, j + 1 + lane, rows)) + ec[j];
         w *= t;
         __syncwarp();
         if (lane == 0) ec[j] -= w;
@@ -142,6 +153,36 @@ tsqr_leaf_factor(TsqrPlan p, Seg a, double* work, double* R, int32_t ldr, DevSta
   for (int e = threadIdx.x; e < mt * s; e += kTsqrThreads) H[e] = A[e];
   double* tg = work + p.off_tau[0] + (size_t)t * s;
   for (int j = threadIdx.x; j < s; j += kTsqrThreads) tg[j] = tau[j];
+  // WY triangle of the leaf: H_0 ... H_{s-1} = I - V T V^T (forward, columnwise)
+  {
+    double* VV = A + (size_t)mt * s;  // s x s: (V^T V)_{ij} for i < j
+    double* Tl = VV + (size_t)s * s;
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    // (V^T V)_ij = v_i[j] + sum_{r > j} v_i[r] v_j[r]  (v_j[j] = 1, v_j[r < j] = 0)
+    for (int e = warp; e < s * s; e += kWarps) {
+      const int i = e % s, j = e / s;
+      if (i < j) {
+        const double* vi = A + (size_t)i * mt;
+        const double* vj = A + (size_t)j * mt;
+        const double d = warp_sum(dot4(vi, vj, j + 1 + lane, mt));
+        if (lane == 0) VV[i + (size_t)j * s] = d + vi[j];
+      }
+    }
+    __syncthreads();
+    // T(i, j) = -tau_j sum_{l = i}^{j-1} T(i, l) (V^T V)(l, j), T(j, j) = tau_j:
+    // column by column, the rows of a column in parallel
+    for (int j = 0; j < s; ++j) {
+      for (int i = threadIdx.x; i < s; i += kTsqrThreads) {
+        double x = 0.0;
+        if (i < j)
+          for (int l = i; l < j; ++l) x = fma(Tl[i + (size_t)l * s], VV[l + (size_t)j * s], x);
+        Tl[i + (size_t)j * s] = i < j ? -tau[j] * x : (i == j ? tau[j] : 0.0);
+      }
+      __syncthreads();
+    }
+    double* tw = work + p.off_t0 + (size_t)t * s * s;
+    for (int e = threadIdx.x; e < s * s; e += kTsqrThreads) tw[e] = Tl[e];
+  }
   if (p.nlevels == 1) {
     finish_root(A, mt, s, R, ldr, work + p.off_b[0], st, block);
     return;
@@ -221,28 +262,65 @@ __global__ void __launch_bounds__(kTsqrThreads)
 tsqr_leaf_apply(TsqrPlan p, const double* work, void* q, int64_t ldq, const DevStatus* st, MaxOut qmax) {
   if (failed(st)) return;
   extern __shared__ double sm[];
-  __shared__ double tau[64];
   const int mt = p.mt, s = p.s;
   const int t = blockIdx.x;
-  double* V = sm;
-  double* E = sm + (size_t)mt * s;
+  // E = H_0 ... H_{s-1} [B; 0] = [B; 0] - V (T (V_top^T B))  (compact WY: one row-wise
+  // product instead of s reflector sweeps with reductions)
+  double* V = sm;                     // mt x s (reflectors below the diagonal)
+  double* Bs = V + (size_t)mt * s;    // s x s coefficient block from the parent
+  double* Tl = Bs + (size_t)s * s;    // s x s WY triangle
+  double* W = Tl + (size_t)s * s;     // s x s: V_top^T B, then M = T W
+  double* E = W + (size_t)s * s;      // mt x s output (for the maxima)
   const double* H = work + p.off_h + (size_t)t * mt * s;
   const double* B = work + p.off_b[0] + (size_t)t * s * s;
-  for (int e = threadIdx.x; e < mt * s; e += kTsqrThreads) {
-    const int r = e % mt, j = e / mt;
-    V[e] = H[e];
-    E[e] = r < s ? B[r + (size_t)j * s] : 0.0;
+  const double* Tg = work + p.off_t0 + (size_t)t * s * s;
+  for (int e = threadIdx.x; e < mt * s; e += kTsqrThreads) V[e] = H[e];
+  for (int e = threadIdx.x; e < s * s; e += kTsqrThreads) {
+    Bs[e] = B[e];
+    Tl[e] = Tg[e];
   }
-  for (int j = threadIdx.x; j < s; j += kTsqrThreads) tau[j] = work[p.off_tau[0] + (size_t)t * s + j];
   __syncthreads();
-  block_apply_q(V, tau, E, mt, s);
+  // W = V_top^T B: V_top(i, l) = 1 (i = l), V(i, l) (i > l), 0 (i < l)
+  for (int e = threadIdx.x; e < s * s; e += kTsqrThreads) {
+    const int l = e % s, c = e / s;
+    double x = Bs[l + (size_t)c * s];
+    for (int i = l + 1; i < s; ++i) x = fma(V[i + (size_t)l * mt], Bs[i + (size_t)c * s], x);
+    E[e] = x;  // scratch until W is final
+  }
+  __syncthreads();
+  // M = T W (T upper triangular)
+  for (int e = threadIdx.x; e < s * s; e += kTsqrThreads) {
+    const int l = e % s, c = e / s;
+    double x = 0.0;
+    for (int i = l; i < s; ++i) x = fma(Tl[l + (size_t)i * s], E[i + (size_t)c * s], x);
+    W[e] = x;
+  }
+  __syncthreads();
   const int64_t row0 = (int64_t)t * mt;
   const int rows_here = (int)(p.m - row0 < (int64_t)mt ? p.m - row0 : (int64_t)mt);
   T* dst = reinterpret_cast<T*>(q);
-  for (int e = threadIdx.x; e < mt * s; e += kTsqrThreads) {
-    const int r = e % mt, j = e / mt;
-    if (r < rows_here) dst[row0 + r + (int64_t)j * ldq] = (T)E[e];
+  for (int r = threadIdx.x; r < mt; r += kTsqrThreads) {
+    for (int c0 = 0; c0 < s; c0 += 16) {
+      const int nc = s - c0 < 16 ? s - c0 : 16;
+      double e[16];
+#pragma unroll
+      for (int c = 0; c < 16; ++c) e[c] = (c < nc && r < s) ? Bs[r + (size_t)(c0 + c) * s] : 0.0;
+      const int lmax = r < s ? r + 1 : s;  // V(r, l) = 0 for l > r
+      for (int l = 0; l < lmax; ++l) {
+        const double v = l == r ? 1.0 : V[r + (size_t)l * mt];
+#pragma unroll
+        for (int c = 0; c < 16; ++c)
+          if (c < nc) e[c] = fma(-v, W[l + (size_t)(c0 + c) * s], e[c]);
+      }
+#pragma unroll
+      for (int c = 0; c < 16; ++c)
+        if (c < nc) {
+          E[r + (size_t)(c0 + c) * mt] = e[c];
+          if (r < rows_here) dst[row0 + r + (int64_t)(c0 + c) * ldq] = (T)e[c];
+        }
+    }
   }
+  __syncthreads();
   // maxima of the written Q block (of the stored values)
   if (qmax.col != nullptr) {
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
@@ -265,23 +343,24 @@ template <typename T>
 cudaError_t launch_tsqr_t(const TsqrPlan& p, Seg a, void* q, int64_t ldq, double* R, int32_t ldr,
                           double* work, DevStatus* st, int32_t block, cudaStream_t stream, MaxOut qmax) {
   const size_t leaf_f = (size_t)p.mt * p.s * sizeof(double);
+  const size_t ss = (size_t)p.s * p.s * sizeof(double);
   const size_t node_f = (size_t)p.fan * p.s * p.s * sizeof(double);
   cudaError_t e;
-  e = ensure_dyn_smem(tsqr_leaf_factor<T>, (size_t)(leaf_f));
+  e = ensure_dyn_smem(tsqr_leaf_factor<T>, leaf_f + 2 * ss);
   if (e != cudaSuccess) return e;
-  e = ensure_dyn_smem(tsqr_leaf_apply<T>, (size_t)(2 * leaf_f));
+  e = ensure_dyn_smem(tsqr_leaf_apply<T>, 2 * leaf_f + 3 * ss);
   if (e != cudaSuccess) return e;
   e = ensure_dyn_smem(tsqr_node_factor, (size_t)(node_f));
   if (e != cudaSuccess) return e;
   e = ensure_dyn_smem(tsqr_node_apply, (size_t)(2 * node_f));
   if (e != cudaSuccess) return e;
   const int slot = prof_begin(stream);
-  tsqr_leaf_factor<T><<<p.nodes[0], kTsqrThreads, leaf_f, stream>>>(p, a, work, R, ldr, st, block);
+  tsqr_leaf_factor<T><<<p.nodes[0], kTsqrThreads, leaf_f + 2 * ss, stream>>>(p, a, work, R, ldr, st, block);
   for (int l = 1; l < p.nlevels; ++l)
     tsqr_node_factor<<<p.nodes[l], kTsqrThreads, node_f, stream>>>(p, l, work, R, ldr, st, block);
   for (int l = p.nlevels - 1; l >= 1; --l)
     tsqr_node_apply<<<p.nodes[l], kTsqrThreads, 2 * node_f, stream>>>(p, l, work, st);
-  tsqr_leaf_apply<T><<<p.nodes[0], kTsqrThreads, 2 * leaf_f, stream>>>(p, work, q, ldq, st, qmax);
+  tsqr_leaf_apply<T><<<p.nodes[0], kTsqrThreads, 2 * leaf_f + 3 * ss, stream>>>(p, work, q, ldq, st, qmax);
   // Householder QR and explicit Q of the m x s block: 2 m s^2 flops each.
   prof_end(slot, kProfTsqr, stream, 4.0 * (double)p.m * p.s * p.s,
            2.0 * (double)p.m * p.s * sizeof(T) + 2.0 * (double)p.nodes[0] * p.mt * p.s * 8.0);
@@ -313,6 +392,8 @@ void tsqr_plan(int64_t m, int32_t s, TsqrPlan* p) {
   size_t off = 0;
   p->off_h = off;
   off += (size_t)p->nodes[0] * mt * s;
+  p->off_t0 = off;
+  off += (size_t)p->nodes[0] * s * s;
   for (int l = 0; l < p->nlevels; ++l) {
     p->off_tau[l] = off;
     off += round_up((size_t)p->nodes[l] * s, 32);
