@@ -108,6 +108,67 @@ __global__ void __launch_bounds__(kStoreRows) qsplit_kernel(QStore qs, const dou
   }
 }
 
+// The common case of the split: k0 a multiple of 8 and at most NC <= 16 columns
+// (s <= 16): each thread holds its row's values in registers, so all loads are
+// in flight at once and Q is read once.
+template <int NC>
+__global__ void __launch_bounds__(kStoreRows) qsplit_reg_kernel(QStore qs, const double* src, int64_t lds,
+                                                                int64_t m, int32_t k0, int32_t s,
+                                                                DevStatus* st, int32_t block) {
+  if (block_failed(st)) return;
+  __shared__ int s_wmax[kStoreRows / 32][NC];
+  const int i = threadIdx.x, warp = i >> 5, lane = i & 31;
+  const int64_t b = blockIdx.x, r = b * kStoreRows + i;
+  const bool live = r < m;
+  double v[NC];
+#pragma unroll
+  for (int k = 0; k < NC; ++k) v[k] = (live && k < s) ? src[r + (int64_t)k * lds] : 0.0;
+#pragma unroll
+  for (int k = 0; k < NC; ++k) {
+    const int mx = __reduce_max_sync(0xffffffffu, exp_field(v[k]));
+    if (lane == 0) s_wmax[warp][k] = mx;
+  }
+  __syncthreads();
+  int ce[NC];
+#pragma unroll
+  for (int k = 0; k < NC; ++k) {
+    int e = 0;
+#pragma unroll
+    for (int w = 0; w < kStoreRows / 32; ++w) e = max(e, s_wmax[w][k]);
+    ce[k] = k < s ? e : 0;
+  }
+  if (i < s) {
+    int e = 0;
+#pragma unroll
+    for (int w = 0; w < kStoreRows / 32; ++w) e = max(e, s_wmax[w][i]);
+    qs.exps[b * qs.ld_exp + k0 + i] = e;
+    if (e == 0x7FF) set_failure(st, BCGS_ERR_NONFINITE, block);
+  }
+  // columns [k0, k0 + s) and zeros up to the end of the 16-column chunk
+  const int kwr = (((k0 + s) + 15) & ~15) - k0;
+#pragma unroll
+  for (int g8 = 0; g8 < NC + 16; g8 += 8) {
+    if (g8 < kwr) {
+      uint64_t N[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) N[u] = (g8 + u < NC) ? fixed62_offset(v[g8 + u], ce[g8 + u]) : fixed62_offset(0.0, 0);
+      uint32_t w[4][8];
+#pragma unroll
+      for (int p = 0; p < 4; ++p)
+        digits_pair_f16((uint32_t)(N[2 * p] >> 32), (uint32_t)N[2 * p], (uint32_t)(N[2 * p + 1] >> 32),
+                        (uint32_t)N[2 * p + 1], w[p]);
+      const int col = k0 + g8;
+      const int G = col / kStoreCols, g = (col % kStoreCols) / 8;
+      uint8_t* dst = qs.dig + ((size_t)(b * qs.ngroups + G) * 8) * (kStoreRows * kStoreCols * 2) +
+                     (size_t)(g * 16 + (i >> 3)) * 128 + (i & 7) * 16;
+#pragma unroll
+      for (int t = 0; t < 8; ++t)
+        *reinterpret_cast<uint4*>(dst + (size_t)t * (kStoreRows * kStoreCols * 2)) =
+            make_uint4(w[0][t], w[1][t], w[2][t], w[3][t]);
+    }
+  }
+}
+
 // ---------------------------------------------------------------- projection
 // Persistent, one CTA per SM, warp-specialized:
 //   warp 0      bulk copies of the A digit chunks and the MMAs (one thread);
@@ -613,7 +674,12 @@ cudaError_t launch_qsplit(const QStore& qs, const double* src, int64_t lds, cons
                           cudaStream_t stream) {
   if (s < 1 || s > 64 || qs.nblk <= 0 || k0 < 0 || k0 + s > qs.ld_exp) return cudaErrorInvalidValue;
   const int slot = prof_begin(stream);
-  qsplit_kernel<<<(unsigned)qs.nblk, kStoreRows, 0, stream>>>(qs, src, lds, Q, ldq, m, k0, s, st, block);
+  if (k0 % 8 == 0 && s <= 8)
+    qsplit_reg_kernel<8><<<(unsigned)qs.nblk, kStoreRows, 0, stream>>>(qs, src, lds, m, k0, s, st, block);
+  else if (k0 % 8 == 0 && s <= 16)
+    qsplit_reg_kernel<16><<<(unsigned)qs.nblk, kStoreRows, 0, stream>>>(qs, src, lds, m, k0, s, st, block);
+  else
+    qsplit_kernel<<<(unsigned)qs.nblk, kStoreRows, 0, stream>>>(qs, src, lds, Q, ldq, m, k0, s, st, block);
   // reads the s new columns, writes 16 bytes of digits per element
   prof_end(slot, kProfStoreSplit, stream, 0.0, (double)m * s * (8.0 + 16.0));
   note_launch(1);

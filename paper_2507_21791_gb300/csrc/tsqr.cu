@@ -50,39 +50,47 @@ __device__ __forceinline__ double dot4(const double* a, const double* b, int r0,
 // diagonal (v_j has an implicit 1 at row j); tau[j] the reflector scalars.
 __device__ void block_householder(double* A, int rows, int s, double* tau) {
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  for (int j = 0; j < s; ++j) {
+  // reflector of column j by one warp: v_j below the diagonal, beta on it, tau[j]
+  auto reflect = [&](int j) {
     double* aj = A + (size_t)j * rows;
-    if (warp == 0) {
-      const double sum = warp_sum(dot4(aj, aj, j + 1 + lane, rows));
-      const double x0 = aj[j];
-      const double alpha = sqrt(fma(x0, x0, sum));
-      double t = 0.0, beta = 0.0, denom = 1.0;
-      if (alpha != 0.0) {
-        beta = x0 >= 0.0 ? -alpha : alpha;
-        denom = x0 - beta;
-        t = (beta - x0) / beta;
-      }
-      if (alpha != 0.0) {
-        const double rden = 1.0 / denom;  // one FP64 division per column
-        for (int r = j + 1 + lane; r < rows; r += 32) aj[r] *= rden;
-      }
-      __syncwarp();
-      if (lane == 0) {
-        tau[j] = t;
-        if (alpha != 0.0) aj[j] = beta;
-      }
+    const double sum = warp_sum(dot4(aj, aj, j + 1 + lane, rows));
+    const double x0 = aj[j];
+    const double alpha = sqrt(fma(x0, x0, sum));
+    double t = 0.0, beta = 0.0, denom = 1.0;
+    if (alpha != 0.0) {
+      beta = x0 >= 0.0 ? -alpha : alpha;
+      denom = x0 - beta;
+      t = (beta - x0) / beta;
     }
-    __syncthreads();
+    if (alpha != 0.0) {
+      const double rden = 1.0 / denom;  // one FP64 division per column
+      for (int r = j + 1 + lane; r < rows; r += 32) aj[r] *= rden;
+    }
+    __syncwarp();
+    if (lane == 0) {
+      tau[j] = t;
+      if (alpha != 0.0) aj[j] = beta;
+    }
+  };
+  if (warp == 0) reflect(0);
+  __syncthreads();
+  for (int j = 0; j < s; ++j) {
+    // reflector j is final; apply it to the columns l > j.  Warp 0 takes column
+    // j + 1 first and forms reflector j + 1 at once (look-ahead), while the other
+    // warps finish their columns with reflector j: one barrier per column.
+    const double* aj = A + (size_t)j * rows;
     const double t = tau[j];
-    if (t != 0.0) {
-      for (int l = j + 1 + warp; l < s; l += kWarps) {
-        double* al = A + (size_t)l * rows;
+    for (int l = j + 1 + warp; l < s; l += kWarps) {
+      double* al = A + (size_t)l * rows;
+      if (t != 0.0) {
         double w = warp_sum(dot4(aj, al, j + 1 + lane, rows)) + al[j];
         w *= t;
         __syncwarp();  // every lane has read al[j] before lane 0 updates it
         if (lane == 0) al[j] -= w;
         for (int r = j + 1 + lane; r < rows; r += 32) al[r] = fma(-aj[r], w, al[r]);
+        __syncwarp();
       }
+      if (l == j + 1) reflect(l);
     }
     __syncthreads();
   }
