@@ -141,10 +141,14 @@ __global__ void __launch_bounds__(kThreads, 1) gram_store_kernel(GramStoreDesc d
       const int g_cnt = min(NBT / 8, qs.ngroups * 16 - g_lo);
       const int G1 = g_lo / 16, gs = g_lo % 16;
       const int n1 = min(g_cnt, 16 - gs), n2 = g_cnt - n1;
+      // only the 8-column groups of the tile that hold columns < na (the rows of
+      // the MMA beyond them read earlier, finite digits and are not written out)
+      const int a_cols = min(kStoreCols, d.na - kStoreCols * G);
+      const uint32_t a_bytes = (uint32_t)((a_cols + 7) / 8) * 2048u;
       auto issue_A = [&](int a) {
         const int slot = a % S;
-        mbar_arrive_expect_tx(&fullA[slot], kDigBytes);
-        bulk_g2s(Aring + slot * kDigBytes, tile(b_first + a / kDigits, G, a % kDigits), kDigBytes, &fullA[slot]);
+        mbar_arrive_expect_tx(&fullA[slot], a_bytes);
+        bulk_g2s(Aring + slot * kDigBytes, tile(b_first + a / kDigits, G, a % kDigits), a_bytes, &fullA[slot]);
       };
       auto issue_B = [&](int bl) {
         const int p = bl & 1;
