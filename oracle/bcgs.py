@@ -351,13 +351,50 @@ def bcgsi_plus_p_2s(X: np.ndarray, s: int):
     return Q, R
 
 
+def bcgs_pipi_plus(X: np.ndarray, s: int):
+    """BCGS-PIPI+, Alg. 1: two synchronizations per block, both passes normalized
+    by the Pythagorean Cholesky (O(u) loss of orthogonality for O(u) kappa^2 <= 1,
+    Sec. 2).  Step by step as in Alg. 1:
+        [Q_1, R_11] = TSQR(X_1)
+        for k = 1..q-1:
+            [S; T] = [Q_k X_{k+1}]^T X_{k+1}            (first synchronization)
+            S_{k+1,k+1} = chol(T - S^T S)
+            U = (X_{k+1} - Q_k S) S_{k+1,k+1}^{-1}
+            [Y; Omega] = [Q_k U]^T U                    (second synchronization)
+            Y_{k+1,k+1} = chol(Omega - Y^T Y);  Q_{k+1} = (U - Q_k Y) Y_{k+1,k+1}^{-1}
+            R_{1:k,k+1} = S + Y S_{k+1,k+1};    R_{k+1,k+1} = Y_{k+1,k+1} S_{k+1,k+1}
+    """
+    X, m, n, q = _check(X, s)
+    Q = np.zeros((m, n))
+    R = np.zeros((n, n))
+    blk = lambda k: slice((k - 1) * s, k * s)
+    upto = lambda k: slice(0, k * s)
+    Q[:, blk(1)], R[blk(1), blk(1)] = tsqr(X[:, blk(1)], 1)
+    for k in range(1, q):
+        c = k * s
+        Qk = Q[:, upto(k)]
+        Xk1 = X[:, blk(k + 1)]
+        G1 = gram([Qk, Xk1], [Xk1])
+        S, T = G1[:c], G1[c:]
+        Skk = chol(T - S.T @ S, k + 1)
+        U = project_normalize(Xk1, Qk, S, Skk)
+        G2 = gram([Qk, U], [U])
+        Y, Om = G2[:c], G2[c:]
+        Ykk = chol(Om - Y.T @ Y, k + 1)
+        Q[:, blk(k + 1)] = project_normalize(U, Qk, Y, Ykk)
+        R[upto(k), blk(k + 1)] = S + Y @ Skk
+        R[blk(k + 1), blk(k + 1)] = Ykk @ Skk
+    return Q, R
+
+
 VARIANTS = {
     "bcgsi+": bcgsi_plus,
     "bcgsi+p-1s": bcgsi_plus_p_1s,
     "bcgsi+p-2s": bcgsi_plus_p_2s,
+    "bcgs-pipi+": bcgs_pipi_plus,
 }
 
 
 def factor(X: np.ndarray, s: int, variant: str):
-    """Dispatch by variant name ("bcgsi+", "bcgsi+p-1s", "bcgsi+p-2s")."""
+    """Dispatch by variant name ("bcgsi+", "bcgsi+p-1s", "bcgsi+p-2s", "bcgs-pipi+")."""
     return VARIANTS[variant](X, s)

@@ -157,6 +157,21 @@ def textbook_cgs2(X):
     return Q, R
 
 
+def test_pipi_plus_first_pass_is_pythagorean_cholqr():
+    """Alg. 1's first pass of a block equals a Cholesky QR of X_{k+1} - Q_k S:
+    S_{k+1,k+1} is its R factor and U its Q factor (Pythagorean identity), checked
+    on one block against LAPACK's QR of the projected block."""
+    rng = np.random.default_rng(71)
+    Qk, _ = np.linalg.qr(rng.standard_normal((600, 12)))
+    X2 = rng.standard_normal((600, 4)) * np.array([1.0, 1e-2, 1e2, 3.0])
+    Q, R = oracle.bcgs_pipi_plus(np.hstack([Qk @ np.diag(np.arange(1.0, 13.0)), X2]), 4)
+    V = X2 - Qk @ (Qk.T @ X2)
+    Ql, Rl = sign_normalized_lapack_qr(V)
+    # final block of Q spans the projected block with positive diagonal R
+    assert np.abs(Q[:, 12:] - Ql).max() < 1e-10
+    assert np.abs(np.abs(np.diag(R)[12:]) - np.abs(np.diag(Rl))).max() / np.abs(np.diag(Rl)).max() < 1e-10
+
+
 def test_s_equals_1_is_cgs2():
     """BCGSI+ with s = 1 is CGSI+ (Sec. 4, Table 2's normalization point)."""
     X = synth.make_matrix_np(400, 20, 1e6, seed=13)
@@ -182,7 +197,7 @@ def test_cross_variant_agreement(kappa):
 def test_invariants(variant, kappa):
     m, n, s = 3000, 64, 8
     X = synth.make_matrix_np(m, n, kappa, seed=19)
-    if variant == "bcgsi+p-1s" and kappa >= 1e8:
+    if variant in ("bcgsi+p-1s", "bcgs-pipi+") and kappa >= 1e8:
         pytest.skip("outside Table 1's O(u) kappa^2 <= 1 range")
     Q, R = oracle.factor(X, s, variant)
     assert np.array_equal(np.tril(R, -1), np.zeros_like(R))
@@ -276,11 +291,12 @@ def test_table1_loo_ordering():
     for v in ("bcgsi+", "bcgsi+p-2s"):
         Q, R = oracle.factor(X, 8, v)
         assert oracle.loo(Q) < 1e-13
-    try:
-        Q, _ = oracle.factor(X, 8, "bcgsi+p-1s")
-        assert oracle.loo(Q) > 1e-10
-    except oracle.Breakdown as e:
-        assert e.kind == "not_spd"
+    for v in ("bcgsi+p-1s", "bcgs-pipi+"):  # both need O(u) kappa^2 <= 1 (Sec. 2)
+        try:
+            Q, _ = oracle.factor(X, 8, v)
+            assert oracle.loo(Q) > 1e-10
+        except oracle.Breakdown as e:
+            assert e.kind == "not_spd"
 
 
 # ---------------------------------------------------------------- degenerate inputs
@@ -340,8 +356,9 @@ def test_mutation_transposed_index_in_solve_is_caught(monkeypatch):
     assert _solve_pin_error() < 1e-12
     monkeypatch.setattr(ob, "solve_right_upper", bad_solve)
     assert _solve_pin_error() > 1e-3
-    # In BCGSI+P-1S the solve by S_{k+1,k+1} (far from identity) is exposed.
+    # In BCGSI+P-1S and BCGS-PIPI+ the solve by S_{k+1,k+1} (far from identity) is exposed.
     assert _recovery_error("bcgsi+p-1s") > 1e-6
+    assert _recovery_error("bcgs-pipi+") > 1e-6
 
 
 def test_mutation_wrong_sign_in_chol_is_caught(monkeypatch):
@@ -354,9 +371,10 @@ def test_mutation_wrong_sign_in_chol_is_caught(monkeypatch):
     assert np.abs(ob.chol(R0.T @ R0) - R0).max() < 1e-10
     monkeypatch.setattr(ob, "chol", bad_chol)
     assert np.abs(ob.chol(R0.T @ R0) - R0).max() > 1e-3
-    # BCGSI+P-1S's S_{k+1,k+1} = chol(T - S^T S) is far from identity; in
-    # BCGSI+P-2S chol only factors Omega - Y^T Y ~ I, and BCGSI+ has no chol.
+    # BCGSI+P-1S's and BCGS-PIPI+'s S_{k+1,k+1} = chol(T - S^T S) is far from
+    # identity; in BCGSI+P-2S chol only factors Omega - Y^T Y ~ I, and BCGSI+ has no chol.
     assert _recovery_error("bcgsi+p-1s") > 1e-6
+    assert _recovery_error("bcgs-pipi+") > 1e-6
 
 
 def test_mutation_missing_sign_normalization_is_caught(monkeypatch):
