@@ -5,8 +5,8 @@ Workload (one step = one whole factorization, i.e. every block step of the hot
 path over one synthetic matrix): single FP64 economic QR of X = U diag(sigma) V^T,
 m = 2^22 rows, n = 256 columns, block size s = 16 (q = 16 blocks),
 kappa = 1e5 (inside every variant's O(u)-loss-of-orthogonality range, so the
-variants are compared at equal loss of orthogonality), BCGSI+P-1S timed; BCGSI+
-and BCGSI+P-2S are timed the same way for the speedup.
+variants are compared at equal loss of orthogonality), BCGSI+P-1S timed; BCGSI+,
+BCGSI+P-2S and BCGS-PIPI+ (Alg. 1) are timed the same way for the speedup.
 
 value  = algorithmic HBM bytes of the fused BCGSI+P-1S schedule per step / time
          (GB/s); bytes per step = 8 m s q(q-1)/2 (each block reads the previous
@@ -305,14 +305,15 @@ def main_ours(args):
 
     compare = {}
     if not args.no_compare:
-        for v in ("bcgsi+", "bcgsi+p-2s"):
+        for v in ("bcgsi+", "bcgsi+p-2s", "bcgs-pipi+"):
             r = run_variant(v)
             compare[v] = {"ms": r["ms"], "loo": r["loo"], "residual": r["residual"]}
             del r
     compare["bcgsi+p-1s"] = {"ms": main["ms"], "loo": main["loo"], "residual": main["residual"]}
     speedup = None
     if "bcgsi+" in compare:
-        speedup = {v: compare["bcgsi+"]["ms"] / compare[v]["ms"] for v in ("bcgsi+p-1s", "bcgsi+p-2s")}
+        speedup = {v: compare["bcgsi+"]["ms"] / compare[v]["ms"]
+                   for v in ("bcgsi+p-1s", "bcgsi+p-2s", "bcgs-pipi+")}
 
     forms = None
     if not args.no_forms and world == 1:

@@ -9,6 +9,9 @@
  *   BCGS_BCGSI_PLUS_P_1S  BCGSI+P-1S (Alg. 2: 1 synchronization per block)
  *   BCGS_BCGSI_PLUS_P_2S  BCGSI+P-2S (Sec. 2: Alg. 2 with TSQR as the first
  *                         intraorthogonalization, 2 synchronizations per block)
+ *   BCGS_BCGS_PIPI_PLUS   BCGS-PIPI+ (Alg. 1: both passes normalized by the
+ *                         Pythagorean Cholesky, 2 synchronizations per block;
+ *                         O(u) loss of orthogonality only while O(u) kappa^2 <= 1)
  * A synchronization point of the paper (one MPI_Allreduce, Sec. 3) is here one
  * streaming pass over HBM that ends in a deterministic grid-wide reduction.
  *
@@ -64,7 +67,8 @@ typedef enum {
 typedef enum {
   BCGS_BCGSI_PLUS = 0,
   BCGS_BCGSI_PLUS_P_1S = 1,
-  BCGS_BCGSI_PLUS_P_2S = 2
+  BCGS_BCGSI_PLUS_P_2S = 2,
+  BCGS_BCGS_PIPI_PLUS = 3
 } bcgs_variant;
 
 typedef enum { BCGS_FP64 = 0, BCGS_FP32_STORAGE = 1 } bcgs_precision;
@@ -114,8 +118,9 @@ BCGS_API int bcgs_qr_factor_status(const void* workspace, void* stream, int32_t*
  * bcgs_qr_step ingests the next m x s block X_j; bcgs_qr_finish runs the last
  * block's branch of Alg. 2.  Delayed normalization (Sec. 2, eq. (1)) means that
  * under BCGSI+P-1S and -2S, after step j (j >= 2) the columns of Q and R of
- * blocks 1..j-1 are final and block j is still provisional; under BCGSI+ block
- * j is final after step j.  bcgs_qr_sync reports how many columns are final.
+ * blocks 1..j-1 are final and block j is still provisional; under BCGSI+ and
+ * BCGS-PIPI+ block j is final after step j (bcgs_qr_finish enqueues nothing).
+ * bcgs_qr_sync reports how many columns are final.
  * The handle is a small host object (the only host allocation of the library).
  * ------------------------------------------------------------------------- */
 BCGS_API int bcgs_qr_init(bcgs_qr_t* handle, int64_t m, int32_t n_max, int32_t s,

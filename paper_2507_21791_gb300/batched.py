@@ -145,8 +145,9 @@ class Batch:
 
 def alg_bytes(m: int, n: int, s: int, variant: str, b: int = 8) -> float:
     """Algorithmic HBM bytes of one factorization: passes over the previous basis
-    (1 per block for BCGSI+P-1S, 2 for -2S, 4 for BCGSI+) plus the block passes."""
+    (1 per block for BCGSI+P-1S, 2 for -2S, 4 for BCGSI+ and BCGS-PIPI+) plus the
+    block passes."""
     q = n // s
-    qpasses = {"bcgsi+p-1s": 1, "bcgsi+p-2s": 2, "bcgsi+": 4}[variant]
-    bpasses = {"bcgsi+p-1s": 5, "bcgsi+p-2s": 8, "bcgsi+": 10}[variant]
+    qpasses = {"bcgsi+p-1s": 1, "bcgsi+p-2s": 2, "bcgsi+": 4, "bcgs-pipi+": 4}[variant]
+    bpasses = {"bcgsi+p-1s": 5, "bcgsi+p-2s": 8, "bcgsi+": 10, "bcgs-pipi+": 6}[variant]
     return b * m * s * q * (q - 1) / 2 * qpasses + bpasses * b * m * n

@@ -1,4 +1,4 @@
-// Host driver and C ABI: the three variants as block-step state machines over
+// Host driver and C ABI: the four variants as block-step state machines over
 // the kernels of gram.cu, proj.cu, tsqr.cu and tail.cu.
 //
 // Every step is a fixed sequence of stream-ordered launches; nothing here
@@ -63,7 +63,8 @@ void make_layout(int64_t m, int32_t n_max, int32_t s, int variant, int precision
   L->G = take((size_t)n_max * 2 * s * sizeof(double));
   L->G2 = take((size_t)n_max * 2 * s * sizeof(double));
   // (c + s) x 2s coefficients of the paired projection (BCGSI+P-1S / -2S)
-  L->Bp = variant == BCGS_BCGSI_PLUS ? off : take((size_t)n_max * 2 * s * sizeof(double));
+  const bool paired = variant == BCGS_BCGSI_PLUS_P_1S || variant == BCGS_BCGSI_PLUS_P_2S;
+  L->Bp = paired ? take((size_t)n_max * 2 * s * sizeof(double)) : off;
   L->partial = take(gram_partial_doubles(m, n_max, 2 * s) * sizeof(double));
   L->amax = take(((size_t)n_max + 4 * (size_t)s) * sizeof(unsigned long long));
   // maxima kept by the writers: per column of Q, per column of U, per row of Q
@@ -72,7 +73,9 @@ void make_layout(int64_t m, int32_t n_max, int32_t s, int variant, int precision
   L->rowmaxQ = take((size_t)m * sizeof(unsigned long long));
   L->ldu = round_up(m, 64);
   L->U = take((size_t)L->ldu * s * esz);
-  L->V = variant == BCGS_BCGSI_PLUS_P_1S ? off : take((size_t)L->ldu * s * esz);
+  // the projected block TSQR reads (no TSQR after block 1 under 1S and PIPI+)
+  const bool tsqr_in = variant == BCGS_BCGSI_PLUS || variant == BCGS_BCGSI_PLUS_P_2S;
+  L->V = tsqr_in ? take((size_t)L->ldu * s * esz) : off;
   tsqr_plan(m, s, &L->tp);
   L->tsqr = take(L->tp.doubles * sizeof(double));
   L->store = store;
@@ -483,8 +486,8 @@ int do_step(bcgs_qr_s* h, const void* X, int64_t ldx) {
         // [S_12; T_2] = [Q_1 X_2]^T X_2, S_22 = chol(T_2 - S_12^T S_12), U_2
         TRY(store_put(h, X, ldx, s));
         TRY(gram_cols(h, 2 * s, s, s, {h->Qseg(s), Xs}, {Xs}, G));
-        TRY(launch_tail_start_1s(s, G, ldg, h->buf(h->L.S[h->cur]), h->n_max,
-                                 h->buf(h->L.Sd[h->cur]), 2, h->st(), h->stream));
+        TRY(launch_tail_pchol(s, s, G, ldg, h->buf(h->L.S[h->cur]), h->n_max, h->buf(h->L.Sd[h->cur]), 2,
+                              h->st(), h->stream));
         TRY(zero_umax(h));
         TRY(project(h, Xs, s, h->buf(h->L.S[h->cur]), h->n_max, h->buf(h->L.Sd[h->cur]), h->U(),
                     h->L.ldu, h->Umax()));
@@ -505,6 +508,29 @@ int do_step(bcgs_qr_s* h, const void* X, int64_t ldx) {
         return BCGS_OK;
       }
       return step_p(h, X, ldx);
+    case BCGS_BCGS_PIPI_PLUS: {
+      const int k = j - 1, c = k * s;
+      double* G2 = h->buf(h->L.G2);
+      double* Skk = h->buf(h->L.Rt1);
+      double* Ykk = h->buf(h->L.Rt2);
+      // [S; T] = [Q_k X_{k+1}]^T X_{k+1}, S_kk = chol(T - S^T S),
+      // U = (X_{k+1} - Q_k S) S_kk^{-1}
+      TRY(store_put(h, X, ldx, c));
+      TRY(gram_cols(h, c + s, c, s, {h->Qseg(c), Xs}, {Xs}, G));
+      TRY(launch_tail_pchol(c, s, G, ldg, nullptr, 0, Skk, j, h->st(), h->stream));
+      TRY(zero_umax(h));
+      TRY(project(h, Xs, c, G, ldg, Skk, h->U(), h->L.ldu, h->Umax()));
+      // [Y; Omega] = [Q_k U]^T U, Y_kk = chol(Omega - Y^T Y),
+      // Q_{k+1} = (U - Q_k Y) Y_kk^{-1}
+      TRY(store_put(h, h->U(), h->L.ldu, c));
+      TRY(gram_cols(h, c + s, c, s, {h->Qseg(c), h->Useg()}, {h->Useg()}, G2));
+      TRY(launch_tail_pchol(c, s, G2, ldg, nullptr, 0, Ykk, j, h->st(), h->stream));
+      TRY(project(h, h->Useg(), c, G2, ldg, Ykk, h->Qblk(j), h->ldq, h->Qmax(j)));
+      TRY(wrote_q(h, j));
+      // R_{1:k,k+1} = S + Y S_kk, R_{k+1,k+1} = Y_kk S_kk
+      TRY(launch_r_assemble(c, s, G, ldg, G2, ldg, Skk, Ykk, h->R, h->ldr, c, h->st(), h->stream));
+      return BCGS_OK;
+    }
   }
   return BCGS_ERR_INVALID_ARG;
 }
@@ -513,7 +539,7 @@ int init_handle(bcgs_qr_s* h, int64_t m, int32_t n_max, int32_t s, int variant, 
                 void* Q, int64_t ldq, double* R, int32_t ldr, void* workspace, size_t ws_bytes,
                 void* stream) {
   if (!valid_shape(m, n_max, s)) return BCGS_ERR_INVALID_ARG;
-  if (variant < 0 || variant > 2 || precision < 0 || precision > 1) return BCGS_ERR_INVALID_ARG;
+  if (variant < 0 || variant > 3 || precision < 0 || precision > 1) return BCGS_ERR_INVALID_ARG;
   if (Q == nullptr || R == nullptr || workspace == nullptr) return BCGS_ERR_INVALID_ARG;
   if (ldq < m || ldr < n_max) return BCGS_ERR_INVALID_ARG;
   if (((uintptr_t)workspace) % 256 != 0) return BCGS_ERR_WORKSPACE;
@@ -537,7 +563,8 @@ int init_handle(bcgs_qr_s* h, int64_t m, int32_t n_max, int32_t s, int variant, 
   h->fp32 = precision == BCGS_FP32_STORAGE ? 1 : 0;
   h->esz = h->fp32 ? 4 : 8;
   // Grams from the store need whole 8-column groups per block and nb <= 32
-  h->sgram = h->L.store && s % 8 == 0 && (variant == BCGS_BCGSI_PLUS ? s <= 32 : s <= 16);
+  const bool paired = variant == BCGS_BCGSI_PLUS_P_1S || variant == BCGS_BCGSI_PLUS_P_2S;
+  h->sgram = h->L.store && s % 8 == 0 && (paired ? s <= 16 : s <= 32);
   h->j = 0;
   h->cur = 0;
   h->finished = 0;
@@ -560,7 +587,7 @@ int step_handle(bcgs_qr_s* h, const void* X, int64_t ldx) {
 int finish_handle(bcgs_qr_s* h) {
   if (h->finished) return BCGS_OK;
   if (h->j == 0) return BCGS_ERR_STATE;
-  if (h->variant != BCGS_BCGSI_PLUS && h->j >= 2) {
+  if ((h->variant == BCGS_BCGSI_PLUS_P_1S || h->variant == BCGS_BCGSI_PLUS_P_2S) && h->j >= 2) {
     const int rc = finish_p(h);
     if (rc != BCGS_OK) return rc;
   }
@@ -656,7 +683,7 @@ int64_t bcgs_get_option(int option) {
 int bcgs_qr_workspace_size(int64_t m, int32_t n_max, int32_t s, int variant, int precision,
                            size_t* bytes) {
   if (bytes == nullptr || !valid_shape(m, n_max, s)) return BCGS_ERR_INVALID_ARG;
-  if (variant < 0 || variant > 2 || precision < 0 || precision > 1) return BCGS_ERR_INVALID_ARG;
+  if (variant < 0 || variant > 3 || precision < 0 || precision > 1) return BCGS_ERR_INVALID_ARG;
   Layout L;
   make_layout(m, n_max, s, variant, precision, want_store(m, s, precision), &L);
   *bytes = L.total;
@@ -723,7 +750,7 @@ int bcgs_qr_sync(bcgs_qr_t h, int32_t* n_final, int32_t* fail_block) {
   if (rc != BCGS_OK) return rc;
   if (n_final) {
     int fin;
-    if (h->finished || h->variant == BCGS_BCGSI_PLUS) fin = h->j;
+    if (h->finished || h->variant == BCGS_BCGSI_PLUS || h->variant == BCGS_BCGS_PIPI_PLUS) fin = h->j;
     else fin = h->j <= 1 ? h->j : h->j - 1;
     *n_final = code ? 0 : fin * h->s;
   }

@@ -243,9 +243,11 @@ struct TailDesc {
   double* Bpair; int32_t ldb;
 };
 cudaError_t launch_tail_1s2s(const TailDesc& d, DevStatus* st, cudaStream_t stream);
-// S22 = chol(T2 - S12^T S12) from the startup Gram [Q1 X2]^T X2 (1S only).
-cudaError_t launch_tail_start_1s(int32_t s, const double* G, int32_t ldg, double* S, int32_t ldsm,
-                                 double* Sd, int32_t block, DevStatus* st, cudaStream_t stream);
+// R_kk = chol(T - S^T S) from G = [S; T] = [Q_{1:k} V]^T V, S the top c rows
+// (Alg. 1's two normalizations; c = s is the BCGSI+P-1S startup).  S is copied
+// to S_out (ld ldsm) unless S_out is null.
+cudaError_t launch_tail_pchol(int32_t c, int32_t s, const double* G, int32_t ldg, double* S_out,
+                              int32_t ldsm, double* Rkk, int32_t block, DevStatus* st, cudaStream_t stream);
 // Copy S12 = G[0:s,0:s] (2S startup), and BCGSI+ R assembly.
 cudaError_t launch_copy_small(int32_t rows, int32_t cols, const double* A, int32_t lda,
                               double* B, int32_t ldb, DevStatus* st, cudaStream_t stream);

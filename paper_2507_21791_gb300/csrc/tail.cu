@@ -213,28 +213,34 @@ __global__ void __launch_bounds__(kTailThreads) tail_1s2s_kernel(TailDesc d, Dev
   tail_1s2s_body(d, st, dyn);
 }
 
-// Startup of BCGSI+P-1S: [S_12; T_2] = [Q_1 X_2]^T X_2, S_22 = chol(T_2 - S_12^T S_12).
+// Pythagorean Cholesky of one block (Alg. 1; the startup of BCGSI+P-1S is its
+// c = s case): G = [S; T] = [Q_{1:k} V]^T V with S = G[0:c, :], T = G[c:c+s, :],
+// R_kk = chol(T - S^T S).  S is copied to S_out (ld ldsm) when S_out is set.
 __global__ void __launch_bounds__(kTailThreads)
-tail_start_1s_kernel(int32_t s, const double* G, int32_t ldg, double* S, int32_t ldsm, double* Sdo,
-                     int32_t block, DevStatus* st) {
+tail_pchol_kernel(int32_t c, int32_t s, const double* G, int32_t ldg, double* S_out, int32_t ldsm,
+                  double* Rkk, int32_t block, DevStatus* st) {
   if (failed(st)) return;
   extern __shared__ double dyn[];
   double* Ms = dyn;
   double* Rc = dyn + s * s;
-  small_tn(s, s, G, ldg, G, ldg, Ms);
+  small_tn(c, s, G, ldg, G, ldg, Ms);
   __syncthreads();
   for (int e = threadIdx.x; e < s * s; e += blockDim.x) {
     const int i = e % s, j = e / s;
-    Ms[e] = G[(s + i) + (size_t)j * ldg] - Ms[e];
-    S[i + (size_t)j * ldsm] = G[i + (size_t)j * ldg];
+    Ms[e] = G[(c + i) + (size_t)j * ldg] - Ms[e];
   }
+  if (S_out != nullptr)
+    for (int e = threadIdx.x; e < c * s; e += blockDim.x) {
+      const int i = e % c, j = e / c;
+      S_out[i + (size_t)j * ldsm] = G[i + (size_t)j * ldg];
+    }
   __syncthreads();
   const int code = small_chol(s, Ms, Rc);
   if (code) {
     if (threadIdx.x == 0) set_failure(st, code, block);
     return;
   }
-  for (int e = threadIdx.x; e < s * s; e += blockDim.x) Sdo[e] = Rc[e];
+  for (int e = threadIdx.x; e < s * s; e += blockDim.x) Rkk[e] = Rc[e];
 }
 
 __global__ void copy_small_kernel(int32_t rows, int32_t cols, const double* A, int32_t lda,
@@ -326,14 +332,16 @@ cudaError_t launch_tail_1s2s(const TailDesc& d, DevStatus* st, cudaStream_t stre
   return cudaGetLastError();
 }
 
-cudaError_t launch_tail_start_1s(int32_t s, const double* G, int32_t ldg, double* S, int32_t ldsm,
-                                 double* Sd, int32_t block, DevStatus* st, cudaStream_t stream) {
-  if (s > kMaxS) return cudaErrorInvalidValue;
+cudaError_t launch_tail_pchol(int32_t c, int32_t s, const double* G, int32_t ldg, double* S_out,
+                              int32_t ldsm, double* Rkk, int32_t block, DevStatus* st, cudaStream_t stream) {
+  if (s > kMaxS || c < 0) return cudaErrorInvalidValue;
   const size_t smem = 2 * (size_t)s * s * sizeof(double);
-  cudaError_t e = ensure_dyn_smem(tail_start_1s_kernel, (size_t)(smem));
+  cudaError_t e = ensure_dyn_smem(tail_pchol_kernel, (size_t)(smem));
   if (e != cudaSuccess) return e;
-  tail_start_1s_kernel<<<1, kTailThreads, smem, stream>>>(s, G, ldg, S, ldsm, Sd, block, st);
+  const int slot = prof_begin(stream);
+  tail_pchol_kernel<<<1, kTailThreads, smem, stream>>>(c, s, G, ldg, S_out, ldsm, Rkk, block, st);
   note_launch(1);
+  prof_end(slot, kProfTail, stream, 2.0 * (double)c * s * s + (double)s * s * s / 3.0, 0.0);
   return cudaGetLastError();
 }
 

@@ -49,8 +49,10 @@ def test_workspace_size_queries():
 
     m, n, s = 10000, 64, 8
     sizes = {v: bcgs.workspace_size(m, n, s, v) for v in bcgs.VARIANTS}
-    # 1S needs no separate projected block V; the others do
+    # 1S needs no separate projected block V, BCGS-PIPI+ neither V nor the paired
+    # coefficients; BCGSI+ and 2S keep V for their TSQR
     assert sizes["bcgsi+p-1s"] < sizes["bcgsi+p-2s"]
+    assert sizes["bcgs-pipi+"] < sizes["bcgsi+p-1s"] and sizes["bcgs-pipi+"] < sizes["bcgsi+"]
     assert bcgs.workspace_size(m, n, s, "bcgsi+p-1s", "fp32") < sizes["bcgsi+p-1s"]
     # FP64 engine: U, the TSQR tree and the row maxima, a few m x s blocks
     old = bcgs.get_gram_engine()
@@ -91,7 +93,9 @@ def test_bad_enums_and_null_pointers_rejected():
 
     lib = bcgs.load_library()
     out = ctypes.c_size_t(0)
-    assert lib.bcgs_qr_workspace_size(100, 16, 8, 3, 0, ctypes.byref(out)) == 1
+    assert lib.bcgs_qr_workspace_size(100, 16, 8, 4, 0, ctypes.byref(out)) == 1
+    assert lib.bcgs_qr_workspace_size(100, 16, 8, -1, 0, ctypes.byref(out)) == 1
+    assert lib.bcgs_qr_workspace_size(100, 16, 8, 3, 0, ctypes.byref(out)) == 0
     assert lib.bcgs_qr_workspace_size(100, 16, 8, 1, 2, ctypes.byref(out)) == 1
     assert lib.bcgs_qr_factor(100, 16, 8, 1, 0, None, 100, 16, 100, 32, 16, 256, 1 << 20, None) == 1
     h = ctypes.c_void_p(None)

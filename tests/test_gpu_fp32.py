@@ -19,7 +19,7 @@ import oracle
 from paper_2507_21791_gb300 import synth
 
 U32 = 2.0 ** -24
-VARIANTS = ["bcgsi+", "bcgsi+p-1s", "bcgsi+p-2s"]
+VARIANTS = ["bcgsi+", "bcgsi+p-1s", "bcgsi+p-2s", "bcgs-pipi+"]
 pytestmark = pytest.mark.gpu
 
 
@@ -38,7 +38,7 @@ def test_fp32_storage_accuracy(cuda, variant, kappa):
     m, n, s = 2 ** 16, 64, 8
     X = synth.make_matrix_np(m, n, kappa, seed=7)
     Q, R, code, blk = run_fp32(cuda, X, s, variant)
-    if variant == "bcgsi+p-1s" and kappa >= 1e6:
+    if variant in ("bcgsi+p-1s", "bcgs-pipi+") and kappa >= 1e6:
         assert cuda.STATUS[code] == "not_spd" and blk >= 2
         return
     assert code == 0

@@ -42,10 +42,10 @@ def check_against_oracle(X, s, variant, Q, R):
     assert np.max(np.abs(Qh - Qo)) <= tol
 
 
-@pytest.mark.parametrize("variant", ["bcgsi+", "bcgsi+p-1s", "bcgsi+p-2s"])
+@pytest.mark.parametrize("variant", ["bcgsi+", "bcgsi+p-1s", "bcgsi+p-2s", "bcgs-pipi+"])
 @pytest.mark.parametrize("m,n,s,kappa", SHAPES)
 def test_store_path_matches_the_oracle(tensor, variant, m, n, s, kappa):
-    if variant == "bcgsi+p-1s" and kappa > 1e5:
+    if variant in ("bcgsi+p-1s", "bcgs-pipi+") and kappa > 1e5:
         pytest.skip("1S is for kappa <= 1e5")
     X = synth.make_matrix_np(m, n, kappa, seed=m + 3 * n + s)
     Xd = tensor.to_device_colmajor(X)
@@ -58,7 +58,7 @@ def test_store_path_matches_the_oracle(tensor, variant, m, n, s, kappa):
     assert np.array_equal(R.cpu().numpy(), R2.cpu().numpy())
 
 
-@pytest.mark.parametrize("variant", ["bcgsi+", "bcgsi+p-1s", "bcgsi+p-2s"])
+@pytest.mark.parametrize("variant", ["bcgsi+", "bcgsi+p-1s", "bcgsi+p-2s", "bcgs-pipi+"])
 def test_store_and_on_the_fly_paths_agree(tensor, variant):
     """A workspace sized without the store runs the same factorization with the
     on-the-fly tensor projections; both meet the FP64 gates and agree to the

@@ -77,13 +77,13 @@ def test_tensor_gram_reports_nonfinite(tensor):
     assert tensor.STATUS[code] == "nonfinite" and blk == 2
 
 
-@pytest.mark.parametrize("variant", ["bcgsi+", "bcgsi+p-1s", "bcgsi+p-2s"])
+@pytest.mark.parametrize("variant", ["bcgsi+", "bcgsi+p-1s", "bcgsi+p-2s", "bcgs-pipi+"])
 @pytest.mark.parametrize("engine", ["tensor", "fp64"])
 def test_variants_on_each_engine(cuda, variant, engine):
     cuda.set_gram_engine(engine)
     try:
         for (m, n, s, kappa) in [(50000, 64, 8, 1e4), (3000, 48, 16, 1e6), (70000, 96, 32, 1e2)]:
-            if variant == "bcgsi+p-1s" and kappa > 1e5:
+            if variant in ("bcgsi+p-1s", "bcgs-pipi+") and kappa > 1e5:
                 continue
             X = synth.make_matrix_np(m, n, kappa, seed=m + n)
             Q, R, code, _ = cuda.factor(cuda.to_device_colmajor(X), s, variant)
@@ -104,7 +104,7 @@ def test_row_scaled_heavy_tails_meet_the_gates(cuda):
     cuda.set_gram_engine("tensor")
     try:
         X = synth.make_matrix_np(200000, 64, 1e5, seed=77, row_scaled=True)
-        for v in ("bcgsi+", "bcgsi+p-1s", "bcgsi+p-2s"):
+        for v in ("bcgsi+", "bcgsi+p-1s", "bcgsi+p-2s", "bcgs-pipi+"):
             Q, R, code, _ = cuda.factor(cuda.to_device_colmajor(X), 16, v)
             assert code == 0
             Qh, Rh = Q.cpu().numpy(), R.cpu().numpy()

@@ -1,9 +1,9 @@
-"""End-to-end parity of the three variants on the GPU (through the C ABI)
+"""End-to-end parity of the four variants on the GPU (through the C ABI)
 against the CPU oracle, on seeded inputs with controlled kappa.
 
 Gates (backward quantities, kappa-independent):
     ||X - Q R||_F / ||X||_F <= 1e-13,   ||I - Q^T Q||_2 <= 1e-12
-for kappa <= 1e8 (BCGSI+P-1S only where u kappa^2 << 1, Table 1).
+for kappa <= 1e8 (BCGSI+P-1S and BCGS-PIPI+ only where u kappa^2 << 1, Table 1).
 Forward agreement with the oracle (both are backward stable, so the factors
 differ by O(kappa u) times a modest polynomial in n):
     ||R - R_oracle||_F / ||R_oracle||_F <= 10 n kappa u,  max |Q - Q_oracle| <= 10 n kappa u.
@@ -15,7 +15,9 @@ import oracle
 from paper_2507_21791_gb300 import synth
 
 U64 = np.finfo(np.float64).eps / 2
-VARIANTS = ["bcgsi+", "bcgsi+p-1s", "bcgsi+p-2s"]
+VARIANTS = ["bcgsi+", "bcgsi+p-1s", "bcgsi+p-2s", "bcgs-pipi+"]
+# the variants whose first intraorthogonalization is the Pythagorean Cholesky
+PYTHAGOREAN = ("bcgsi+p-1s", "bcgs-pipi+")
 pytestmark = pytest.mark.gpu
 
 
@@ -60,8 +62,8 @@ def test_shapes(cuda, variant, m, n, s):
 @pytest.mark.parametrize("variant", VARIANTS)
 @pytest.mark.parametrize("kappa", [1e2, 1e5, 1e8])
 def test_kappa_sweep(cuda, variant, kappa):
-    if variant == "bcgsi+p-1s" and kappa >= 1e8:
-        pytest.skip("BCGSI+P-1S needs O(u) kappa^2 <= 1 (Table 1)")
+    if variant in PYTHAGOREAN and kappa >= 1e8:
+        pytest.skip("the Pythagorean variants need O(u) kappa^2 <= 1 (Table 1)")
     X = synth.make_matrix_np(20000, 64, kappa, seed=int(np.log10(kappa)))
     Q, R, code, _ = run_gpu(cuda, X, 8, variant)
     assert code == 0
@@ -77,13 +79,15 @@ def test_row_scaled_input(cuda):
 
 
 def test_one_sync_breaks_down_beyond_its_range(cuda):
-    """kappa = 1e10: u kappa^2 >> 1, BCGSI+P-1S's Pythagorean chol fails (Table 1);
-    BCGSI+ and BCGSI+P-2S keep O(u) loss of orthogonality."""
+    """kappa = 1e10: u kappa^2 >> 1, the Pythagorean Cholesky of BCGSI+P-1S and
+    BCGS-PIPI+ fails (Table 1); BCGSI+ and BCGSI+P-2S keep O(u) loss of
+    orthogonality."""
     X = synth.make_matrix_np(5000, 64, 1e10, seed=5)
-    _, _, code, blk = run_gpu(cuda, X, 8, "bcgsi+p-1s")
-    with pytest.raises(oracle.Breakdown):
-        oracle.factor(X, 8, "bcgsi+p-1s")
-    assert cuda.STATUS[code] in ("not_spd", "nonfinite") and blk >= 2
+    for v in PYTHAGOREAN:
+        _, _, code, blk = run_gpu(cuda, X, 8, v)
+        with pytest.raises(oracle.Breakdown):
+            oracle.factor(X, 8, v)
+        assert cuda.STATUS[code] in ("not_spd", "nonfinite") and blk >= 2
     for v in ("bcgsi+", "bcgsi+p-2s"):
         Q, R, code, _ = run_gpu(cuda, X, 8, v)
         assert code == 0
@@ -126,7 +130,7 @@ def test_step_interface_matches_factor(cuda, variant):
         h.step(Xd[:, j * s:(j + 1) * s])
         code, n_final, _ = h.sync()
         assert code == 0
-        if variant == "bcgsi+":
+        if variant in ("bcgsi+", "bcgs-pipi+"):
             assert n_final == (j + 1) * s
         else:
             assert n_final == max(j, 1) * s
