@@ -319,6 +319,7 @@ def main_ours(args):
     if not args.no_forms and world == 1:
         del main["Q"], main["R"]
         forms = {"fp32_storage": bench_fp32(args, dev, stream),
+                 "block_sizes": bench_block_sizes(args, dev, stream),
                  "batched": bench_batched(args, dev, stream),
                  "serving": bench_serving(args, dev)}
 
@@ -434,6 +435,44 @@ def bench_fp32(args, dev, stream):
             "value": alg_bytes_1s(m, n, s, b=4) / (ms * 1e-3) / 1e9, "unit": "GB/s",
             "ms_per_step": ms, "status": bcgs.STATUS[code], "loo": loo,
             "residual_vs_fp64_x": res, "bound": "FP64 ALU (products accumulated in FP64)"}
+
+
+# Table 2 of the paper: speedup over CGSI+ (BCGSI+ with s = 1) at 10^6 x 400 on
+# 64 nodes, by variant and block size s
+TABLE2_64_NODES = {
+    "bcgsi+p-2s": {1: 1.3, 2: 2.6, 4: 5.2, 8: 10.2, 16: 15.9},
+    "bcgsi+p-1s": {1: 2.8, 2: 5.4, 4: 10.8, 8: 20.0, 16: 37.5},
+    "bcgs-pipi+": {1: 1.6, 2: 3.0, 4: 5.9, 8: 11.7, 16: 22.7},
+    "bcgsi+": {1: 1.0, 2: 1.4, 4: 2.7, 8: 5.4, 16: 8.8},
+}
+
+
+def bench_block_sizes(args, dev, stream):
+    """Block-size form, the one-GPU analog of Table 2: m = 10^6, n = 400,
+    s in {1, 2, 4, 8, 16}, every variant timed as one factorization (one warm-up,
+    one timed run each); speedup over CGSI+ = BCGSI+ with s = 1."""
+    import torch
+
+    from paper_2507_21791_gb300 import bcgs, synth
+
+    m, n, kappa = 10 ** 6, 400, 1e5
+    X = synth.make_matrix_torch(m, n, kappa, seed=1300, device=str(dev))
+    Q = bcgs.empty_colmajor(m, n, torch.float64, dev)
+    R = bcgs.empty_colmajor(n, n, torch.float64, dev)
+    ms, status = {}, {}
+    for v in TABLE2_64_NODES:
+        ms[v], status[v] = {}, {}
+        for s in (1, 2, 4, 8, 16):
+            ws = torch.empty(bcgs.workspace_size(m, n, s, v), dtype=torch.uint8, device=dev)
+            ms[v][s] = _timed(lambda: bcgs.factor_async(X, s, v, "fp64", Q, R, ws), 1, 1, stream)
+            status[v][s] = bcgs.STATUS[bcgs.factor_status(ws)[0]]
+            del ws
+    base = ms["bcgsi+"][1]
+    speedup = {v: {s: base / t for s, t in row.items()} for v, row in ms.items()}
+    return {"workload": f"m=10^6 n=400 kappa={kappa:g}, s in (1, 2, 4, 8, 16), FP64",
+            "ms": ms, "status": status, "speedup_vs_cgsi_plus": speedup,
+            "paper_speedup_64_nodes": TABLE2_64_NODES,
+            "note": "one warm-up and one timed factorization per cell; CGSI+ = BCGSI+ at s = 1"}
 
 
 def bench_batched(args, dev, stream):

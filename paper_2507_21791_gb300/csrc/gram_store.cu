@@ -162,23 +162,42 @@ __global__ void __launch_bounds__(kThreads, 1) gram_store_kernel(GramStoreDesc d
       };
       bool ok = true;
       int issuedA = 0, issuedB = 0, gotA = 0, gotB = 0;
-      if (nbl > 0) {
-        issue_B(0);
-        issuedB = 1;
-      }
+      for (; issuedB < 2 && issuedB < nbl; ++issuedB) issue_B(issuedB);
       for (; issuedA < S && issuedA < ntot; ++issuedA) issue_A(issuedA);
-      int a = 0;
-      for (int bl = 0; bl < nbl && ok; ++bl) {
-        const int p = bl & 1;
-        ok = mbar_wait_bounded(&fullB[p], (bl >> 1) & 1);
-        if (ok) gotB = bl + 1;
-        if (ok && bl >= 2) ok = mbar_wait_bounded(&accfree[p], ((bl >> 1) - 1) & 1);
-        tc_after_sync();
-        for (int t = 0; t < kDigits && ok; ++t, ++a) {
-          const int slot = a % S;
-          ok = mbar_wait_bounded(&fullA[slot], (a / S) & 1);
-          if (!ok) break;
+      // Event loop: A slots and B buffers are refilled as soon as the MMAs that
+      // read them are done, and a chunk's MMAs go out as soon as its operands are
+      // ready, so every copy slot stays in flight while the tensor core waits.
+      // No progress for kWaitCycles ends the loop with a failure.
+      int a = 0, need = 0;  // chunk a = (block a / 8, digit a % 8); need: 0 = B, 1 = accumulator, 2 = A
+      long long idle0 = clock64();
+      while (a < ntot) {
+        bool progress = false;
+        const int xa = issuedA - S;  // the chunk that last used the slot of chunk issuedA
+        if (issuedA < ntot && xa < a && mbar_test(&doneA[xa % S], (xa / S) & 1)) {
+          issue_A(issuedA);
+          ++issuedA;
+          progress = true;
+        }
+        // B of block issuedB into the buffer of block issuedB - 2 once all its MMAs are done
+        const int xb = issuedB - 2;
+        if (issuedB < nbl && (xb + 1) * kDigits <= a && mbar_test(&accdone[xb & 1], (xb >> 1) & 1)) {
+          issue_B(issuedB);
+          ++issuedB;
+          progress = true;
+        }
+        const int bl = a / kDigits, t = a % kDigits, p = bl & 1, slot = a % S;
+        if (need == 0) {
+          if (t != 0) {
+            need = 1;
+          } else if (mbar_test(&fullB[p], (bl >> 1) & 1)) {
+            gotB = bl + 1;
+            need = 1;
+          }
+        }
+        if (need == 1 && (t != 0 || bl < 2 || mbar_test(&accfree[p], ((bl >> 1) - 1) & 1))) need = 2;
+        if (need == 2 && mbar_test(&fullA[slot], (a / S) & 1)) {
           gotA = a + 1;
+          tc_after_sync();
           const uint32_t acc = tmem + (uint32_t)(p * C::kAcc + t * NBT);
           const uint32_t a0 = smem_u32(Aring + slot * kDigBytes);
           const uint32_t b0 = smem_u32(Bbuf + p * C::kBBuf);
@@ -190,23 +209,15 @@ __global__ void __launch_bounds__(kThreads, 1) gram_store_kernel(GramStoreDesc d
                      (t == 0 && ks == 0) ? 0u : 1u);
           mma_commit(&doneA[slot]);
           if (t == kDigits - 1) mma_commit(&accdone[p]);
-          if (t == 3 && bl + 1 < nbl) {
-            // the next block's B into the other buffer, free once block bl - 1 is multiplied
-            if (bl >= 1) ok = mbar_wait_bounded(&accdone[(bl - 1) & 1], ((bl - 1) >> 1) & 1);
-            if (ok) {
-              issue_B(bl + 1);
-              issuedB = bl + 2;
-            }
-          }
-          // refill the slot of chunk a - 1 (its MMAs ran while chunk a's copy landed)
-          const int na = a - 1 + S;
-          if (ok && a >= 1 && na < ntot && na >= issuedA) {
-            ok = mbar_wait_bounded(&doneA[(a - 1) % S], ((a - 1) / S) & 1);
-            if (ok) {
-              issue_A(na);
-              issuedA = na + 1;
-            }
-          }
+          ++a;
+          need = 0;
+          progress = true;
+        }
+        if (progress) {
+          idle0 = clock64();
+        } else if (clock64() - idle0 > kWaitCycles) {
+          ok = false;
+          break;
         }
       }
       if (!ok) {

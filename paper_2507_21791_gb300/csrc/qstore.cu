@@ -370,38 +370,54 @@ __global__ void __launch_bounds__(kThreads, 1) proj_store_kernel(StoreProjDesc d
       };
       int issued = 0, got = 0;
       for (; issued < kStages && issued < total; ++issued) issue_copy(issued);
-      bool ok = true;
-      for (int g = 0; g < total && ok; ++g) {
+      // Event loop: a slot is refilled as soon as the MMAs of its last chunk are
+      // done, and a chunk's MMAs go out as soon as its operands are ready, so all
+      // kStages copies stay in flight while the tensor core waits for data.  No
+      // progress for kWaitCycles (or an abort elsewhere) ends the loop.
+      int g = 0, need = 0;  // need: 0 = A of chunk g, 1 = its B' digits, 2 = a free accumulator set
+      long long idle0 = clock64();
+      while (g < total) {
+        bool progress = false;
+        const int x = issued - kStages;  // the chunk that last used the slot of chunk `issued`
+        if (issued < total && x < g && mbar_test(&done[x % kStages], (x / kStages) & 1)) {
+          issue_copy(issued);
+          ++issued;
+          progress = true;
+        }
         const int slot = g % kStages, kc = g % nch, bi = g / nch;
         const int gg = bi * ngrp + kc / kGroupChunks;
         const bool first = kc % kGroupChunks == 0;
         const int bslot = g % C::kBRing;
-        ok = wait_or_abort(&fullA[slot], (g / kStages) & 1, &s_abort);
-        if (ok) got = g + 1;
-        if (ok) ok = wait_or_abort(&bready[bslot], (g / C::kBRing) & 1, &s_abort);
-        if (ok && first && gg >= 2) ok = wait_or_abort(&accfree[gg & 1], ((gg >> 1) - 1) & 1, &s_abort);
-        if (!ok) break;
-        tc_after_sync();
-        const uint32_t a0 = smem_u32(Aring + slot * kAStage);
-        const uint32_t b0 = smem_u32(Bring + bslot * C::kBStage);
-        const uint32_t acc = tmem + (uint32_t)((gg & 1) * C::kAcc);
-        // digit t of A times digit tiles [B_0 .. B_{7-t}]: tile u lands in level t + u
+        if (need == 0 && mbar_test(&fullA[slot], (g / kStages) & 1)) {
+          need = 1;
+          got = g + 1;
+        }
+        if (need == 1 && mbar_test(&bready[bslot], (g / C::kBRing) & 1)) need = 2;
+        if (need == 2 && (!first || gg < 2 || mbar_test(&accfree[gg & 1], ((gg >> 1) - 1) & 1))) {
+          tc_after_sync();
+          const uint32_t a0 = smem_u32(Aring + slot * kAStage);
+          const uint32_t b0 = smem_u32(Bring + bslot * C::kBStage);
+          const uint32_t acc = tmem + (uint32_t)((gg & 1) * C::kAcc);
+          // digit t of A times digit tiles [B_0 .. B_{7-t}]: tile u lands in level t + u
 #pragma unroll 1
-        for (int t = 0; t < kDigits; ++t)
-          mma_bf16(acc + (uint32_t)(t * NBT), desc_interleave(a0 + t * kATileT, 2048, 128),
-                   desc_interleave(b0, 128, 256), idesc_f16(kRows, (kDigits - t) * NBT),
-                   (first && t == 0) ? 0u : 1u);
-        mma_commit(&done[slot]);
-        mma_commit(&bdone[bslot]);
-        if (kc % kGroupChunks == kGroupChunks - 1 || kc == nch - 1) mma_commit(&accdone[gg & 1]);
-        // refill the slot of chunk g - 1 (free once its MMAs are done) with chunk g + 3
-        const int ng = g + kStages - 1;
-        if (g >= 1 && ng < total && ng >= issued) {
-          ok = wait_or_abort(&done[(g - 1) % kStages], ((g - 1) / kStages) & 1, &s_abort);
-          if (ok) {
-            issue_copy(ng);
-            issued = ng + 1;
-          }
+          for (int t = 0; t < kDigits; ++t)
+            mma_bf16(acc + (uint32_t)(t * NBT), desc_interleave(a0 + t * kATileT, 2048, 128),
+                     desc_interleave(b0, 128, 256), idesc_f16(kRows, (kDigits - t) * NBT),
+                     (first && t == 0) ? 0u : 1u);
+          mma_commit(&done[slot]);
+          mma_commit(&bdone[bslot]);
+          if (kc % kGroupChunks == kGroupChunks - 1 || kc == nch - 1) mma_commit(&accdone[gg & 1]);
+          ++g;
+          need = 0;
+          progress = true;
+        }
+        if (progress) {
+          idle0 = clock64();
+        } else if (s_abort) {
+          break;
+        } else if (clock64() - idle0 > kWaitCycles) {
+          s_abort = 1;
+          break;
         }
       }
       // copies still in flight land before the CTA's shared memory goes away

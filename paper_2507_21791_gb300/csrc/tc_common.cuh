@@ -77,6 +77,18 @@ __device__ __forceinline__ bool mbar_try(uint32_t mbar, uint32_t phase) {
   return ok != 0;
 }
 
+// Non-blocking test of the phase (for event loops that watch several barriers).
+__device__ __forceinline__ bool mbar_test(uint64_t* mbar, uint32_t phase) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(mbar)), "r"(phase)
+      : "memory");
+  return ok != 0;
+}
+
 template <typename T>
 __device__ __forceinline__ double ld_elem(const void* base, int64_t idx) {
   return (double)__ldg(reinterpret_cast<const T*>(base) + idx);

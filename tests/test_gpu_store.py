@@ -18,10 +18,10 @@ U64 = np.finfo(np.float64).eps / 2
 pytestmark = pytest.mark.gpu
 
 # (m, n, s, kappa): ragged row blocks, s not a multiple of 8, c not a multiple of
-# 16, column groups past 128, s > 16 (single projections only)
+# 16, column groups past 128, s > 16 (single projections only), s = 1 (CGSI+) and 2
 SHAPES = [(129, 40, 5, 1e3), (1000, 60, 3, 1e4), (3001, 72, 12, 1e5), (12345, 128, 8, 1e4),
           (20000, 160, 16, 1e5), (5000, 96, 24, 1e3), (700, 64, 4, 1e2), (40000, 272, 16, 1e5),
-          (2048, 64, 32, 1e4)]
+          (2048, 64, 32, 1e4), (3000, 20, 1, 1e3), (5000, 36, 2, 1e4)]
 
 
 @pytest.fixture
