@@ -20,9 +20,12 @@
 //     Q_k     = (U_k - [Q U_k] B[:, 0:s]) Y_kk^{-1}
 //     U_{k+1} = (X_{k+1} - [Q U_k] B[:, s:2s]) S_{k+1,k+1}^{-1}   (1S; 2S: no solve)
 // which is Q_{1:k} S_{1:k,k+1} = Q_{1:k-1} Z + Q_k W regrouped (eq. (1)).
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <string.h>
 
 #include <climits>
+#include <mutex>
 
 #include "tc_common.cuh"
 
@@ -263,7 +266,8 @@ __device__ __forceinline__ bool wait_or_abort(uint64_t* mbar, uint32_t parity, v
 
 template <int NBT, int NOUT>
 __global__ void __launch_bounds__(kThreads, 1) proj_store_kernel(StoreProjDesc d, int32_t b_staged,
-                                                                  DevStatus* st) {
+                                                                  const __grid_constant__ CUtensorMap amap,
+                                                                  int32_t use_amap, DevStatus* st) {
   using C = SPCfg<NBT, NOUT>;
   static_assert(NBT == 16 || NBT == 32, "N tile");
   constexpr int kHalf = NBT / 2;                 // read-back columns per thread
@@ -358,10 +362,17 @@ __global__ void __launch_bounds__(kThreads, 1) proj_store_kernel(StoreProjDesc d
   if (warp == kCtl) {
     // ------------------------------------------------ copies and MMAs
     if (lane == 0) {
+      // one chunk = the 4 KB piece kc & 7 of the 8 digit tiles of store tile (b, kc >> 3):
+      // one tensor copy through amap (box {256, 2, 1, 8, 1} of u64 at x = 0), else 8 bulk copies
       auto issue_copy = [&](int g) {
         const int slot = g % kStages, kc = g % nch;
         const int64_t b = blk_of(g / nch);
         mbar_arrive_expect_tx(&fullA[slot], kAStage);
+        if (use_amap) {
+          tma_load_5d(Aring + slot * kAStage, &amap, 0, 0, kc & 7, 0, (int32_t)(b * d.qs.ngroups + (kc >> 3)),
+                      &fullA[slot]);
+          return;
+        }
         const uint8_t* src = d.qs.dig + (size_t)b * d.qs.ngroups * kStoreTileBytes +
                              (size_t)(kc >> 3) * kStoreTileBytes + (size_t)(kc & 7) * kATileT;
 #pragma unroll
@@ -658,6 +669,38 @@ __global__ void __launch_bounds__(kThreads, 1) proj_store_kernel(StoreProjDesc d
 
 int g_sm_count = 0;
 
+// cuTensorMapEncodeTiled from the driver, looked up once through the runtime
+// (no link against libcuda); null when the driver does not provide it.
+PFN_cuTensorMapEncodeTiled_v12000 encode_tiled() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+// The digit store as a 5-d tensor of u64 (innermost first): 256 x 2 (one 4 KB
+// piece = 16 columns of one digit of a tile), 8 pieces, 8 digits, nblk * ngroups
+// tiles; strides 2 KB, 4 KB, 32 KB, 256 KB.  False when it cannot be encoded.
+bool store_tensor_map(const QStore& qs, CUtensorMap* map) {
+  PFN_cuTensorMapEncodeTiled_v12000 fn = encode_tiled();
+  if (fn == nullptr) return false;
+  const cuuint64_t dims[5] = {256, 2, 8, (cuuint64_t)kDigits, (cuuint64_t)qs.nblk * (cuuint64_t)qs.ngroups};
+  const cuuint64_t strides[4] = {2048, (cuuint64_t)kATileT, (cuuint64_t)kDigTile, (cuuint64_t)kStoreTileBytes};
+  const cuuint32_t box[5] = {256, 2, 1, (cuuint32_t)kDigits, 1};
+  const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+  if (dims[4] == 0 || dims[4] > (1ull << 32)) return false;
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 5, qs.dig, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 template <int NBT, int NOUT>
 cudaError_t launch_sp(const StoreProjDesc& d, DevStatus* st, cudaStream_t stream) {
   using C = SPCfg<NBT, NOUT>;
@@ -679,7 +722,10 @@ cudaError_t launch_sp(const StoreProjDesc& d, DevStatus* st, cudaStream_t stream
   const int64_t fgrid = ceil_div(d.qs.nblk, 8);
   proj_fexp_kernel<NBT, NOUT><<<(unsigned)(fgrid < 4 * sms ? fgrid : 4 * sms), 256, fsmem, stream>>>(d, st);
   const unsigned grid = (unsigned)(d.qs.nblk < sms ? d.qs.nblk : (int64_t)sms);
-  proj_store_kernel<NBT, NOUT><<<grid, kThreads, smem, stream>>>(d, staged, st);
+  CUtensorMap amap;
+  memset(&amap, 0, sizeof(amap));
+  const int32_t use_amap = store_tensor_map(d.qs, &amap) ? 1 : 0;
+  proj_store_kernel<NBT, NOUT><<<grid, kThreads, smem, stream>>>(d, staged, amap, use_amap, st);
   return cudaSuccess;
 }
 
