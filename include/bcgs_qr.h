@@ -106,6 +106,25 @@ BCGS_API int bcgs_qr_factor(int64_t m, int32_t n, int32_t s, int variant, int pr
                    const void* X, int64_t ldx, void* Q, int64_t ldq, double* R,
                    int32_t ldr, void* workspace, size_t ws_bytes, void* stream);
 
+/* The same factorization end to end from host memory.  X_host (m x n,
+ * leading dimension ldxh) is copied to the device buffer Xd (ldx) one block
+ * column at a time on a copy stream, so that block j + 1 travels while block
+ * j is factored on `stream`; every block column of Q is copied from Qd (ldq)
+ * to Q_host (ldqh) on a second copy stream as soon as it is final (delayed
+ * normalization, Sec. 2: block j - 1 after step j under BCGSI+P-1S and -2S,
+ * block j under BCGSI+ and BCGS-PIPI+), and R (n x n) goes from Rd (ldr) to
+ * R_host (ldrh) at the end.  Xd, Qd, Rd and the workspace (as for
+ * bcgs_qr_factor) are caller-owned device memory; X_host, Q_host and R_host
+ * are host memory, page-locked for the copies to overlap (pageable memory
+ * works, without overlap).  Everything is ordered on `stream`: the results
+ * are on the host once `stream` has completed, and the status is read with
+ * bcgs_qr_factor_status.  Returns BCGS_ERR_INVALID_ARG for a null pointer or
+ * a leading dimension below m (n for R). */
+BCGS_API int bcgs_qr_factor_host(int64_t m, int32_t n, int32_t s, int variant, int precision,
+                   const void* X_host, int64_t ldxh, void* Q_host, int64_t ldqh, double* R_host,
+                   int32_t ldrh, void* Xd, int64_t ldx, void* Qd, int64_t ldq, double* Rd,
+                   int32_t ldr, void* workspace, size_t ws_bytes, void* stream);
+
 /* Synchronize `stream`, then return the device status word of the last
  * factorization that used `workspace`; *fail_block (may be NULL) gets the
  * 1-based block column at which it failed, 0 on success. */

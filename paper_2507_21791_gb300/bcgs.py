@@ -39,6 +39,8 @@ SIGNATURES = [
     ("bcgs_qr_workspace_size", ctypes.c_int, [_i64, _i32, _i32, ctypes.c_int, ctypes.c_int, _psz]),
     ("bcgs_qr_factor", ctypes.c_int, [_i64, _i32, _i32, ctypes.c_int, ctypes.c_int, _vp, _i64, _vp,
                                       _i64, _vp, _i32, _vp, _sz, _vp]),
+    ("bcgs_qr_factor_host", ctypes.c_int, [_i64, _i32, _i32, ctypes.c_int, ctypes.c_int, _vp, _i64, _vp,
+                                           _i64, _vp, _i32, _vp, _i64, _vp, _i64, _vp, _i32, _vp, _sz, _vp]),
     ("bcgs_qr_factor_status", ctypes.c_int, [_vp, _vp, _pi32]),
     ("bcgs_qr_init", ctypes.c_int, [ctypes.POINTER(_vp), _i64, _i32, _i32, ctypes.c_int, ctypes.c_int,
                                     _vp, _i64, _vp, _i32, _vp, _sz, _vp]),
@@ -177,6 +179,25 @@ def factor_async(X, s, variant, precision, Q, R, workspace, stream=None):
                             _colmajor_ld(R), workspace.data_ptr(), workspace.numel(),
                             _stream_ptr(stream))
     _check(rc, "bcgs_qr_factor")
+
+
+def factor_host_async(Xh, s, variant, precision, Qh, Rh, Xd, Qd, Rd, workspace, stream=None):
+    """End-to-end factorization from host memory (bcgs_qr_factor_host): Xh, Qh,
+    Rh are column-major CPU tensors (pinned for the copies to overlap the
+    factorization), Xd, Qd, Rd column-major device tensors of the same shapes.
+    Enqueue only; the host results are complete once the stream is."""
+    lib = load_library()
+    m, n = Xh.shape
+    for name, t, dev in (("Xh", Xh, False), ("Qh", Qh, False), ("Rh", Rh, False), ("Xd", Xd, True),
+                         ("Qd", Qd, True), ("Rd", Rd, True)):
+        if t.is_cuda != dev:
+            raise ValueError(f"{name} must be a {'device' if dev else 'host'} tensor")
+    rc = lib.bcgs_qr_factor_host(m, n, s, VARIANTS[variant], PRECISIONS[precision], Xh.data_ptr(),
+                                 _colmajor_ld(Xh), Qh.data_ptr(), _colmajor_ld(Qh), Rh.data_ptr(),
+                                 _colmajor_ld(Rh), Xd.data_ptr(), _colmajor_ld(Xd), Qd.data_ptr(),
+                                 _colmajor_ld(Qd), Rd.data_ptr(), _colmajor_ld(Rd), workspace.data_ptr(),
+                                 workspace.numel(), _stream_ptr(stream))
+    _check(rc, "bcgs_qr_factor_host")
 
 
 def factor_status(workspace, stream=None):

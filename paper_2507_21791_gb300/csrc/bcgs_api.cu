@@ -637,6 +637,34 @@ int batch_streams(BatchStreams** out) {
   return BCGS_OK;
 }
 
+// The two copy streams of bcgs_qr_factor_host (one per direction) and the
+// events that order them against the caller's stream, one set per device.
+struct CopyStreams {
+  cudaStream_t h2d, d2h;
+  cudaEvent_t start, in, out, done;
+};
+std::mutex g_copy_mu;
+CopyStreams* g_copy[64] = {nullptr};
+
+int copy_streams(CopyStreams** out) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return BCGS_ERR_CUDA;
+  std::lock_guard<std::mutex> lk(g_copy_mu);
+  if (g_copy[dev] == nullptr) {
+    CopyStreams* cs = new (std::nothrow) CopyStreams;
+    if (cs == nullptr) return BCGS_ERR_INVALID_ARG;
+    if (cudaStreamCreateWithFlags(&cs->h2d, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&cs->d2h, cudaStreamNonBlocking) != cudaSuccess)
+      return BCGS_ERR_CUDA;
+    cudaEvent_t* evs[4] = {&cs->start, &cs->in, &cs->out, &cs->done};
+    for (cudaEvent_t* e : evs)
+      if (cudaEventCreateWithFlags(e, cudaEventDisableTiming) != cudaSuccess) return BCGS_ERR_CUDA;
+    g_copy[dev] = cs;
+  }
+  *out = g_copy[dev];
+  return BCGS_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -705,6 +733,74 @@ int bcgs_qr_factor(int64_t m, int32_t n, int32_t s, int variant, int precision, 
     if (rc != BCGS_OK) return rc;
   }
   return finish_handle(h);
+}
+
+int bcgs_qr_factor_host(int64_t m, int32_t n, int32_t s, int variant, int precision, const void* X_host,
+                        int64_t ldxh, void* Q_host, int64_t ldqh, double* R_host, int32_t ldrh, void* Xd,
+                        int64_t ldx, void* Qd, int64_t ldq, double* Rd, int32_t ldr, void* workspace,
+                        size_t ws_bytes, void* stream) {
+  if (X_host == nullptr || Q_host == nullptr || R_host == nullptr || Xd == nullptr) return BCGS_ERR_INVALID_ARG;
+  if (ldxh < m || ldqh < m || ldx < m || ldrh < n) return BCGS_ERR_INVALID_ARG;
+  bcgs_qr_s hs;
+  bcgs_qr_s* h = &hs;
+  int rc = init_handle(h, m, n, s, variant, precision, Qd, ldq, Rd, ldr, workspace, ws_bytes, stream);
+  if (rc != BCGS_OK) return rc;
+  CopyStreams* cs = nullptr;
+  rc = copy_streams(&cs);
+  if (rc != BCGS_OK) return rc;
+  const size_t esz = precision == BCGS_FP32_STORAGE ? 4 : 8;
+  const int q = n / s;
+  const cudaStream_t main = h->stream;
+  const char* Xh = reinterpret_cast<const char*>(X_host);
+  char* Qh = reinterpret_cast<char*>(Q_host);
+  char* Xdc = reinterpret_cast<char*>(Xd);
+  const char* Qdc = reinterpret_cast<const char*>(Qd);
+  // block columns [k0, k1) of X to the device, of Q to the host
+  auto h2d = [&](int k0, int k1) {
+    return cudaMemcpy2DAsync(Xdc + (size_t)k0 * s * ldx * esz, (size_t)ldx * esz, Xh + (size_t)k0 * s * ldxh * esz,
+                             (size_t)ldxh * esz, (size_t)m * esz, (size_t)(k1 - k0) * s, cudaMemcpyHostToDevice,
+                             cs->h2d);
+  };
+  auto d2h = [&](int k0, int k1) {
+    return cudaMemcpy2DAsync(Qh + (size_t)k0 * s * ldqh * esz, (size_t)ldqh * esz, Qdc + (size_t)k0 * s * ldq * esz,
+                             (size_t)ldq * esz, (size_t)m * esz, (size_t)(k1 - k0) * s, cudaMemcpyDeviceToHost,
+                             cs->d2h);
+  };
+  // the copies start after what `stream` already holds (Xd, Qd may still be in use)
+  TRY(cudaEventRecord(cs->start, main));
+  TRY(cudaStreamWaitEvent(cs->h2d, cs->start, 0));
+  TRY(cudaStreamWaitEvent(cs->d2h, cs->start, 0));
+  TRY(h2d(0, 1));
+  TRY(cudaEventRecord(cs->in, cs->h2d));
+  TRY(cudaStreamWaitEvent(main, cs->in, 0));
+  const bool delayed = variant == BCGS_BCGSI_PLUS_P_1S || variant == BCGS_BCGSI_PLUS_P_2S;
+  int sent = 0;  // Q blocks already on their way to the host
+  for (int k = 0; k < q; ++k) {
+    if (k + 1 < q) TRY(h2d(k + 1, k + 2));  // travels while block k is factored
+    rc = step_handle(h, Xdc + (size_t)k * s * ldx * esz, ldx);
+    if (rc != BCGS_OK) return rc;
+    if (k + 1 < q) {
+      TRY(cudaEventRecord(cs->in, cs->h2d));
+      TRY(cudaStreamWaitEvent(main, cs->in, 0));
+    }
+    const int final_blocks = delayed ? (k > 1 ? k : 1) : k + 1;
+    if (final_blocks > sent) {
+      TRY(cudaEventRecord(cs->out, main));
+      TRY(cudaStreamWaitEvent(cs->d2h, cs->out, 0));
+      TRY(d2h(sent, final_blocks));
+      sent = final_blocks;
+    }
+  }
+  rc = finish_handle(h);
+  if (rc != BCGS_OK) return rc;
+  TRY(cudaEventRecord(cs->out, main));
+  TRY(cudaStreamWaitEvent(cs->d2h, cs->out, 0));
+  if (sent < q) TRY(d2h(sent, q));
+  TRY(cudaMemcpy2DAsync(R_host, (size_t)ldrh * sizeof(double), Rd, (size_t)ldr * sizeof(double),
+                        (size_t)n * sizeof(double), (size_t)n, cudaMemcpyDeviceToHost, cs->d2h));
+  TRY(cudaEventRecord(cs->done, cs->d2h));
+  TRY(cudaStreamWaitEvent(main, cs->done, 0));
+  return BCGS_OK;
 }
 
 int bcgs_qr_factor_status(const void* workspace, void* stream, int32_t* fail_block) {

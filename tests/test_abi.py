@@ -101,6 +101,11 @@ def test_bad_enums_and_null_pointers_rejected():
     h = ctypes.c_void_p(None)
     assert lib.bcgs_qr_init(ctypes.byref(h), 100, 16, 8, 1, 0, None, 100, 32, 16, 256, 1 << 20, None) == 1
     assert lib.bcgs_qr_step(None, None, 100) == 1
+    # host entry point: null host or device pointers, leading dimensions below m
+    assert lib.bcgs_qr_factor_host(100, 16, 8, 1, 0, None, 100, 8, 100, 8, 16, 8, 100, 8, 100, 8, 16, 256,
+                                   1 << 20, None) == 1
+    assert lib.bcgs_qr_factor_host(100, 16, 8, 1, 0, 8, 99, 8, 100, 8, 16, 8, 100, 8, 100, 8, 16, 256,
+                                   1 << 20, None) == 1
     # misaligned workspace
     assert lib.bcgs_qr_factor(100, 16, 8, 1, 0, 8, 100, 16, 100, 32, 16, 257, 1 << 20, None) == 5
     # too small workspace
