@@ -516,16 +516,19 @@ def bench_serving(args, dev):
 
     sources, meta = draw_sources(24, seed=1400, device=str(dev))
     out = {}
-    for rate, window in ((2000.0, 4.0), (10.0, 4.0)):
+    # the same unsaturated arrivals with lazy (delayed) and eager finalization
+    for rate, window, eager, key in ((2000.0, 4.0, 0.0, "lambda_2000"), (10.0, 4.0, 0.0, "lambda_10"),
+                                     (10.0, 4.0, 1.0, "lambda_10_eager")):
         be = GpuBackend(sources, variant="bcgsi+p-2s", nstreams=32, device=str(dev))
         srv = Server(be, budget_bytes=120e9)
-        reqs = make_requests(rate, window, meta, seed=int(rate))
+        reqs = make_requests(rate, window, meta, seed=int(rate), eager_frac=eager)
         rep = srv.run(reqs, duration=window)
         rep["offered_req_per_s"] = rate
         rep["arrivals"] = len(reqs)
-        out[f"lambda_{int(rate)}"] = rep
+        out[key] = rep
     return {"workload": "Poisson Krylov-basis requests, m=2^U(14,20), q~U{4..32}, s in {4,8,16}, "
-                        "120 GB budget, BCGSI+P-2S, pool of 24 pre-generated bases", **out}
+                        "120 GB budget, BCGSI+P-2S (lazy) or BCGSI+ (eager finalize), pool of 24 "
+                        "pre-generated bases", **out}
 
 
 def main_kernel(args):

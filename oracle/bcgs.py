@@ -18,8 +18,8 @@ each algorithm states.
 Pins (tests/test_oracle_pins.py): agreement with LAPACK QR and with a 60-digit
 QR on small inputs, exact recovery of a Hadamard-based closed form, s = n and
 s = 1 special cases, recovery of R0 from X = Q0 R0, cross-variant agreement,
-the Pythagorean identity, eq. (1) against the direct product, and the loss of
-orthogonality ordering of Table 1.
+the Pythagorean identity, eq. (1) against the direct product, the loss of
+orthogonality ordering of Table 1, and LAPACK's R for a ragged last block.
 """
 from __future__ import annotations
 
@@ -28,7 +28,8 @@ import numpy as np
 __all__ = [
     "Breakdown", "householder_qr", "tsqr", "chol", "solve_right_upper",
     "solve_left_upper_t", "delayed_projection", "gram", "project_normalize",
-    "bcgsi_plus", "bcgsi_plus_p_1s", "bcgsi_plus_p_2s", "factor", "VARIANTS",
+    "bcgsi_plus", "bcgsi_plus_p_1s", "bcgsi_plus_p_2s", "bcgs_pipi_plus", "eager_step", "factor",
+    "VARIANTS", "EAGER_FAMILY",
 ]
 
 
@@ -395,6 +396,63 @@ VARIANTS = {
 }
 
 
+# The variant whose step finalizes a block at once, in the stability range of
+# each variant (Table 1): BCGSI+ for BCGSI+ and BCGSI+P-2S, BCGS-PIPI+ for
+# BCGSI+P-1S and BCGS-PIPI+.
+EAGER_FAMILY = {"bcgsi+": "bcgsi+", "bcgsi+p-2s": "bcgsi+", "bcgsi+p-1s": "bcgs-pipi+",
+                "bcgs-pipi+": "bcgs-pipi+"}
+
+
+def eager_step(Qk: np.ndarray, Xn: np.ndarray, family: str, block: int):
+    """One block step of BCGSI+ or of BCGS-PIPI+ (Alg. 1) for a new block Xn of
+    any width against the final basis Qk; returns Q_new, R_{1:k,new}, R_new,new.
+        BCGSI+:      S = Q^T Xn, [U, S_nn] = TSQR(Xn - Q S), Y = Q^T U, [Q_new, Y_nn] = TSQR(U - Q Y)
+        BCGS-PIPI+:  [S; T] = [Q Xn]^T Xn, S_nn = chol(T - S^T S), U = (Xn - Q S) S_nn^{-1},
+                     [Y; Omega] = [Q U]^T U, Y_nn = chol(Omega - Y^T Y), Q_new = (U - Q Y) Y_nn^{-1}
+        R_{1:k,new} = S + Y S_nn,  R_new,new = Y_nn S_nn
+    """
+    c = Qk.shape[1]
+    if family == "bcgsi+":
+        S = gram([Qk], [Xn])
+        U, Skk = tsqr(Xn - Qk @ S, block)
+        Y = gram([Qk], [U])
+        Qn, Ykk = tsqr(U - Qk @ Y, block)
+    else:
+        G1 = gram([Qk, Xn], [Xn])
+        S, T = G1[:c], G1[c:]
+        Skk = chol(T - S.T @ S, block)
+        U = project_normalize(Xn, Qk, S, Skk)
+        G2 = gram([Qk, U], [U])
+        Y, Om = G2[:c], G2[c:]
+        Ykk = chol(Om - Y.T @ Y, block)
+        Qn = project_normalize(U, Qk, Y, Ykk)
+    return Qn, S + Y @ Skk, Ykk @ Skk
+
+
 def factor(X: np.ndarray, s: int, variant: str):
-    """Dispatch by variant name ("bcgsi+", "bcgsi+p-1s", "bcgsi+p-2s", "bcgs-pipi+")."""
-    return VARIANTS[variant](X, s)
+    """Dispatch by variant name ("bcgsi+", "bcgsi+p-1s", "bcgsi+p-2s", "bcgs-pipi+").
+
+    n need not be a multiple of s (the paper assumes it is).  Reading for a
+    ragged last block of r = n mod s columns: the first n - r columns are
+    factored by the variant (its last full block finalized as in its own last
+    step), then the ragged block takes one step of EAGER_FAMILY[variant]; for
+    n < s the factorization is TSQR(X) alone.
+    """
+    X = np.asarray(X, dtype=np.float64)
+    m, n = X.shape
+    r = n % s if s >= 1 else 0
+    if s < 1 or r == 0:
+        return VARIANTS[variant](X, s)
+    if m < n:
+        raise ValueError("need m >= n")
+    n1 = n - r
+    q = n1 // s + 1
+    if n1 == 0:
+        return tsqr(X, 1)
+    Q1, R1 = VARIANTS[variant](X[:, :n1], s)
+    Qn, Rt, Rd = eager_step(Q1, X[:, n1:], EAGER_FAMILY[variant], q)
+    R = np.zeros((n, n))
+    R[:n1, :n1] = R1
+    R[:n1, n1:] = Rt
+    R[n1:, n1:] = Rd
+    return np.hstack([Q1, Qn]), R

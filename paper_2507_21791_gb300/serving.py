@@ -12,8 +12,15 @@ one block per call (the shape of an s-step / block Krylov basis).  The server:
     the GPU, and a new request starts as soon as memory frees up;
   * closes the loop per basis: block j+1 is issued when the call for block j
     has completed (BCGSI+P-1S/-2S finalize block j-1 at step j, eq. (1));
-  * records per-call latency (issue -> completion) and per-request latency
-    (arrival -> last block final), reported as p50 / p99.
+  * finalizes lazily or eagerly per request: "lazy" keeps the delayed
+    normalization of BCGSI+P-1S/-2S (one synchronization per block, block j
+    final one call later), "eager" runs the variant of the same stability range
+    whose blocks are final after their own call (BCGS-PIPI+ for 1S, BCGSI+ for
+    2S: one more synchronization per block, Table 1);
+  * records per-call latency (issue -> completion), per-block finalization
+    latency (issue of the block's call -> completion of the call that makes it
+    final) and per-request latency (arrival -> last block final), as p50 / p99,
+    overall and per finalize mode.
 
 The scheduling logic talks to a backend with four operations (open, issue,
 done, close), so it can be exercised on the CPU with a fake backend.
@@ -34,6 +41,7 @@ class Request:
     n: int                  # final number of columns (q blocks of s)
     s: int
     source: int = 0         # index of the pre-generated basis that supplies the blocks
+    finalize: str = "lazy"  # "lazy" (delayed normalization) or "eager"
     # runtime state
     admitted: float | None = None
     finished: float | None = None
@@ -41,6 +49,9 @@ class Request:
     finishing: bool = False
     issued_at: float | None = None
     call_latencies: list = field(default_factory=list)
+    block_issued: list = field(default_factory=list)    # issue time of each block's call
+    final_latencies: list = field(default_factory=list)  # per block: issue -> final
+    n_final: int = 0
     status: int = 0
     slot: object = None     # backend resources
 
@@ -97,6 +108,17 @@ class Server:
             self.active.append(req)
         self.max_active = max(self.max_active, len(self.active))
 
+    def _finalized(self, req, nblocks, t):
+        while req.n_final < nblocks:
+            req.final_latencies.append(t - req.block_issued[req.n_final])
+            req.n_final += 1
+
+    def _close(self, req):
+        req.status = self.backend.close(req)
+        req.finished = self.now()
+        self.reserved -= self.backend.bytes_for(req)
+        self.done.append(req)
+
     def _progress(self):
         still = []
         for req in self.active:
@@ -104,22 +126,27 @@ class Server:
                 if not self.backend.done(req):
                     still.append(req)
                     continue
-                req.call_latencies.append(self.now() - req.issued_at)
+                t = self.now()
+                req.call_latencies.append(t - req.issued_at)
                 req.issued_at = None
                 if req.finishing:
-                    req.status = self.backend.close(req)
-                    req.finished = self.now()
-                    self.reserved -= self.backend.bytes_for(req)
-                    self.done.append(req)
+                    self._finalized(req, req.q, t)
+                    self._close(req)
                     continue
-            # issue the next call of this basis
+                self._finalized(req, self.backend.final_blocks(req, req.next_block), t)
+            # issue the next call of this basis (its latency counts from here)
+            t_issue = self.now()
             if req.next_block < req.q:
+                req.block_issued.append(t_issue)
                 self.backend.issue_step(req, req.next_block)
                 req.next_block += 1
-            else:
+            elif self.backend.needs_finish(req):
                 self.backend.issue_finish(req)
                 req.finishing = True
-            req.issued_at = self.now()
+            else:  # eager: every block is final after its own call
+                self._close(req)
+                continue
+            req.issued_at = t_issue
             still.append(req)
         self.active = still
 
@@ -146,13 +173,27 @@ class Server:
                 self._progress()
         return self.report(self.now())
 
+    @staticmethod
+    def _latencies(done):
+        calls = [x for r in done for x in r.call_latencies]
+        finals = [x for r in done for x in r.final_latencies]
+        reqs = [r.finished - r.arrival for r in done]
+        return {"requests_done": len(done),
+                "call_latency_ms": {"p50": _ms(percentile(calls, 50)), "p99": _ms(percentile(calls, 99))},
+                "block_final_latency_ms": {"p50": _ms(percentile(finals, 50)), "p99": _ms(percentile(finals, 99))},
+                "request_latency_ms": {"p50": _ms(percentile(reqs, 50)), "p99": _ms(percentile(reqs, 99))}}
+
     def report(self, elapsed):
         """Latency percentiles and throughput over `elapsed` seconds (arrival
         window plus drain)."""
         calls = [x for r in self.done for x in r.call_latencies]
+        finals = [x for r in self.done for x in r.final_latencies]
         reqs = [r.finished - r.arrival for r in self.done]
         served = [r.finished - r.admitted for r in self.done]
+        modes = sorted({r.finalize for r in self.done})
         return {
+            "by_finalize": {mo: self._latencies([r for r in self.done if r.finalize == mo]) for mo in modes},
+            "block_final_latency_ms": {"p50": _ms(percentile(finals, 50)), "p99": _ms(percentile(finals, 99))},
             "requests_done": len(self.done), "requests_rejected": len(self.rejected),
             "requests_unserved": getattr(self, "unserved", 0),
             "calls_done": len(calls),
@@ -171,6 +212,21 @@ def _ms(x):
     return None if x is None else 1e3 * x
 
 
+# the variant of the same stability range (Table 1) whose blocks are final
+# after their own step, for the "eager" finalize mode
+EAGER = {"bcgsi+p-1s": "bcgs-pipi+", "bcgsi+p-2s": "bcgsi+", "bcgs-pipi+": "bcgs-pipi+", "bcgsi+": "bcgsi+"}
+DELAYED = ("bcgsi+p-1s", "bcgsi+p-2s")
+
+
+def final_blocks_after(variant: str, steps: int) -> int:
+    """Blocks of Q final after `steps` steps (before the finish call): delayed
+    normalization (Sec. 2) keeps the newest block provisional under
+    BCGSI+P-1S/-2S, except that block 1 comes final from TSQR."""
+    if variant in DELAYED:
+        return max(steps - 1, 1) if steps >= 1 else 0
+    return steps
+
+
 class GpuBackend:
     """Backend over the C ABI: one QRHandle per admitted basis, streams from a pool."""
 
@@ -187,10 +243,20 @@ class GpuBackend:
         self._next_stream = 0
         self._bytes = {}
 
+    def variant_for(self, req: Request) -> str:
+        return EAGER[self.variant] if getattr(req, "finalize", "lazy") == "eager" else self.variant
+
+    def final_blocks(self, req: Request, steps: int) -> int:
+        return final_blocks_after(self.variant_for(req), steps)
+
+    def needs_finish(self, req: Request) -> bool:
+        return self.variant_for(req) in DELAYED
+
     def bytes_for(self, req: Request) -> float:
-        key = (req.m, req.n, req.s)
+        v = self.variant_for(req)
+        key = (req.m, req.n, req.s, v)
         if key not in self._bytes:
-            ws = self.bcgs.workspace_size(req.m, req.n, req.s, self.variant)
+            ws = self.bcgs.workspace_size(req.m, req.n, req.s, v)
             self._bytes[key] = ws + 8.0 * (req.m * req.n + req.n * req.n)
         return self._bytes[key]
 
@@ -198,7 +264,7 @@ class GpuBackend:
         stream = self.streams[self._next_stream % len(self.streams)]
         self._next_stream += 1
         with self.torch.cuda.stream(stream):
-            h = self.bcgs.QRHandle(req.m, req.n, req.s, self.variant, device=self.device,
+            h = self.bcgs.QRHandle(req.m, req.n, req.s, self.variant_for(req), device=self.device,
                                    stream=stream)
         return {"h": h, "stream": stream, "ev": None}
 
@@ -228,13 +294,15 @@ class GpuBackend:
         return code
 
 
-def make_requests(rate: float, duration: float, sources_meta, seed: int = 0):
+def make_requests(rate: float, duration: float, sources_meta, seed: int = 0, eager_frac: float = 0.0):
     """Poisson arrivals at `rate` per second over `duration` seconds; request k
     takes its shape and blocks from source k mod len(sources_meta) (a pool of
-    pre-generated bases stands in for per-request generation)."""
+    pre-generated bases stands in for per-request generation) and asks for
+    eager finalization with probability eager_frac."""
     import numpy as np
 
     rng = np.random.default_rng(seed)
+    rng_mode = np.random.default_rng(seed + 7919)  # arrivals do not depend on eager_frac
     t, out, k = 0.0, [], 0
     while True:
         t += rng.exponential(1.0 / rate)
@@ -242,7 +310,8 @@ def make_requests(rate: float, duration: float, sources_meta, seed: int = 0):
             break
         src = k % len(sources_meta)
         m, n, s = sources_meta[src]
-        out.append(Request(rid=k, arrival=t, m=m, n=n, s=s, source=src))
+        mode = "eager" if rng_mode.random() < eager_frac else "lazy"
+        out.append(Request(rid=k, arrival=t, m=m, n=n, s=s, source=src, finalize=mode))
         k += 1
     return out
 

@@ -52,13 +52,14 @@ def test_batched_matches_single_and_graph_replay(cuda):
         assert torch.equal(q0, q) and torch.equal(r0, r)
 
 
-def _serve(cuda, sources, meta, rids, arrivals, budget=8e9):
+def _serve(cuda, sources, meta, rids, arrivals, budget=8e9, modes=None):
     from paper_2507_21791_gb300.serving import GpuBackend, Request, Server
 
     be = GpuBackend(sources, variant="bcgsi+p-2s", nstreams=8)
     srv = Server(be, budget_bytes=budget)
-    reqs = [Request(rid=r, arrival=a, m=meta[r][0], n=meta[r][1], s=meta[r][2], source=r)
-            for r, a in zip(rids, arrivals)]
+    modes = modes or ["lazy"] * len(rids)
+    reqs = [Request(rid=r, arrival=a, m=meta[r][0], n=meta[r][1], s=meta[r][2], source=r, finalize=f)
+            for r, a, f in zip(rids, arrivals, modes)]
     rep = srv.run(reqs, duration=120.0)
     return {r.rid: r for r in srv.done}, rep
 
@@ -99,3 +100,24 @@ def test_server_respects_the_budget(cuda):
     done, rep = _serve(cuda, sources, meta, list(range(8)), [0.0] * 8, budget=2.2 * per)
     assert rep["requests_done"] == 8
     assert rep["peak_reserved_gb"] * 1e9 <= 2.2 * per
+
+
+def test_eager_and_lazy_finalize_give_their_variants_results(cuda):
+    """Eager requests run BCGSI+ (every block final after its own call), lazy ones
+    BCGSI+P-2S (delayed normalization); each served result is bitwise the same
+    as that variant's factorization alone."""
+    import torch
+
+    from paper_2507_21791_gb300.serving import draw_sources
+
+    sources, meta = draw_sources(6, seed=8, m_exp=(12, 15), p_range=(2, 6))
+    modes = ["eager", "lazy"] * 3
+    done, rep = _serve(cuda, sources, meta, list(range(6)), [0.0] * 6, modes=modes)
+    assert rep["requests_done"] == 6 and rep["failed"] == 0
+    assert set(rep["by_finalize"]) == {"eager", "lazy"}
+    for r, req in done.items():
+        m, n, s = meta[r]
+        Q, R, code, _ = cuda.factor(sources[r][:m, :n], s, "bcgsi+" if modes[r] == "eager" else "bcgsi+p-2s")
+        assert code == 0
+        assert torch.equal(Q, req.result[0]) and torch.equal(R, req.result[1])
+        assert len(req.final_latencies) == req.q

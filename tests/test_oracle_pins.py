@@ -314,8 +314,9 @@ def test_breakdowns(variant):
     with pytest.raises(oracle.Breakdown) as e:
         oracle.factor(Xn, 2, variant)
     assert e.value.kind == "nonfinite"
+    # n mod s != 0 is a ragged last block (R9); m < n is rejected either way
     with pytest.raises(ValueError):
-        oracle.factor(X, 3, variant)
+        oracle.factor(X[:5], 3, variant)
     with pytest.raises(ValueError):
         oracle.factor(X[:1], 2, variant)
 
@@ -390,3 +391,82 @@ def test_mutation_missing_sign_normalization_is_caught(monkeypatch):
     assert np.abs(R - Rl).max() > 1e-3
     for v in VARIANTS:
         assert _recovery_error(v) > 1e-6
+
+
+# ---- a ragged last block (n mod s != 0): R is unique for a full-rank X with
+# positive diagonal, so every variant must reproduce LAPACK's sign-normalized R
+
+
+def _lapack_r(X):
+    _, R = np.linalg.qr(X)
+    return np.sign(np.diag(R))[:, None] * R
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+@pytest.mark.parametrize("m,n,s", [(300, 21, 8), (400, 13, 4), (150, 5, 8), (600, 33, 16), (200, 17, 16)])
+def test_ragged_last_block_matches_lapack(variant, m, n, s):
+    X = synth.make_matrix_np(m, n, 1e3, seed=m + n + s)
+    Q, R = oracle.factor(X, s, variant)
+    assert Q.shape == (m, n) and R.shape == (n, n)
+    Rl = _lapack_r(X)
+    assert np.linalg.norm(R - Rl) / np.linalg.norm(Rl) <= 10 * n * 1e3 * U64
+    assert oracle.loo(Q) <= 1e-13 and oracle.residual(X, Q, R) <= 1e-14
+    assert np.array_equal(np.tril(R, -1), np.zeros_like(R)) and np.all(np.diag(R) > 0)
+
+
+def test_ragged_first_columns_are_the_variants_own():
+    """The full blocks are the variant's factorization of X[:, :n - r] unchanged."""
+    X = synth.make_matrix_np(300, 21, 1e4, seed=7)
+    for v in VARIANTS:
+        Q, R = oracle.factor(X, 8, v)
+        Q1, R1 = oracle.factor(X[:, :16], 8, v)
+        assert np.array_equal(Q[:, :16], Q1) and np.array_equal(R[:16, :16], R1)
+
+
+def test_eager_step_families():
+    """The ragged step of BCGSI+ and 2S is a BCGSI+ step (TSQR passes), that of
+    1S and BCGS-PIPI+ a BCGS-PIPI+ step (Pythagorean passes): at s = n - r the
+    results equal the family's own factorization with that block size."""
+    X = synth.make_matrix_np(300, 12, 1e3, seed=8)
+    # n = 12, s = 8: one full block + a ragged block of 4; BCGSI+ with blocks
+    # (8, 4) is the same arithmetic as its loop body on block 2
+    Q, R = oracle.factor(X, 8, "bcgsi+p-2s")
+    Q1, R1 = oracle.tsqr(X[:, :8], 1)
+    Qn, Rt, Rd = oracle.eager_step(Q1, X[:, 8:], "bcgsi+", 2)
+    assert np.array_equal(Q[:, 8:], Qn) and np.array_equal(R[:8, 8:], Rt) and np.array_equal(R[8:, 8:], Rd)
+    assert oracle.EAGER_FAMILY == {"bcgsi+": "bcgsi+", "bcgsi+p-2s": "bcgsi+",
+                                   "bcgsi+p-1s": "bcgs-pipi+", "bcgs-pipi+": "bcgs-pipi+"}
+
+
+def test_mutation_lost_coupling_block_in_the_ragged_step_is_caught(monkeypatch):
+    """Planting R_{1:k,new} = 0 in the ragged step fails the LAPACK pin."""
+    real = ob.eager_step
+
+    def bad(Qk, Xn, family, block):
+        Qn, Rt, Rd = real(Qk, Xn, family, block)
+        return Qn, 0.0 * Rt, Rd
+
+    X = synth.make_matrix_np(300, 21, 1e3, seed=9)
+    Rl = _lapack_r(X)
+    _, R = oracle.factor(X, 8, "bcgsi+p-1s")
+    assert np.linalg.norm(R - Rl) / np.linalg.norm(Rl) < 1e-12
+    monkeypatch.setattr(ob, "eager_step", bad)
+    _, R = oracle.factor(X, 8, "bcgsi+p-1s")
+    assert np.linalg.norm(R - Rl) / np.linalg.norm(Rl) > 1e-3
+
+
+def test_mutation_single_pass_ragged_step_is_caught(monkeypatch):
+    """Planting a ragged step without its second (reorthogonalization) pass
+    fails the loss-of-orthogonality pin at kappa = 1e7."""
+
+    def single(Qk, Xn, family, block):
+        S = Qk.T @ Xn
+        Qn, Skk = oracle.tsqr(Xn - Qk @ S, block)
+        return Qn, S, Skk
+
+    X = synth.make_matrix_np(2000, 40, 1e7, seed=10)
+    Q, _ = oracle.factor(X, 16, "bcgsi+p-2s")
+    assert oracle.loo(Q) <= 1e-13
+    monkeypatch.setattr(ob, "eager_step", single)
+    Q, _ = oracle.factor(X, 16, "bcgsi+p-2s")
+    assert oracle.loo(Q) > 1e-11

@@ -6,7 +6,7 @@ import itertools
 
 import pytest
 
-from paper_2507_21791_gb300.serving import Request, Server, percentile
+from paper_2507_21791_gb300.serving import Request, Server, final_blocks_after, make_requests, percentile
 
 
 class FakeBackend:
@@ -19,6 +19,13 @@ class FakeBackend:
 
     def bytes_for(self, req):
         return self.bpc * req.m * req.n
+
+    # lazy = delayed normalization (BCGSI+P-2S), eager = BCGSI+
+    def final_blocks(self, req, steps):
+        return final_blocks_after("bcgsi+" if req.finalize == "eager" else "bcgsi+p-2s", steps)
+
+    def needs_finish(self, req):
+        return req.finalize != "eager"
 
     def open(self, req):
         self.open_now += 1
@@ -129,3 +136,41 @@ def test_block_size_tuner_keys_and_persistence(tmp_path):
     t2 = BlockSizeTuner(path=str(tmp_path / "t.json"))
     assert t2.pick(4096, 64) == 8  # cached, no GPU needed
     assert alg_bytes(1000, 64, 8, "bcgsi+") > alg_bytes(1000, 64, 8, "bcgsi+p-2s") > alg_bytes(1000, 64, 8, "bcgsi+p-1s")
+
+
+def test_final_blocks_follow_delayed_normalization():
+    assert [final_blocks_after("bcgsi+p-1s", k) for k in range(5)] == [0, 1, 1, 2, 3]
+    assert [final_blocks_after("bcgsi+p-2s", k) for k in range(5)] == [0, 1, 1, 2, 3]
+    assert [final_blocks_after("bcgs-pipi+", k) for k in range(5)] == [0, 1, 2, 3, 4]
+    assert [final_blocks_after("bcgsi+", k) for k in range(5)] == [0, 1, 2, 3, 4]
+
+
+def test_eager_requests_skip_the_finish_call_and_finalize_each_block_in_its_call():
+    be = FakeBackend(polls_per_call=3)
+    reqs = make(4, n=8, s=2)
+    for r in reqs[::2]:
+        r.finalize = "eager"
+    rep = Server(be, budget_bytes=1e9, clock=FakeClock()).run(reqs, duration=1.0)
+    assert rep["requests_done"] == 4 and set(rep["by_finalize"]) == {"eager", "lazy"}
+    for r in reqs:
+        finishes = [e for e in be.log if e[0] == "finish" and e[1] == r.rid]
+        assert len(finishes) == (0 if r.finalize == "eager" else 1)
+        assert r.n_final == r.q and len(r.final_latencies) == r.q
+        if r.finalize == "eager":
+            # each block is final when its own call completes
+            assert r.final_latencies == pytest.approx(r.call_latencies)
+        else:
+            # block 1 final with its own call (TSQR), blocks 2..q-1 one call later, the last at finish
+            assert len(r.call_latencies) == r.q + 1
+            assert r.final_latencies[0] == pytest.approx(r.call_latencies[0])
+            for b in range(1, r.q):
+                assert r.final_latencies[b] > r.call_latencies[b]
+
+
+def test_eager_fraction_does_not_move_arrivals():
+    meta = [(100, 8, 2)]
+    a = make_requests(50.0, 1.0, meta, seed=3, eager_frac=0.0)
+    b = make_requests(50.0, 1.0, meta, seed=3, eager_frac=0.5)
+    assert [r.arrival for r in a] == [r.arrival for r in b]
+    assert all(r.finalize == "lazy" for r in a)
+    assert 0 < sum(r.finalize == "eager" for r in b) < len(b)
