@@ -4,7 +4,8 @@
  *
  * Operation (Sec. 1): the economic QR X = Q R of a tall-skinny m x n matrix X,
  * Q^T Q = I, R upper triangular with positive diagonal, computed block column
- * by block column, X = [X_1 ... X_q], q = n / s blocks of s columns, by one of
+ * by block column, X = [X_1 ... X_q], q = ceil(n / s) blocks of s columns (the
+ * last one ragged, n mod s columns, when s does not divide n), by one of
  *   BCGS_BCGSI_PLUS       BCGSI+ (Sec. 1, Table 1: 4 synchronizations per block)
  *   BCGS_BCGSI_PLUS_P_1S  BCGSI+P-1S (Alg. 2: 1 synchronization per block)
  *   BCGS_BCGSI_PLUS_P_2S  BCGSI+P-2S (Sec. 2: Alg. 2 with TSQR as the first
@@ -86,8 +87,14 @@ BCGS_API int bcgs_version(void);
  * ------------------------------------------------------------------------- */
 
 /* Bytes of device workspace needed by a factorization (or a handle) of an
- * m x n_max matrix with block size s.  Requirements: 1 <= s <= 64, n_max <= m,
- * n_max a multiple of s, n_max <= 2048.  Writes *bytes; returns BCGS_OK or
+ * m x n_max matrix with block size s.  Requirements: 1 <= s <= 64,
+ * 1 <= n_max <= m, n_max <= 2048.  The paper takes n = q s; when s does not
+ * divide n the last block is ragged (r = n mod s columns): the full blocks are
+ * factored by the variant (BCGSI+P-1S / -2S finalize their delayed block first),
+ * then the ragged block takes one step of the variant of the same stability
+ * range that finalizes a block at once: a BCGS-PIPI+ step (Alg. 1) under
+ * BCGSI+P-1S and BCGS-PIPI+, a BCGSI+ step under BCGSI+ and BCGSI+P-2S
+ * (n < s: TSQR alone).  Writes *bytes; returns BCGS_OK or
  * BCGS_ERR_INVALID_ARG.  With FP64 storage, s <= 32 and the tensor engine
  * selected for m rows (BCGS_OPT_GRAM_ENGINE below) the size includes the digit
  * store of Q: 16 bytes per element of the m x n_max basis (rounded up to 128
@@ -146,8 +153,10 @@ BCGS_API int bcgs_qr_init(bcgs_qr_t* handle, int64_t m, int32_t n_max, int32_t s
                  int variant, int precision, void* Q, int64_t ldq, double* R,
                  int32_t ldr, void* workspace, size_t ws_bytes, void* stream);
 
-/* Ingest the next block X_j (m x s, leading dimension ldx).  Returns
- * BCGS_ERR_STATE after bcgs_qr_finish or once n_max columns were ingested. */
+/* Ingest the next block X_j (m x s, leading dimension ldx; the last block is
+ * m x (n_max mod s) when s does not divide n_max, and after it every column is
+ * final).  Returns BCGS_ERR_STATE after bcgs_qr_finish or once n_max columns
+ * were ingested. */
 BCGS_API int bcgs_qr_step(bcgs_qr_t handle, const void* X_block, int64_t ldx);
 
 /* Finalize the last block (the else-branch of Alg. 2).  Idempotent. */

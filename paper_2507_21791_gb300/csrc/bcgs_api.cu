@@ -28,12 +28,13 @@ struct Layout {
   int ldg;      // leading dimension of G, G2 (= n_max)
   int64_t ldu;  // leading dimension of U, V
   TsqrPlan tp;
+  TsqrPlan tp_last;  // TSQR of the ragged last block (n_max mod s columns), if any
 };
 
 size_t align256(size_t v) { return (v + 255) / 256 * 256; }
 
 bool valid_shape(int64_t m, int32_t n, int32_t s) {
-  return s >= 1 && s <= kMaxS && m >= n && n >= s && n % s == 0 && n <= kMaxN;
+  return s >= 1 && s <= kMaxS && n >= 1 && m >= n && n <= kMaxN;
 }
 
 // The digit store of Q pays for itself where the projections run on the tensor
@@ -77,7 +78,9 @@ void make_layout(int64_t m, int32_t n_max, int32_t s, int variant, int precision
   const bool tsqr_in = variant == BCGS_BCGSI_PLUS || variant == BCGS_BCGSI_PLUS_P_2S;
   L->V = tsqr_in ? take((size_t)L->ldu * s * esz) : off;
   tsqr_plan(m, s, &L->tp);
-  L->tsqr = take(L->tp.doubles * sizeof(double));
+  const int32_t s_last = n_max % s;
+  tsqr_plan(m, s_last > 0 ? s_last : s, &L->tp_last);
+  L->tsqr = take((L->tp.doubles > L->tp_last.doubles ? L->tp.doubles : L->tp_last.doubles) * sizeof(double));
   L->store = store;
   L->qstore = store ? take(qstore_bytes(m, n_max)) : off;
   L->fexp = store ? take((size_t)ceil_div(m, kStoreRows) * 32 * sizeof(int32_t)) : off;
@@ -132,6 +135,7 @@ struct bcgs_qr_s {
   int32_t esz;
   int32_t fp32;
   int32_t sgram;  // Grams read the digit store (the current U and X blocks are split into it)
+  int32_t flushed;  // a ragged last block was stepped: every block is final, finish does nothing
   cudaError_t last_cuda;
 
   DevStatus* st() { return reinterpret_cast<DevStatus*>(ws + L.status); }
@@ -145,8 +149,16 @@ struct bcgs_qr_s {
   unsigned long long* rowmaxQ() { return reinterpret_cast<unsigned long long*>(ws + L.rowmaxQ); }
   // Q and U carry the column maxima their writers kept
   Seg Qseg(int ncols) { return seg(Q, ldq, ncols, fp32, amaxQ()); }
-  Seg Useg() { return seg(U(), L.ldu, s, fp32, amaxU()); }
-  Seg Vseg() { return seg(V(), L.ldu, s, fp32); }
+  Seg Useg(int w = 0) { return seg(U(), L.ldu, w ? w : s, fp32, amaxU()); }
+  Seg Vseg(int w = 0) { return seg(V(), L.ldu, w ? w : s, fp32); }
+  // columns [col0, ...) of Q, and the maxima to keep when writing them
+  char* Qcol(int col0) { return Q + (size_t)col0 * ldq * esz; }
+  MaxOut Qmax_at(int col0) {
+    return MaxOut{sgram ? nullptr : amaxQ() + col0, L.store ? nullptr : rowmaxQ()};
+  }
+  bool delayed() const { return variant == BCGS_BCGSI_PLUS_P_1S || variant == BCGS_BCGSI_PLUS_P_2S; }
+  // width of block column j (1-based): s, or the ragged rest of n_max
+  int width(int j) const { return (int)((int64_t)j * s <= n_max ? s : n_max - (int64_t)(j - 1) * s); }
   // maxima to keep when writing block k of Q, or U: the column maxima feed the
   // on-the-fly Gram (not needed when the Grams read the store), the row maxima
   // of Q the on-the-fly projection (not needed with the store)
@@ -214,7 +226,8 @@ cudaError_t gram(bcgs_qr_s* h, std::initializer_list<Seg> A, std::initializer_li
 }
 
 cudaError_t project(bcgs_qr_s* h, Seg v, int c, const double* C, int ldc, const double* T,
-                    void* w, int64_t ldw, MaxOut wmax = MaxOut{nullptr, nullptr}) {
+                    void* w, int64_t ldw, MaxOut wmax = MaxOut{nullptr, nullptr}, int sb = 0) {
+  if (sb == 0) sb = h->s;
   ProjDesc d;
   memset(&d, 0, sizeof(d));
   d.q_rowmax = h->rowmaxQ();
@@ -224,22 +237,22 @@ cudaError_t project(bcgs_qr_s* h, Seg v, int c, const double* C, int ldc, const 
   d.C = C;
   d.ldc = ldc;
   d.T = T;
-  d.ldt = h->s;
+  d.ldt = sb;
   d.w = w;
   d.ldw = ldw;
   d.w_fp32 = h->fp32;
   d.m = h->m;
-  d.s = h->s;
-  if (h->L.store && use_tensor_project(d) && project_store_supported(h->s, 1)) {
+  d.s = sb;
+  if (h->L.store && use_tensor_project(d) && project_store_supported(sb, 1)) {
     StoreProjDesc p;
     memset(&p, 0, sizeof(p));
     p.qs = h->qs();
     p.c = c;
     p.B = C;
     p.ldb = ldc;
-    p.s = h->s;
+    p.s = sb;
     p.nouts = 1;
-    p.out[0] = ProjOut{reinterpret_cast<const double*>(v.p), v.ld, T, h->s, reinterpret_cast<double*>(w),
+    p.out[0] = ProjOut{reinterpret_cast<const double*>(v.p), v.ld, T, sb, reinterpret_cast<double*>(w),
                        ldw, wmax};
     p.m = h->m;
     p.block = h->j + 1;
@@ -250,21 +263,23 @@ cudaError_t project(bcgs_qr_s* h, Seg v, int c, const double* C, int ldc, const 
   return launch_project(d, h->st(), h->stream);
 }
 
-// Digits of the freshly written block column k of Q into the store.
-cudaError_t wrote_q(bcgs_qr_s* h, int k) {
+// Digits of the freshly written columns [col0, col0 + sb) of Q into the store.
+cudaError_t wrote_q_cols(bcgs_qr_s* h, int col0, int sb, int block) {
   if (!h->L.store) return cudaSuccess;
   const double* Q = reinterpret_cast<const double*>(h->Q);
-  return launch_qsplit(h->qs(), Q + (size_t)(k - 1) * h->s * h->ldq, h->ldq, Q, h->ldq, h->m, (k - 1) * h->s,
-                       h->s, h->st(), k, h->stream);
+  return launch_qsplit(h->qs(), Q + (size_t)col0 * h->ldq, h->ldq, Q, h->ldq, h->m, col0, sb, h->st(), block,
+                       h->stream);
 }
+// ... of the freshly written (full) block column k of Q.
+cudaError_t wrote_q(bcgs_qr_s* h, int k) { return wrote_q_cols(h, (k - 1) * h->s, h->s, k); }
 
 // With store Grams: digits of an m x s block (X or U) into store columns
 // [k0, k0 + s), the columns Q fills next.
-cudaError_t store_put(bcgs_qr_s* h, const void* src, int64_t ld, int k0) {
+cudaError_t store_put(bcgs_qr_s* h, const void* src, int64_t ld, int k0, int sb = 0) {
   if (!h->sgram) return cudaSuccess;
   const double* Q = reinterpret_cast<const double*>(h->Q);
-  return launch_qsplit(h->qs(), reinterpret_cast<const double*>(src), ld, Q, h->ldq, h->m, k0, h->s, h->st(),
-                       h->j + 1, h->stream);
+  return launch_qsplit(h->qs(), reinterpret_cast<const double*>(src), ld, Q, h->ldq, h->m, k0, sb ? sb : h->s,
+                       h->st(), h->j + 1, h->stream);
 }
 
 // G = A^T B: from the store (A = store columns [0, na), B = [b0, b0 + nb)) when
@@ -286,10 +301,11 @@ cudaError_t gram_cols(bcgs_qr_s* h, int na, int b0, int nb, std::initializer_lis
 
 cudaError_t tsqr(bcgs_qr_s* h, Seg a, void* q, int64_t ldq, double* R, int ldr, int block,
                  MaxOut qmax = MaxOut{nullptr, nullptr}) {
-  return launch_tsqr(h->L.tp, a, q, ldq, h->fp32, R, ldr, h->buf(h->L.tsqr), h->st(), block,
-                     h->stream, qmax);
+  // the plan of the block's width (a.ncols is s or the ragged rest)
+  const TsqrPlan& tp = a.ncols == h->s ? h->L.tp : h->L.tp_last;
+  return launch_tsqr(tp, a, q, ldq, h->fp32, R, ldr, h->buf(h->L.tsqr), h->st(), block, h->stream, qmax);
 }
-cudaError_t zero_umax(bcgs_qr_s* h) { return launch_zero_u64(h->amaxU(), h->s, h->stream); }
+cudaError_t zero_umax(bcgs_qr_s* h, int sb = 0) { return launch_zero_u64(h->amaxU(), sb ? sb : h->s, h->stream); }
 
 // Last-block branch of Alg. 2 (shared by BCGSI+P-1S and -2S):
 // [Y_{1:q-1,q}; Omega_q] = [Q_{q-1} U_q]^T U_q, Y_qq, R column block q, Q_q.
@@ -450,8 +466,82 @@ int step_p(bcgs_qr_s* h, const void* X, int64_t ldx) {
   return BCGS_OK;
 }
 
+// One BCGSI+ step (two projections, each followed by TSQR) for the block X
+// (sb columns, block index j) against Q's first c final columns:
+//   S = Q^T X;  [U, S_jj] = TSQR(X - Q S);  Y = Q^T U;  [Q_j, Y_jj] = TSQR(U - Q Y)
+//   R_{1:c,j} = S + Y S_jj;  R_jj = Y_jj S_jj
+int step_bcgsi(bcgs_qr_s* h, const void* X, int64_t ldx, int j, int c, int sb) {
+  const Seg Xs = seg(X, ldx, sb, h->fp32);
+  double* G = h->buf(h->L.G);
+  double* G2 = h->buf(h->L.G2);
+  const int ldg = h->L.ldg;
+  TRY(store_put(h, X, ldx, c, sb));
+  TRY(gram_cols(h, c, c, sb, {h->Qseg(c)}, {Xs}, G));
+  TRY(project(h, Xs, c, G, ldg, nullptr, h->V(), h->L.ldu, MaxOut{nullptr, nullptr}, sb));
+  TRY(zero_umax(h, sb));
+  TRY(tsqr(h, h->Vseg(sb), h->U(), h->L.ldu, h->buf(h->L.Rt1), sb, j, h->Umax()));
+  TRY(store_put(h, h->U(), h->L.ldu, c, sb));
+  TRY(gram_cols(h, c, c, sb, {h->Qseg(c)}, {h->Useg(sb)}, G2));
+  TRY(project(h, h->Useg(sb), c, G2, ldg, nullptr, h->V(), h->L.ldu, MaxOut{nullptr, nullptr}, sb));
+  TRY(tsqr(h, h->Vseg(sb), h->Qcol(c), h->ldq, h->buf(h->L.Rt2), sb, j, h->Qmax_at(c)));
+  TRY(wrote_q_cols(h, c, sb, j));
+  TRY(launch_r_assemble(c, sb, G, ldg, G2, ldg, h->buf(h->L.Rt1), h->buf(h->L.Rt2), h->R, h->ldr, c, h->st(),
+                        h->stream));
+  return BCGS_OK;
+}
+
+// One BCGS-PIPI+ step (Alg. 1) for the block X (sb columns, block index j)
+// against Q's first c final columns:
+//   [S; T] = [Q X]^T X, S_jj = chol(T - S^T S), U = (X - Q S) S_jj^{-1}
+//   [Y; Omega] = [Q U]^T U, Y_jj = chol(Omega - Y^T Y), Q_j = (U - Q Y) Y_jj^{-1}
+//   R_{1:c,j} = S + Y S_jj;  R_jj = Y_jj S_jj
+int step_pipi(bcgs_qr_s* h, const void* X, int64_t ldx, int j, int c, int sb) {
+  const Seg Xs = seg(X, ldx, sb, h->fp32);
+  double* G = h->buf(h->L.G);
+  double* G2 = h->buf(h->L.G2);
+  const int ldg = h->L.ldg;
+  double* Skk = h->buf(h->L.Rt1);
+  double* Ykk = h->buf(h->L.Rt2);
+  TRY(store_put(h, X, ldx, c, sb));
+  TRY(gram_cols(h, c + sb, c, sb, {h->Qseg(c), Xs}, {Xs}, G));
+  TRY(launch_tail_pchol(c, sb, G, ldg, nullptr, 0, Skk, j, h->st(), h->stream));
+  TRY(zero_umax(h, sb));
+  TRY(project(h, Xs, c, G, ldg, Skk, h->U(), h->L.ldu, h->Umax(), sb));
+  TRY(store_put(h, h->U(), h->L.ldu, c, sb));
+  TRY(gram_cols(h, c + sb, c, sb, {h->Qseg(c), h->Useg(sb)}, {h->Useg(sb)}, G2));
+  TRY(launch_tail_pchol(c, sb, G2, ldg, nullptr, 0, Ykk, j, h->st(), h->stream));
+  TRY(project(h, h->Useg(sb), c, G2, ldg, Ykk, h->Qcol(c), h->ldq, h->Qmax_at(c), sb));
+  TRY(wrote_q_cols(h, c, sb, j));
+  TRY(launch_r_assemble(c, sb, G, ldg, G2, ldg, Skk, Ykk, h->R, h->ldr, c, h->st(), h->stream));
+  return BCGS_OK;
+}
+
+// A ragged last block (sb = n_max mod s columns; the paper assumes n = q s):
+// the delayed block of BCGSI+P-1S / -2S is finalized first (their last-block
+// branch), then the ragged block takes one step of the variant of the same
+// stability range whose step finalizes it at once: BCGS-PIPI+ for 1S and
+// PIPI+, BCGSI+ for BCGSI+ and 2S.  A first block that is already ragged
+// (n_max < s) is TSQR alone.
+int step_ragged(bcgs_qr_s* h, const void* X, int64_t ldx, int sb) {
+  const int j = h->j + 1, c = h->j * h->s;
+  if (j == 1) {
+    TRY(tsqr(h, seg(X, ldx, sb, h->fp32), h->Q, h->ldq, h->R, h->ldr, 1, h->Qmax_at(0)));
+    TRY(wrote_q_cols(h, 0, sb, 1));
+    return BCGS_OK;
+  }
+  if (h->delayed() && h->j >= 2) {
+    const int rc = finish_p(h);
+    if (rc != BCGS_OK) return rc;
+  }
+  h->flushed = 1;  // after the ragged step every block is final: nothing left for finish
+  if (h->variant == BCGS_BCGSI_PLUS_P_1S || h->variant == BCGS_BCGS_PIPI_PLUS)
+    return step_pipi(h, X, ldx, j, c, sb);
+  return step_bcgsi(h, X, ldx, j, c, sb);
+}
+
 int do_step(bcgs_qr_s* h, const void* X, int64_t ldx) {
   const int s = h->s, j = h->j + 1;
+  if (h->width(j) < s) return step_ragged(h, X, ldx, h->width(j));
   const Seg Xs = seg(X, ldx, s, h->fp32);
   double* G = h->buf(h->L.G);
   const int ldg = h->L.ldg;
@@ -462,25 +552,8 @@ int do_step(bcgs_qr_s* h, const void* X, int64_t ldx) {
     return BCGS_OK;
   }
   switch (h->variant) {
-    case BCGS_BCGSI_PLUS: {
-      const int k = j - 1, c = k * s;
-      double* G2 = h->buf(h->L.G2);
-      // S = Q_k^T X_{k+1};  [U, S_kk] = TSQR(X_{k+1} - Q_k S)
-      TRY(store_put(h, X, ldx, c));
-      TRY(gram_cols(h, c, c, s, {h->Qseg(c)}, {Xs}, G));
-      TRY(project(h, Xs, c, G, ldg, nullptr, h->V(), h->L.ldu));
-      TRY(zero_umax(h));
-      TRY(tsqr(h, h->Vseg(), h->U(), h->L.ldu, h->buf(h->L.Rt1), s, j, h->Umax()));
-      // Y = Q_k^T U;  [Q_{k+1}, Y_kk] = TSQR(U - Q_k Y)
-      TRY(store_put(h, h->U(), h->L.ldu, c));
-      TRY(gram_cols(h, c, c, s, {h->Qseg(c)}, {h->Useg()}, G2));
-      TRY(project(h, h->Useg(), c, G2, ldg, nullptr, h->V(), h->L.ldu));
-      TRY(tsqr(h, h->Vseg(), h->Qblk(j), h->ldq, h->buf(h->L.Rt2), s, j, h->Qmax(j)));
-      TRY(wrote_q(h, j));
-      TRY(launch_r_assemble(c, s, G, ldg, G2, ldg, h->buf(h->L.Rt1), h->buf(h->L.Rt2), h->R,
-                            h->ldr, c, h->st(), h->stream));
-      return BCGS_OK;
-    }
+    case BCGS_BCGSI_PLUS:
+      return step_bcgsi(h, X, ldx, j, (j - 1) * s, s);
     case BCGS_BCGSI_PLUS_P_1S:
       if (j == 2) {
         // [S_12; T_2] = [Q_1 X_2]^T X_2, S_22 = chol(T_2 - S_12^T S_12), U_2
@@ -508,29 +581,8 @@ int do_step(bcgs_qr_s* h, const void* X, int64_t ldx) {
         return BCGS_OK;
       }
       return step_p(h, X, ldx);
-    case BCGS_BCGS_PIPI_PLUS: {
-      const int k = j - 1, c = k * s;
-      double* G2 = h->buf(h->L.G2);
-      double* Skk = h->buf(h->L.Rt1);
-      double* Ykk = h->buf(h->L.Rt2);
-      // [S; T] = [Q_k X_{k+1}]^T X_{k+1}, S_kk = chol(T - S^T S),
-      // U = (X_{k+1} - Q_k S) S_kk^{-1}
-      TRY(store_put(h, X, ldx, c));
-      TRY(gram_cols(h, c + s, c, s, {h->Qseg(c), Xs}, {Xs}, G));
-      TRY(launch_tail_pchol(c, s, G, ldg, nullptr, 0, Skk, j, h->st(), h->stream));
-      TRY(zero_umax(h));
-      TRY(project(h, Xs, c, G, ldg, Skk, h->U(), h->L.ldu, h->Umax()));
-      // [Y; Omega] = [Q_k U]^T U, Y_kk = chol(Omega - Y^T Y),
-      // Q_{k+1} = (U - Q_k Y) Y_kk^{-1}
-      TRY(store_put(h, h->U(), h->L.ldu, c));
-      TRY(gram_cols(h, c + s, c, s, {h->Qseg(c), h->Useg()}, {h->Useg()}, G2));
-      TRY(launch_tail_pchol(c, s, G2, ldg, nullptr, 0, Ykk, j, h->st(), h->stream));
-      TRY(project(h, h->Useg(), c, G2, ldg, Ykk, h->Qblk(j), h->ldq, h->Qmax(j)));
-      TRY(wrote_q(h, j));
-      // R_{1:k,k+1} = S + Y S_kk, R_{k+1,k+1} = Y_kk S_kk
-      TRY(launch_r_assemble(c, s, G, ldg, G2, ldg, Skk, Ykk, h->R, h->ldr, c, h->st(), h->stream));
-      return BCGS_OK;
-    }
+    case BCGS_BCGS_PIPI_PLUS:
+      return step_pipi(h, X, ldx, j, (j - 1) * s, s);
   }
   return BCGS_ERR_INVALID_ARG;
 }
@@ -576,7 +628,7 @@ int init_handle(bcgs_qr_s* h, int64_t m, int32_t n_max, int32_t s, int variant, 
 }
 
 int step_handle(bcgs_qr_s* h, const void* X, int64_t ldx) {
-  if (h->finished || (h->j + 1) * h->s > h->n_max) return BCGS_ERR_STATE;
+  if (h->finished || (int64_t)h->j * h->s >= h->n_max) return BCGS_ERR_STATE;
   if (X == nullptr || ldx < h->m) return BCGS_ERR_INVALID_ARG;
   const int rc = do_step(h, X, ldx);
   if (rc != BCGS_OK) return rc;
@@ -587,7 +639,7 @@ int step_handle(bcgs_qr_s* h, const void* X, int64_t ldx) {
 int finish_handle(bcgs_qr_s* h) {
   if (h->finished) return BCGS_OK;
   if (h->j == 0) return BCGS_ERR_STATE;
-  if ((h->variant == BCGS_BCGSI_PLUS_P_1S || h->variant == BCGS_BCGSI_PLUS_P_2S) && h->j >= 2) {
+  if (h->delayed() && h->j >= 2 && !h->flushed) {
     const int rc = finish_p(h);
     if (rc != BCGS_OK) return rc;
   }
@@ -728,7 +780,8 @@ int bcgs_qr_factor(int64_t m, int32_t n, int32_t s, int variant, int precision, 
   if (rc != BCGS_OK) return rc;
   const size_t esz = precision == BCGS_FP32_STORAGE ? 4 : 8;
   const char* Xc = reinterpret_cast<const char*>(X);
-  for (int k = 0; k < n / s; ++k) {
+  const int q = (n + s - 1) / s;  // the last block may be ragged
+  for (int k = 0; k < q; ++k) {
     rc = step_handle(h, Xc + (size_t)k * s * ldx * esz, ldx);
     if (rc != BCGS_OK) return rc;
   }
@@ -749,22 +802,24 @@ int bcgs_qr_factor_host(int64_t m, int32_t n, int32_t s, int variant, int precis
   rc = copy_streams(&cs);
   if (rc != BCGS_OK) return rc;
   const size_t esz = precision == BCGS_FP32_STORAGE ? 4 : 8;
-  const int q = n / s;
+  const int q = (n + s - 1) / s;  // the last block may be ragged
   const cudaStream_t main = h->stream;
   const char* Xh = reinterpret_cast<const char*>(X_host);
   char* Qh = reinterpret_cast<char*>(Q_host);
   char* Xdc = reinterpret_cast<char*>(Xd);
   const char* Qdc = reinterpret_cast<const char*>(Qd);
-  // block columns [k0, k1) of X to the device, of Q to the host
+  // block columns [k0, k1) of X to the device, of Q to the host (the last one may be ragged)
+  auto ncols = [&](int k0, int k1) {
+    const int64_t e = (int64_t)k1 * s < n ? (int64_t)k1 * s : n;
+    return (size_t)(e - (int64_t)k0 * s);
+  };
   auto h2d = [&](int k0, int k1) {
     return cudaMemcpy2DAsync(Xdc + (size_t)k0 * s * ldx * esz, (size_t)ldx * esz, Xh + (size_t)k0 * s * ldxh * esz,
-                             (size_t)ldxh * esz, (size_t)m * esz, (size_t)(k1 - k0) * s, cudaMemcpyHostToDevice,
-                             cs->h2d);
+                             (size_t)ldxh * esz, (size_t)m * esz, ncols(k0, k1), cudaMemcpyHostToDevice, cs->h2d);
   };
   auto d2h = [&](int k0, int k1) {
     return cudaMemcpy2DAsync(Qh + (size_t)k0 * s * ldqh * esz, (size_t)ldqh * esz, Qdc + (size_t)k0 * s * ldq * esz,
-                             (size_t)ldq * esz, (size_t)m * esz, (size_t)(k1 - k0) * s, cudaMemcpyDeviceToHost,
-                             cs->d2h);
+                             (size_t)ldq * esz, (size_t)m * esz, ncols(k0, k1), cudaMemcpyDeviceToHost, cs->d2h);
   };
   // the copies start after what `stream` already holds (Xd, Qd may still be in use)
   TRY(cudaEventRecord(cs->start, main));
@@ -783,7 +838,8 @@ int bcgs_qr_factor_host(int64_t m, int32_t n, int32_t s, int variant, int precis
       TRY(cudaEventRecord(cs->in, cs->h2d));
       TRY(cudaStreamWaitEvent(main, cs->in, 0));
     }
-    const int final_blocks = delayed ? (k > 1 ? k : 1) : k + 1;
+    // a ragged last step finalizes every block (the delayed one first)
+    const int final_blocks = (delayed && !h->flushed) ? (k > 1 ? k : 1) : k + 1;
     if (final_blocks > sent) {
       TRY(cudaEventRecord(cs->out, main));
       TRY(cudaStreamWaitEvent(cs->d2h, cs->out, 0));
@@ -845,10 +901,10 @@ int bcgs_qr_sync(bcgs_qr_t h, int32_t* n_final, int32_t* fail_block) {
   int rc = read_status(h->ws + h->L.status, h->stream, &code, &block);
   if (rc != BCGS_OK) return rc;
   if (n_final) {
-    int fin;
-    if (h->finished || h->variant == BCGS_BCGSI_PLUS || h->variant == BCGS_BCGS_PIPI_PLUS) fin = h->j;
-    else fin = h->j <= 1 ? h->j : h->j - 1;
-    *n_final = code ? 0 : fin * h->s;
+    int64_t fin;
+    if (h->finished || !h->delayed() || h->flushed) fin = (int64_t)h->j * h->s;
+    else fin = (int64_t)(h->j <= 1 ? h->j : h->j - 1) * h->s;
+    *n_final = code ? 0 : (int32_t)(fin < h->n_max ? fin : h->n_max);
   }
   if (fail_block) *fail_block = code ? block : 0;
   return code;

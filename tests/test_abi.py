@@ -74,7 +74,7 @@ def test_workspace_size_queries():
     assert fp32 < small   # no store with FP32 storage
 
 
-@pytest.mark.parametrize("m,n,s", [(100, 30, 8), (100, 16, 0), (4, 8, 8), (100, 64, 65),
+@pytest.mark.parametrize("m,n,s", [(100, 0, 8), (100, 16, 0), (4, 8, 8), (100, 64, 65),
                                    (100, 4096, 8)])
 def test_invalid_shapes_rejected_without_a_gpu(m, n, s):
     ensure_library()
@@ -110,3 +110,16 @@ def test_bad_enums_and_null_pointers_rejected():
     assert lib.bcgs_qr_factor(100, 16, 8, 1, 0, 8, 100, 16, 100, 32, 16, 257, 1 << 20, None) == 5
     # too small workspace
     assert lib.bcgs_qr_factor(100, 16, 8, 1, 0, 8, 100, 16, 100, 32, 16, 256, 1024, None) == 5
+
+
+@pytest.mark.parametrize("m,n,s", [(100, 30, 8), (100, 5, 8), (1000, 17, 16)])
+def test_ragged_shapes_accepted(m, n, s):
+    """n need not be a multiple of s: the last block is ragged (n mod s columns)."""
+    ensure_library()
+    from paper_2507_21791_gb300 import bcgs
+
+    lib = bcgs.load_library()
+    out = ctypes.c_size_t(0)
+    for variant in range(4):
+        assert lib.bcgs_qr_workspace_size(m, n, s, variant, 0, ctypes.byref(out)) == 0
+        assert out.value > 0
