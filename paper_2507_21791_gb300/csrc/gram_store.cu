@@ -85,7 +85,9 @@ __global__ void __launch_bounds__(kThreads, 1) gram_store_kernel(GramStoreDesc d
   uint8_t* Aring = base;
   uint8_t* Bbuf = Aring + S * kDigBytes;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int ch = blockIdx.x, G = blockIdx.y;
+  // the column tiles of one chunk are adjacent in launch order, so they run at
+  // the same time and the second read of the chunk's B digits hits L2
+  const int G = blockIdx.x, ch = blockIdx.y;
   const QStore qs = d.qs;
   const int64_t b_first = (int64_t)ch * d.bpc;
   const int nbl = (int)min((int64_t)d.bpc, qs.nblk - b_first);
@@ -325,7 +327,7 @@ cudaError_t launch_gs(const GramStoreDesc& d, double* partial, DevStatus* st, cu
   const size_t smem = GSCfg<NBT>::kSmem;
   cudaError_t e = ensure_dyn_smem(gram_store_kernel<NBT>, smem);
   if (e != cudaSuccess) return e;
-  const dim3 grid((unsigned)d.nchunks, (unsigned)ceil_div(d.na, kStoreCols));
+  const dim3 grid((unsigned)ceil_div(d.na, kStoreCols), (unsigned)d.nchunks);
   gram_store_kernel<NBT><<<grid, kThreads, smem, stream>>>(d, partial, st);
   return cudaSuccess;
 }
