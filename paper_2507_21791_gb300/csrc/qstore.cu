@@ -193,6 +193,7 @@ constexpr int kCtl = 0;                          // warp roles
 constexpr int kSplit0 = 1, kSplitWarps = 3;
 constexpr int kRead0 = 4, kReadWarps = 8;
 constexpr int kThreads = 32 * (kRead0 + kReadWarps);
+constexpr int kRegsLow = 104, kRegsHigh = 192;   // registers per thread after the split
 
 // Output o occupies tile columns [o SMAX, o SMAX + s) (B column o s + jj); with
 // two outputs each read-back thread holds one output of its row, so the
@@ -358,6 +359,13 @@ __global__ void __launch_bounds__(kThreads, 1) proj_store_kernel(StoreProjDesc d
     for (int j = tid; j < s; j += kThreads) s_inv[j] = 1.0 / s_T[j * 32 + j];
   __syncthreads();
   const uint32_t tmem = tmem_base_s;
+
+  // Warpgroup 0 (control + splitters) hands registers to the two read-back
+  // warpgroups: launched 12 warps x 168 = 64512, then 4 warps x kRegsLow +
+  // 8 warps x kRegsHigh = 62464 <= 64512.
+  static_assert(4 * 32 * kRegsLow + 8 * 32 * kRegsHigh <= kThreads * 168, "register split");
+  if (warp < kRead0) setmaxnreg_dec<kRegsLow>();
+  else setmaxnreg_inc<kRegsHigh>();
 
   if (warp == kCtl) {
     // ------------------------------------------------ copies and MMAs

@@ -330,6 +330,18 @@ __device__ __forceinline__ double fixed_to_double(long long hi, long long lo, in
   return r;
 }
 
+// Register reallocation between warpgroups (every warp of a warpgroup executes
+// the same instruction): dec gives registers back to the CTA's pool, inc waits
+// until the pool holds enough.  The pool is what the CTA was launched with.
+template <int N>
+__device__ __forceinline__ void setmaxnreg_dec() {
+  asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;\n" ::"n"(N));
+}
+template <int N>
+__device__ __forceinline__ void setmaxnreg_inc() {
+  asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;\n" ::"n"(N));
+}
+
 // Tensor-memory allocation of NCOLS (power of two, 32..512) columns by one warp.
 template <int NCOLS>
 __device__ __forceinline__ void tmem_alloc(uint32_t* dst_smem) {
