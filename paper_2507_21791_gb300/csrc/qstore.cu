@@ -536,26 +536,32 @@ __global__ void __launch_bounds__(kThreads, 1) proj_store_kernel(StoreProjDesc d
           tc_after_sync();
           const uint32_t addr =
               tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)((gg & 1) * C::kAcc + my_j0);
+          // batch b = (column octet b / 2, levels 4 (b % 2) .. + 3); batch b + 1 is in flight
+          // while batch b is folded (tcgen05.wait::ld waits for every load issued before it)
+          constexpr int kBatches = kHalf / 8 * 2;
+          uint32_t r[2][4][8];
+          auto issue = [&](int bt, uint32_t (&dst)[4][8]) {
+            const int g8 = (bt >> 1) * 8, hf = bt & 1;
 #pragma unroll
-          for (int g8 = 0; g8 < kHalf; g8 += 8) {
+            for (int l = 0; l < 4; ++l) tmem_ld8_nowait(addr + (uint32_t)((4 * hf + l) * NBT + g8), dst[l]);
+          };
+          issue(0, r[0]);
 #pragma unroll
-            for (int hf = 0; hf < 2; ++hf) {
-              uint32_t r[4][8];
+          for (int bt = 0; bt < kBatches; ++bt) {
+            tmem_wait_ld();
+            if (bt + 1 < kBatches) issue(bt + 1, r[(bt + 1) & 1]);
+            const int g8 = (bt >> 1) * 8, hf = bt & 1;
+            const uint32_t(&rb)[4][8] = r[bt & 1];
 #pragma unroll
-              for (int l = 0; l < 4; ++l) tmem_ld8_nowait(addr + (uint32_t)((4 * hf + l) * NBT + g8), r[l]);
-              tmem_wait_ld();
-#pragma unroll
-              for (int j = 0; j < 8; ++j) {
-                const int32_t L0 = __float2int_rn(__uint_as_float(r[0][j]));
-                const int32_t L1 = __float2int_rn(__uint_as_float(r[1][j]));
-                const int32_t L2 = __float2int_rn(__uint_as_float(r[2][j]));
-                const int32_t L3 = __float2int_rn(__uint_as_float(r[3][j]));
-                if (hf == 0)
-                  hi[g8 + j] += ((long long)((L0 << 8) + L1) << 16) + (long long)((L2 << 8) + L3);
-                else
-                  lo[g8 + j] +=
-                      ((long long)L0 << 24) + ((long long)L1 << 16) + ((long long)L2 << 8) + (long long)L3;
-              }
+            for (int j = 0; j < 8; ++j) {
+              const int32_t L0 = __float2int_rn(__uint_as_float(rb[0][j]));
+              const int32_t L1 = __float2int_rn(__uint_as_float(rb[1][j]));
+              const int32_t L2 = __float2int_rn(__uint_as_float(rb[2][j]));
+              const int32_t L3 = __float2int_rn(__uint_as_float(rb[3][j]));
+              if (hf == 0)
+                hi[g8 + j] += ((long long)((L0 << 8) + L1) << 16) + (long long)((L2 << 8) + L3);
+              else
+                lo[g8 + j] += ((long long)L0 << 24) + ((long long)L1 << 16) + ((long long)L2 << 8) + (long long)L3;
             }
           }
           tc_before_sync();
