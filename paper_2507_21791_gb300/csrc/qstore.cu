@@ -532,42 +532,54 @@ __global__ void __launch_bounds__(kThreads, 1) proj_store_kernel(StoreProjDesc d
       for (int grp = 0; grp < ngrp; ++grp) {
         const int gg = bi * ngrp + grp;
         const bool ok = __all_sync(0xffffffffu, wait_or_abort(&accdone[gg & 1], (gg >> 1) & 1, &s_abort));
-        if (ok && !s_abort) {
+        const bool go = __all_sync(0xffffffffu, ok && !s_abort);
+        if (go) {
           tc_after_sync();
           const uint32_t addr =
               tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)((gg & 1) * C::kAcc + my_j0);
-          // batch b = (column octet b / 2, levels 4 (b % 2) .. + 3); batch b + 1 is in flight
-          // while batch b is folded (tcgen05.wait::ld waits for every load issued before it)
-          constexpr int kBatches = kHalf / 8 * 2;
-          uint32_t r[2][4][8];
-          auto issue = [&](int bt, uint32_t (&dst)[4][8]) {
-            const int g8 = (bt >> 1) * 8, hf = bt & 1;
+          // Levels 4..7 of every column octet stay raw in registers; levels 0..3 are
+          // folded into hi octet by octet.  Once every load has landed the accumulator
+          // set goes back to the MMAs, and levels 4..7 are folded into lo after that.
+          constexpr int kOct = kHalf / 8;
+          uint32_t rk[kOct][4][8], ra[4][8];
 #pragma unroll
-            for (int l = 0; l < 4; ++l) tmem_ld8_nowait(addr + (uint32_t)((4 * hf + l) * NBT + g8), dst[l]);
-          };
-          issue(0, r[0]);
+          for (int oc = 0; oc < kOct; ++oc)
 #pragma unroll
-          for (int bt = 0; bt < kBatches; ++bt) {
+            for (int l = 0; l < 4; ++l) tmem_ld8_nowait(addr + (uint32_t)((4 + l) * NBT + 8 * oc), rk[oc][l]);
+#pragma unroll
+          for (int oc = 0; oc < kOct; ++oc) {
+#pragma unroll
+            for (int l = 0; l < 4; ++l) tmem_ld8_nowait(addr + (uint32_t)(l * NBT + 8 * oc), ra[l]);
             tmem_wait_ld();
-            if (bt + 1 < kBatches) issue(bt + 1, r[(bt + 1) & 1]);
-            const int g8 = (bt >> 1) * 8, hf = bt & 1;
-            const uint32_t(&rb)[4][8] = r[bt & 1];
+            // levels 0..3 into hi (weights 2^24, 2^16, 2^8, 1 above 2^32):
+            // |L0 2^8 + L1| < 2^30 and |L2 2^8 + L3| < 2^31 fit int32
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
-              const int32_t L0 = __float2int_rn(__uint_as_float(rb[0][j]));
-              const int32_t L1 = __float2int_rn(__uint_as_float(rb[1][j]));
-              const int32_t L2 = __float2int_rn(__uint_as_float(rb[2][j]));
-              const int32_t L3 = __float2int_rn(__uint_as_float(rb[3][j]));
-              if (hf == 0)
-                hi[g8 + j] += ((long long)((L0 << 8) + L1) << 16) + (long long)((L2 << 8) + L3);
-              else
-                lo[g8 + j] += ((long long)L0 << 24) + ((long long)L1 << 16) + ((long long)L2 << 8) + (long long)L3;
+              const int32_t L0 = __float2int_rn(__uint_as_float(ra[0][j]));
+              const int32_t L1 = __float2int_rn(__uint_as_float(ra[1][j]));
+              const int32_t L2 = __float2int_rn(__uint_as_float(ra[2][j]));
+              const int32_t L3 = __float2int_rn(__uint_as_float(ra[3][j]));
+              hi[8 * oc + j] += ((long long)((L0 << 8) + L1) << 16) + (long long)((L2 << 8) + L3);
             }
           }
           tc_before_sync();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&accfree[gg & 1]);
+#pragma unroll
+          for (int oc = 0; oc < kOct; ++oc)
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+              const int32_t L4 = __float2int_rn(__uint_as_float(rk[oc][0][j]));
+              const int32_t L5 = __float2int_rn(__uint_as_float(rk[oc][1][j]));
+              const int32_t L6 = __float2int_rn(__uint_as_float(rk[oc][2][j]));
+              const int32_t L7 = __float2int_rn(__uint_as_float(rk[oc][3][j]));
+              lo[8 * oc + j] +=
+                  ((long long)L4 << 24) + ((long long)L5 << 16) + ((long long)L6 << 8) + (long long)L7;
+            }
+        } else {
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&accfree[gg & 1]);
         }
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&accfree[gg & 1]);
       }
       const bool fok = __all_sync(0xffffffffu, wait_or_abort(&fready[bi & 1], (bi >> 1) & 1, &s_abort));
       const int* sF = s_F[bi & 1];
