@@ -10,7 +10,8 @@ the oracle computes one by one:
     dotted there): X^T X = R^T R up to the backward error;
   * sampled rows of Q against X_i R^{-1} by the oracle's triangular solve;
   * at kappa = 1e10 the Pythagorean variants report a breakdown (Table 1) and
-    BCGSI+ / BCGSI+P-2S keep the gates.
+    BCGSI+ / BCGSI+P-2S keep the gates;
+and the FP32-storage form at its full size (m = 2^24, n = 128, s = 32).
 """
 import math
 
@@ -111,3 +112,36 @@ def test_full_size_row_scaled(cuda, buffers, variant):
     assert res <= 1e-13 and loo <= 1e-12, (res, loo)
     sampled_checks(torch, X, Q, R, seed=77)
     del X
+
+
+@pytest.mark.parametrize("kappa", [1e2, 1e4, 1e6])
+def test_full_size_fp32_storage(cuda, kappa):
+    """The precision form at its full size (m = 2^24, n = 128, s = 32, BCGSI+P-1S,
+    X and Q in FP32): LOO <= 1e-6 and the residual against the FP64 X <= 1e-6 for
+    kappa <= 1e4.  At kappa = 1e6, O(u_32) kappa^2 >> 1 (Table 1 read with the
+    storage unit roundoff): no loss-of-orthogonality bound holds; the Pythagorean
+    Cholesky either reports NOT_SPD or completes with the residual kept."""
+    import torch
+
+    m, n, s = 2 ** 24, 128, 32
+    X64 = synth.make_matrix_torch(m, n, kappa, seed=1200 + int(math.log10(kappa)))
+    X = X64.float()
+    Q = cuda.empty_colmajor(m, n, torch.float32)
+    R = cuda.empty_colmajor(n, n, torch.float64)
+    ws = torch.empty(cuda.workspace_size(m, n, s, "bcgsi+p-1s", "fp32"), dtype=torch.uint8, device="cuda")
+    cuda.factor_async(X, s, "bcgsi+p-1s", "fp32", Q, R, ws)
+    code, blk = cuda.factor_status(ws)
+    if kappa >= 1e6 and code != 0:
+        assert cuda.STATUS[code] == "not_spd" and blk >= 2
+        return
+    assert code == 0
+    Qd = Q.double()
+    eye = torch.eye(n, dtype=torch.float64, device="cuda")
+    loo = float(torch.linalg.matrix_norm(eye - Qd.T @ Qd, ord=2))
+    D = X64 - Qd @ R
+    res = math.sqrt(float((D * D).sum()) / float((X64 * X64).sum()))
+    assert res <= 1e-6, (loo, res)
+    if kappa <= 1e4:
+        assert loo <= 1e-6, (loo, res)
+    Rh = R.cpu().numpy()
+    assert np.array_equal(np.tril(Rh, -1), np.zeros_like(Rh)) and np.all(np.diag(Rh) > 0)
