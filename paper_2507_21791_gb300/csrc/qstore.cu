@@ -695,7 +695,7 @@ __global__ void __launch_bounds__(kThreads, 1) proj_store_kernel(StoreProjDesc d
 
 int g_sm_count = 0;
 
-// cuTensorMapEncodeTiled from the driver, looked up once through the runtime
+// cuTensorMapEncodeTiled from the CUDA driver, looked up once through the runtime
 // (no link against libcuda); null when the driver does not provide it.
 PFN_cuTensorMapEncodeTiled_v12000 encode_tiled() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
