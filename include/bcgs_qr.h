@@ -132,6 +132,17 @@ BCGS_API int bcgs_qr_factor_host(int64_t m, int32_t n, int32_t s, int variant, i
                    int32_t ldrh, void* Xd, int64_t ldx, void* Qd, int64_t ldq, double* Rd,
                    int32_t ldr, void* workspace, size_t ws_bytes, void* stream);
 
+/* Self-test of the timeout path, with no fault involved: one bounded device
+ * wait on a barrier that nothing completes gives up after `cycles` SM clock
+ * cycles (1 .. 2e9, about one second at most) and records BCGS_ERR_TIMEOUT in
+ * the status word at the start of `workspace` (device memory, at least 256
+ * bytes, 256-byte aligned), as the library's kernels do when one of their
+ * bounded waits runs out.  The status is reset first; read it with
+ * bcgs_qr_factor_status.  The context stays usable.
+ * Returns BCGS_ERR_INVALID_ARG for a null or short workspace or cycles out of
+ * range, BCGS_ERR_WORKSPACE for a misaligned one. */
+BCGS_API int bcgs_wait_selftest(void* workspace, size_t ws_bytes, int64_t cycles, void* stream);
+
 /* Synchronize `stream`, then return the device status word of the last
  * factorization that used `workspace`; *fail_block (may be NULL) gets the
  * 1-based block column at which it failed, 0 on success. */

@@ -42,6 +42,7 @@ SIGNATURES = [
     ("bcgs_qr_factor_host", ctypes.c_int, [_i64, _i32, _i32, ctypes.c_int, ctypes.c_int, _vp, _i64, _vp,
                                            _i64, _vp, _i32, _vp, _i64, _vp, _i64, _vp, _i32, _vp, _sz, _vp]),
     ("bcgs_qr_factor_status", ctypes.c_int, [_vp, _vp, _pi32]),
+    ("bcgs_wait_selftest", ctypes.c_int, [_vp, _sz, _i64, _vp]),
     ("bcgs_qr_init", ctypes.c_int, [ctypes.POINTER(_vp), _i64, _i32, _i32, ctypes.c_int, ctypes.c_int,
                                     _vp, _i64, _vp, _i32, _vp, _sz, _vp]),
     ("bcgs_qr_step", ctypes.c_int, [_vp, _vp, _i64]),

@@ -859,6 +859,16 @@ int bcgs_qr_factor_host(int64_t m, int32_t n, int32_t s, int variant, int precis
   return BCGS_OK;
 }
 
+int bcgs_wait_selftest(void* workspace, size_t ws_bytes, int64_t cycles, void* stream) {
+  if (workspace == nullptr || ws_bytes < 256 || cycles < 1 || cycles > 2000000000LL) return BCGS_ERR_INVALID_ARG;
+  if (((uintptr_t)workspace) % 256 != 0) return BCGS_ERR_WORKSPACE;
+  DevStatus* st = reinterpret_cast<DevStatus*>(workspace);
+  const cudaStream_t sm = reinterpret_cast<cudaStream_t>(stream);
+  if (launch_reset_status(st, sm) != cudaSuccess) return BCGS_ERR_CUDA;
+  if (launch_wait_selftest(st, (long long)cycles, sm) != cudaSuccess) return BCGS_ERR_CUDA;
+  return BCGS_OK;
+}
+
 int bcgs_qr_factor_status(const void* workspace, void* stream, int32_t* fail_block) {
   if (workspace == nullptr) return BCGS_ERR_INVALID_ARG;
   int32_t code = 0, block = 0;

@@ -332,7 +332,23 @@ cudaError_t launch_gs(const GramStoreDesc& d, double* partial, DevStatus* st, cu
   return cudaSuccess;
 }
 
+// The timeout path without a fault: the barrier expects one arrival that never
+// comes, so the bounded wait gives up after `cycles` and the kernel records
+// BCGS_ERR_TIMEOUT, as every bounded wait of the library does.
+__global__ void wait_selftest_kernel(DevStatus* st, long long cycles) {
+  __shared__ __align__(8) uint64_t mbar;
+  if (threadIdx.x == 0) mbar_init(&mbar);
+  __syncthreads();
+  if (threadIdx.x == 0 && !mbar_wait_limit(&mbar, 0, cycles)) set_failure(st, BCGS_ERR_TIMEOUT, 0);
+}
+
 }  // namespace
+
+cudaError_t launch_wait_selftest(DevStatus* st, long long cycles, cudaStream_t stream) {
+  wait_selftest_kernel<<<1, 32, 0, stream>>>(st, cycles);
+  note_launch(1);
+  return cudaGetLastError();
+}
 
 bool gram_store_supported(int32_t na, int32_t b0, int32_t nb) {
   return na >= 1 && nb >= 1 && nb <= 32 && b0 >= 0 && b0 % 8 == 0;

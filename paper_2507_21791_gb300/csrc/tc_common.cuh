@@ -372,13 +372,17 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* mbar) {
 __device__ __forceinline__ void named_bar_sync(int id, int count) {
   asm volatile("bar.sync %0, %1;\n" ::"r"(id), "r"(count) : "memory");
 }
-// Poll the barrier's phase `phase` for at most kWaitCycles; true when it completed.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* mbar, uint32_t phase) {
+// Poll the barrier's phase `phase` for at most `limit` cycles; true when it completed.
+__device__ __forceinline__ bool mbar_wait_limit(uint64_t* mbar, uint32_t phase, long long limit) {
   const long long t0 = clock64();
   bool ok;
   while (!(ok = mbar_try(smem_u32(mbar), phase)))
-    if (clock64() - t0 > kWaitCycles) break;
+    if (clock64() - t0 > limit) break;
   return ok;
+}
+// ... for at most kWaitCycles (about one second).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* mbar, uint32_t phase) {
+  return mbar_wait_limit(mbar, phase, kWaitCycles);
 }
 __device__ __forceinline__ void fence_smem_to_async() {
   asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");

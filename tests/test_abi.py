@@ -123,3 +123,16 @@ def test_ragged_shapes_accepted(m, n, s):
     for variant in range(4):
         assert lib.bcgs_qr_workspace_size(m, n, s, variant, 0, ctypes.byref(out)) == 0
         assert out.value > 0
+
+
+def test_wait_selftest_argument_checks():
+    """bcgs_wait_selftest rejects bad arguments before touching the GPU."""
+    ensure_library()
+    from paper_2507_21791_gb300 import bcgs
+
+    lib = bcgs.load_library()
+    assert lib.bcgs_wait_selftest(None, 256, 1000, None) == 1
+    assert lib.bcgs_wait_selftest(256, 128, 1000, None) == 1
+    assert lib.bcgs_wait_selftest(256, 256, 0, None) == 1
+    assert lib.bcgs_wait_selftest(256, 256, 3_000_000_000, None) == 1
+    assert lib.bcgs_wait_selftest(257, 256, 1000, None) == 5

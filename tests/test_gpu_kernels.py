@@ -112,3 +112,19 @@ def test_chol_reports_not_spd(cuda):
     A = np.array([[np.nan, 0.0], [0.0, 1.0]])
     _, code = cuda.chol(cuda.to_device_colmajor(A))
     assert cuda.STATUS[code] == "nonfinite"
+
+
+def test_bounded_wait_runs_out_and_reports_timeout(cuda):
+    """A device wait on a barrier that nothing completes gives up after its
+    bound and records BCGS_ERR_TIMEOUT (no fault, no hang); the context stays
+    usable: a factorization right after it succeeds."""
+    import torch
+
+    lib = cuda.load_library()
+    ws = torch.empty(256, dtype=torch.uint8, device="cuda")
+    assert lib.bcgs_wait_selftest(ws.data_ptr(), ws.numel(), 2_000_000, None) == 0
+    code, blk = cuda.factor_status(ws)
+    assert cuda.STATUS[code] == "timeout" and blk == 0
+    X = synth.make_matrix_np(5000, 32, 1e3, seed=3)
+    Q, R, code, _ = cuda.factor(cuda.to_device_colmajor(X), 8, "bcgsi+p-1s")
+    assert code == 0 and oracle.residual(X, Q.cpu().numpy(), R.cpu().numpy()) <= 1e-13
