@@ -12,6 +12,8 @@
 #include <mutex>
 #include <new>
 
+#include <nvtx3/nvToolsExt.h>  // header-only; a no-op unless a profiler is attached
+
 #include "bcgs_internal.cuh"
 
 using namespace bcgs;
@@ -627,8 +629,18 @@ int init_handle(bcgs_qr_s* h, int64_t m, int32_t n_max, int32_t s, int variant, 
   return BCGS_OK;
 }
 
+// NVTX range over the host-side enqueue of one block step (tools show it
+// against the kernels it launched)
+struct StepRange {
+  explicit StepRange(const char* name) { nvtxRangePushA(name); }
+  ~StepRange() { nvtxRangePop(); }
+};
+
 int step_handle(bcgs_qr_s* h, const void* X, int64_t ldx) {
   if (h->finished || (int64_t)h->j * h->s >= h->n_max) return BCGS_ERR_STATE;
+  static const char* kNames[4] = {"bcgs step (BCGSI+)", "bcgs step (BCGSI+P-1S)", "bcgs step (BCGSI+P-2S)",
+                                  "bcgs step (BCGS-PIPI+)"};
+  StepRange range(kNames[h->variant]);
   if (X == nullptr || ldx < h->m) return BCGS_ERR_INVALID_ARG;
   const int rc = do_step(h, X, ldx);
   if (rc != BCGS_OK) return rc;
@@ -638,6 +650,7 @@ int step_handle(bcgs_qr_s* h, const void* X, int64_t ldx) {
 
 int finish_handle(bcgs_qr_s* h) {
   if (h->finished) return BCGS_OK;
+  StepRange range("bcgs finish");
   if (h->j == 0) return BCGS_ERR_STATE;
   if (h->delayed() && h->j >= 2 && !h->flushed) {
     const int rc = finish_p(h);
