@@ -40,10 +40,12 @@ bool valid_shape(int64_t m, int32_t n, int32_t s) {
 }
 
 // The digit store of Q pays for itself where the projections run on the tensor
-// cores: FP64 storage, s <= 32, and the row count the engine option selects.
+// cores: s <= 32 and the row count the engine option selects (FP32 storage
+// converts to FP64 exactly, so both storage types share it).
 bool want_store(int64_t m, int32_t s, int precision) {
   const int e = gram_engine();
-  return precision == BCGS_FP64 && s <= 32 && e != 0 && (e == 2 || m >= gram_tc_min_rows());
+  (void)precision;
+  return s <= 32 && e != 0 && (e == 2 || m >= gram_tc_min_rows());
 }
 
 void make_layout(int64_t m, int32_t n_max, int32_t s, int variant, int precision, int store,
@@ -259,6 +261,7 @@ cudaError_t project(bcgs_qr_s* h, Seg v, int c, const double* C, int ldc, const 
     p.m = h->m;
     p.block = h->j + 1;
     p.fexp = h->fexp();
+    p.fp32 = h->fp32;
     return launch_project_store(p, h->st(), h->stream);
   }
   if (use_tensor_project(d)) return launch_project_tc(d, h->st(), h->stream);
@@ -268,8 +271,7 @@ cudaError_t project(bcgs_qr_s* h, Seg v, int c, const double* C, int ldc, const 
 // Digits of the freshly written columns [col0, col0 + sb) of Q into the store.
 cudaError_t wrote_q_cols(bcgs_qr_s* h, int col0, int sb, int block) {
   if (!h->L.store) return cudaSuccess;
-  const double* Q = reinterpret_cast<const double*>(h->Q);
-  return launch_qsplit(h->qs(), Q + (size_t)col0 * h->ldq, h->ldq, Q, h->ldq, h->m, col0, sb, h->st(), block,
+  return launch_qsplit(h->qs(), h->Qcol(col0), h->ldq, h->Q, h->ldq, h->m, col0, sb, h->fp32, h->st(), block,
                        h->stream);
 }
 // ... of the freshly written (full) block column k of Q.
@@ -279,9 +281,8 @@ cudaError_t wrote_q(bcgs_qr_s* h, int k) { return wrote_q_cols(h, (k - 1) * h->s
 // [k0, k0 + s), the columns Q fills next.
 cudaError_t store_put(bcgs_qr_s* h, const void* src, int64_t ld, int k0, int sb = 0) {
   if (!h->sgram) return cudaSuccess;
-  const double* Q = reinterpret_cast<const double*>(h->Q);
-  return launch_qsplit(h->qs(), reinterpret_cast<const double*>(src), ld, Q, h->ldq, h->m, k0, sb ? sb : h->s,
-                       h->st(), h->j + 1, h->stream);
+  return launch_qsplit(h->qs(), src, ld, h->Q, h->ldq, h->m, k0, sb ? sb : h->s, h->fp32, h->st(), h->j + 1,
+                       h->stream);
 }
 
 // G = A^T B: from the store (A = store columns [0, na), B = [b0, b0 + nb)) when
@@ -361,6 +362,7 @@ int finish_p(bcgs_qr_s* h) {
     p.m = h->m;
     p.block = q;
     p.fexp = h->fexp();
+    p.fp32 = h->fp32;
     TRY(launch_project_store(p, h->st(), h->stream));
   } else {
     TRY(project(h, h->Useg(), c, G, ldg, h->buf(h->L.Yd), h->Qblk(q), h->ldq, h->Qmax(q)));
@@ -443,6 +445,7 @@ int step_p(bcgs_qr_s* h, const void* X, int64_t ldx) {
     p.m = h->m;
     p.block = k;
     p.fexp = h->fexp();
+    p.fp32 = h->fp32;
     TRY(launch_project_store(p, h->st(), h->stream));
     TRY(wrote_q(h, k));
     if (!one_sync) TRY(tsqr(h, h->Vseg(), h->U(), h->L.ldu, h->buf(h->L.Sd[nxt]), s, k + 1, h->Umax()));

@@ -160,9 +160,9 @@ QStore qstore_at(void* base, int64_t m, int32_t n_max);
 // (FP64, ld lds).  The rest of the 16-column chunk holding column k0 + s - 1 is
 // written as zeros, and columns of the 8-column group before k0 are rewritten
 // from Q (ld ldq) with their unchanged exponents.
-cudaError_t launch_qsplit(const QStore& qs, const double* src, int64_t lds, const double* Q, int64_t ldq,
-                          int64_t m, int32_t k0, int32_t s, DevStatus* st, int32_t block,
-                          cudaStream_t stream);
+// src and Q are float when fp32 (the storage type), else double.
+cudaError_t launch_qsplit(const QStore& qs, const void* src, int64_t lds, const void* Q, int64_t ldq, int64_t m,
+                          int32_t k0, int32_t s, int32_t fp32, DevStatus* st, int32_t block, cudaStream_t stream);
 
 // Gram from the store (gram_store.cu): G = A^T B with A = store columns [0, na)
 // and B = store columns [b0, b0 + nb), b0 a multiple of 8, nb <= 32.  Chunks of
@@ -182,6 +182,8 @@ cudaError_t launch_gram_store(const GramStoreDesc& d, double* partial, double* G
 
 // One output of the store projection: W = (V - P_o) T^{-1}; V null means W = P_o T^{-1},
 // T null means no solve.
+// v and w point to the storage type of the factorization (double, or float
+// under StoreProjDesc::fp32); T is always FP64.
 struct ProjOut {
   const double* v; int64_t ldv;
   const double* T; int32_t ldt;
@@ -200,6 +202,7 @@ struct StoreProjDesc {
   int64_t m;
   int32_t block;
   int32_t* fexp;  // scratch: 32 ints per row block (column exponents of B')
+  int32_t fp32;   // X (v) and the outputs (w) are float
 };
 bool project_store_supported(int32_t s, int32_t nouts);
 cudaError_t launch_project_store(const StoreProjDesc& d, DevStatus* st, cudaStream_t stream);

@@ -58,11 +58,12 @@ __device__ __forceinline__ int exp_field(double v) {
   return (int)(((unsigned long long)__double_as_longlong(v) >> 52) & 0x7FF);
 }
 
-// One CTA per 128-row block, one thread per row.
-__global__ void __launch_bounds__(kStoreRows) qsplit_kernel(QStore qs, const double* src, int64_t lds,
-                                                            const double* Q, int64_t ldq, int64_t m,
-                                                            int32_t k0, int32_t s, DevStatus* st,
-                                                            int32_t block) {
+// One CTA per 128-row block, one thread per row.  T is the storage type of src
+// and Q (float values convert to double exactly).
+template <typename T>
+__global__ void __launch_bounds__(kStoreRows) qsplit_kernel(QStore qs, const T* src, int64_t lds, const T* Q,
+                                                            int64_t ldq, int64_t m, int32_t k0, int32_t s,
+                                                            DevStatus* st, int32_t block) {
   if (block_failed(st)) return;
   __shared__ int s_wmax[kStoreRows / 32][kQsplitMaxCols];
   __shared__ int s_e[kQsplitMaxCols];
@@ -72,7 +73,9 @@ __global__ void __launch_bounds__(kStoreRows) qsplit_kernel(QStore qs, const dou
   const int klo = k0 & ~7, kend = k0 + s;
   const int kwr = (kend + 15) & ~15;
   // column k of the store: src column k - k0, or (k < k0) column k of Q
-  auto at = [&](int k) { return k >= k0 ? src[r + (int64_t)(k - k0) * lds] : Q[r + (int64_t)k * ldq]; };
+  auto at = [&](int k) -> double {
+    return k >= k0 ? (double)src[r + (int64_t)(k - k0) * lds] : (double)Q[r + (int64_t)k * ldq];
+  };
   for (int k = klo; k < kend; ++k) {
     const int e = live ? exp_field(at(k)) : 0;
     const int mx = __reduce_max_sync(0xffffffffu, e);
@@ -114,10 +117,10 @@ __global__ void __launch_bounds__(kStoreRows) qsplit_kernel(QStore qs, const dou
 // The common case of the split: k0 a multiple of 8 and at most NC <= 16 columns
 // (s <= 16): each thread holds its row's values in registers, so all loads are
 // in flight at once and Q is read once.
-template <int NC>
-__global__ void __launch_bounds__(kStoreRows) qsplit_reg_kernel(QStore qs, const double* src, int64_t lds,
-                                                                int64_t m, int32_t k0, int32_t s,
-                                                                DevStatus* st, int32_t block) {
+template <int NC, typename T>
+__global__ void __launch_bounds__(kStoreRows) qsplit_reg_kernel(QStore qs, const T* src, int64_t lds, int64_t m,
+                                                                int32_t k0, int32_t s, DevStatus* st,
+                                                                int32_t block) {
   if (block_failed(st)) return;
   __shared__ int s_wmax[kStoreRows / 32][NC];
   const int i = threadIdx.x, warp = i >> 5, lane = i & 31;
@@ -125,7 +128,7 @@ __global__ void __launch_bounds__(kStoreRows) qsplit_reg_kernel(QStore qs, const
   const bool live = r < m;
   double v[NC];
 #pragma unroll
-  for (int k = 0; k < NC; ++k) v[k] = (live && k < s) ? src[r + (int64_t)k * lds] : 0.0;
+  for (int k = 0; k < NC; ++k) v[k] = (live && k < s) ? (double)src[r + (int64_t)k * lds] : 0.0;
 #pragma unroll
   for (int k = 0; k < NC; ++k) {
     const int mx = __reduce_max_sync(0xffffffffu, exp_field(v[k]));
@@ -351,6 +354,19 @@ __global__ void __launch_bounds__(kThreads, 1) proj_store_kernel(StoreProjDesc d
     const int bc = bcol(j);
     return bc >= 0 ? d.B[k + (int64_t)bc * d.ldb] : 0.0;
   };
+  // X and the outputs in the storage type (FP32 when d.fp32; the products and the
+  // epilogue stay FP64); the maxima are those of the stored values
+  const int64_t io_size = d.fp32 ? 4 : 8;
+  auto vload = [&](const ProjOut& o, int64_t idx) -> double {
+    return d.fp32 ? (double)reinterpret_cast<const float*>(o.v)[idx] : o.v[idx];
+  };
+  auto wstore = [&](const ProjOut& o, int64_t idx, double x) {
+    if (d.fp32)
+      reinterpret_cast<float*>(o.w)[idx] = (float)x;
+    else
+      o.w[idx] = x;
+  };
+  auto stored = [&](double x) -> double { return d.fp32 ? (double)(float)x : x; };
   if (warp == kCtl) tmem_alloc<C::kTmem>(&tmem_base_s);
   tc_before_sync();
   __syncthreads();
@@ -524,7 +540,8 @@ __global__ void __launch_bounds__(kThreads, 1) proj_store_kernel(StoreProjDesc d
         const ProjOut& o1 = d.out[1];
         if (half == 1 && o1.v != nullptr && r0 + qrow < d.m)
           for (int j = 0; j < s; ++j)
-            asm volatile("prefetch.global.L2 [%0];\n" ::"l"(o1.v + r0 + qrow + (int64_t)j * o1.ldv));
+            asm volatile("prefetch.global.L2 [%0];\n" ::"l"(reinterpret_cast<const char*>(o1.v) +
+                                                            (r0 + qrow + (int64_t)j * o1.ldv) * io_size));
       }
       long long hi[kHalf], lo[kHalf];
 #pragma unroll
@@ -599,7 +616,7 @@ __global__ void __launch_bounds__(kThreads, 1) proj_store_kernel(StoreProjDesc d
           if (out.v != nullptr) {
 #pragma unroll
             for (int j = 0; j < kHalf; ++j)
-              if (j < s) w[j] = out.v[r + (int64_t)j * out.ldv] - w[j];
+              if (j < s) w[j] = vload(out, r + (int64_t)j * out.ldv) - w[j];
           }
           if (o == NOUT - 1 && has_t) {
 #pragma unroll
@@ -615,19 +632,19 @@ __global__ void __launch_bounds__(kThreads, 1) proj_store_kernel(StoreProjDesc d
           }
 #pragma unroll
           for (int j = 0; j < kHalf; ++j)
-            if (j < s) out.w[r + (int64_t)j * out.ldw] = w[j];
+            if (j < s) wstore(out, r + (int64_t)j * out.ldw, w[j]);
           if (out.wmax.row != nullptr) {
             unsigned long long mx = 0ull;
 #pragma unroll
             for (int j = 0; j < kHalf; ++j)
-              if (j < s) mx = umax64(mx, abs_bits64(w[j]));
+              if (j < s) mx = umax64(mx, abs_bits64(stored(w[j])));
             out.wmax.row[r] = umax64(out.wmax.row[r], mx);
           }
         }
         if (out.wmax.col != nullptr) {  // warp-uniform: o is
 #pragma unroll
           for (int j = 0; j < kHalf; ++j)
-            if (j < s) warp_max_to(live ? abs_bits64(w[j]) : 0ull, out.wmax.col + j);
+            if (j < s) warp_max_to(live ? abs_bits64(stored(w[j])) : 0ull, out.wmax.col + j);
         }
       } else {
         // one output: the two halves of a row meet in P, one thread per row
@@ -649,7 +666,8 @@ __global__ void __launch_bounds__(kThreads, 1) proj_store_kernel(StoreProjDesc d
         if (live) {
 #pragma unroll
           for (int j = 0; j < SMAX; ++j)
-            if (j < s) w[j] = out.v != nullptr ? out.v[r + (int64_t)j * out.ldv] - P[i * NBT + j] : P[i * NBT + j];
+            if (j < s)
+              w[j] = out.v != nullptr ? vload(out, r + (int64_t)j * out.ldv) - P[i * NBT + j] : P[i * NBT + j];
         }
         named_bar_sync(2, 32 * kReadWarps);  // P read before the next block writes it
         if (live) {
@@ -667,19 +685,19 @@ __global__ void __launch_bounds__(kThreads, 1) proj_store_kernel(StoreProjDesc d
           }
 #pragma unroll
           for (int j = 0; j < SMAX; ++j)
-            if (j < s) out.w[r + (int64_t)j * out.ldw] = w[j];
+            if (j < s) wstore(out, r + (int64_t)j * out.ldw, w[j]);
           if (out.wmax.row != nullptr) {
             unsigned long long mx = 0ull;
 #pragma unroll
             for (int j = 0; j < SMAX; ++j)
-              if (j < s) mx = umax64(mx, abs_bits64(w[j]));
+              if (j < s) mx = umax64(mx, abs_bits64(stored(w[j])));
             out.wmax.row[r] = umax64(out.wmax.row[r], mx);
           }
         }
         if (mine && out.wmax.col != nullptr) {  // warp-uniform: rt < 128 is
 #pragma unroll
           for (int j = 0; j < SMAX; ++j)
-            if (j < s) warp_max_to(live ? abs_bits64(w[j]) : 0ull, out.wmax.col + j);
+            if (j < s) warp_max_to(live ? abs_bits64(stored(w[j])) : 0ull, out.wmax.col + j);
         }
       }
     }
@@ -757,19 +775,28 @@ cudaError_t launch_sp(const StoreProjDesc& d, DevStatus* st, cudaStream_t stream
 
 }  // namespace
 
-cudaError_t launch_qsplit(const QStore& qs, const double* src, int64_t lds, const double* Q, int64_t ldq,
-                          int64_t m, int32_t k0, int32_t s, DevStatus* st, int32_t block,
-                          cudaStream_t stream) {
+cudaError_t launch_qsplit(const QStore& qs, const void* src, int64_t lds, const void* Q, int64_t ldq, int64_t m,
+                          int32_t k0, int32_t s, int32_t fp32, DevStatus* st, int32_t block, cudaStream_t stream) {
   if (s < 1 || s > 64 || qs.nblk <= 0 || k0 < 0 || k0 + s > qs.ld_exp) return cudaErrorInvalidValue;
   const int slot = prof_begin(stream);
-  if (k0 % 8 == 0 && s <= 8)
-    qsplit_reg_kernel<8><<<(unsigned)qs.nblk, kStoreRows, 0, stream>>>(qs, src, lds, m, k0, s, st, block);
-  else if (k0 % 8 == 0 && s <= 16)
-    qsplit_reg_kernel<16><<<(unsigned)qs.nblk, kStoreRows, 0, stream>>>(qs, src, lds, m, k0, s, st, block);
+  const unsigned grid = (unsigned)qs.nblk;
+  auto run = [&](auto tag) {
+    using T = decltype(tag);
+    const T* sp = reinterpret_cast<const T*>(src);
+    const T* qp = reinterpret_cast<const T*>(Q);
+    if (k0 % 8 == 0 && s <= 8)
+      qsplit_reg_kernel<8, T><<<grid, kStoreRows, 0, stream>>>(qs, sp, lds, m, k0, s, st, block);
+    else if (k0 % 8 == 0 && s <= 16)
+      qsplit_reg_kernel<16, T><<<grid, kStoreRows, 0, stream>>>(qs, sp, lds, m, k0, s, st, block);
+    else
+      qsplit_kernel<T><<<grid, kStoreRows, 0, stream>>>(qs, sp, lds, qp, ldq, m, k0, s, st, block);
+  };
+  if (fp32)
+    run(0.0f);
   else
-    qsplit_kernel<<<(unsigned)qs.nblk, kStoreRows, 0, stream>>>(qs, src, lds, Q, ldq, m, k0, s, st, block);
+    run(0.0);
   // reads the s new columns, writes 16 bytes of digits per element
-  prof_end(slot, kProfStoreSplit, stream, 0.0, (double)m * s * (8.0 + 16.0));
+  prof_end(slot, kProfStoreSplit, stream, 0.0, (double)m * s * ((fp32 ? 4.0 : 8.0) + 16.0));
   note_launch(1);
   return cudaGetLastError();
 }

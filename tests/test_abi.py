@@ -59,10 +59,11 @@ def test_workspace_size_queries():
     try:
         bcgs.set_gram_engine("fp64")
         small = bcgs.workspace_size(2 ** 22, 256, 16, "bcgsi+p-1s")
+        small32 = bcgs.workspace_size(2 ** 22, 256, 16, "bcgsi+p-1s", "fp32")
         bcgs.set_gram_engine("tensor")
         big = bcgs.workspace_size(2 ** 22, 256, 16, "bcgsi+p-1s")
         # the tensor engine adds the digit store of Q: 16 bytes per element
-        # plus one exponent per 128 rows and column
+        # plus one exponent per 128 rows and column, for both storage types
         fp32 = bcgs.workspace_size(2 ** 22, 256, 16, "bcgsi+p-1s", "fp32")
     finally:
         bcgs.set_gram_engine(old)
@@ -71,7 +72,8 @@ def test_workspace_size_queries():
     # block for the coefficient side of the projections
     store = 2 ** 22 * 256 * 16 + (2 ** 22 // 128) * 256 * 4 + (2 ** 22 // 128) * 32 * 4
     assert big - small == pytest.approx(store, abs=2 ** 12)
-    assert fp32 < small   # no store with FP32 storage
+    assert fp32 - small32 == pytest.approx(store, abs=2 ** 12)
+    assert small32 < small and fp32 < big  # FP32 blocks of U and V
 
 
 @pytest.mark.parametrize("m,n,s", [(100, 0, 8), (100, 16, 0), (4, 8, 8), (100, 64, 65),
