@@ -268,7 +268,7 @@ __device__ __forceinline__ bool wait_or_abort(uint64_t* mbar, uint32_t parity, v
   return true;
 }
 
-template <int NBT, int NOUT>
+template <int NBT, int NOUT, bool F32>
 __global__ void __launch_bounds__(kThreads, 1) proj_store_kernel(StoreProjDesc d, int32_t b_staged,
                                                                   const __grid_constant__ CUtensorMap amap,
                                                                   int32_t use_amap, DevStatus* st) {
@@ -354,19 +354,27 @@ __global__ void __launch_bounds__(kThreads, 1) proj_store_kernel(StoreProjDesc d
     const int bc = bcol(j);
     return bc >= 0 ? d.B[k + (int64_t)bc * d.ldb] : 0.0;
   };
-  // X and the outputs in the storage type (FP32 when d.fp32; the products and the
+  // X and the outputs in the storage type (float when F32; the products and the
   // epilogue stay FP64); the maxima are those of the stored values
-  const int64_t io_size = d.fp32 ? 4 : 8;
+  constexpr int64_t io_size = F32 ? 4 : 8;
   auto vload = [&](const ProjOut& o, int64_t idx) -> double {
-    return d.fp32 ? (double)reinterpret_cast<const float*>(o.v)[idx] : o.v[idx];
+    if constexpr (F32)
+      return (double)reinterpret_cast<const float*>(o.v)[idx];
+    else
+      return o.v[idx];
   };
   auto wstore = [&](const ProjOut& o, int64_t idx, double x) {
-    if (d.fp32)
+    if constexpr (F32)
       reinterpret_cast<float*>(o.w)[idx] = (float)x;
     else
       o.w[idx] = x;
   };
-  auto stored = [&](double x) -> double { return d.fp32 ? (double)(float)x : x; };
+  auto stored = [&](double x) -> double {
+    if constexpr (F32)
+      return (double)(float)x;
+    else
+      return x;
+  };
   if (warp == kCtl) tmem_alloc<C::kTmem>(&tmem_base_s);
   tc_before_sync();
   __syncthreads();
@@ -745,13 +753,13 @@ bool store_tensor_map(const QStore& qs, CUtensorMap* map) {
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int NBT, int NOUT>
+template <int NBT, int NOUT, bool F32>
 cudaError_t launch_sp(const StoreProjDesc& d, DevStatus* st, cudaStream_t stream) {
   using C = SPCfg<NBT, NOUT>;
   const size_t bbytes = (size_t)(NBT + 4) * (size_t)d.c * sizeof(double);
   const int32_t staged = C::kFixed + bbytes <= kSmemLimit ? 1 : 0;
   const size_t smem = C::kFixed + (staged ? bbytes : 0);
-  cudaError_t e = ensure_dyn_smem(proj_store_kernel<NBT, NOUT>, smem);
+  cudaError_t e = ensure_dyn_smem(proj_store_kernel<NBT, NOUT, F32>, smem);
   if (e != cudaSuccess) return e;
   int sms = g_sm_count;
   if (sms <= 0) {
@@ -769,7 +777,7 @@ cudaError_t launch_sp(const StoreProjDesc& d, DevStatus* st, cudaStream_t stream
   CUtensorMap amap;
   memset(&amap, 0, sizeof(amap));
   const int32_t use_amap = store_tensor_map(d.qs, &amap) ? 1 : 0;
-  proj_store_kernel<NBT, NOUT><<<grid, kThreads, smem, stream>>>(d, staged, amap, use_amap, st);
+  proj_store_kernel<NBT, NOUT, F32><<<grid, kThreads, smem, stream>>>(d, staged, amap, use_amap, st);
   return cudaSuccess;
 }
 
@@ -815,9 +823,15 @@ cudaError_t launch_project_store(const StoreProjDesc& d, DevStatus* st, cudaStre
   if (d.m == 0) return cudaSuccess;
   const int slot = prof_begin(stream);
   cudaError_t e;
-  if (d.nouts == 2) e = launch_sp<32, 2>(d, st, stream);
-  else if (d.s <= 16) e = launch_sp<16, 1>(d, st, stream);
-  else e = launch_sp<32, 1>(d, st, stream);
+  if (d.fp32) {
+    if (d.nouts == 2) e = launch_sp<32, 2, true>(d, st, stream);
+    else if (d.s <= 16) e = launch_sp<16, 1, true>(d, st, stream);
+    else e = launch_sp<32, 1, true>(d, st, stream);
+  } else {
+    if (d.nouts == 2) e = launch_sp<32, 2, false>(d, st, stream);
+    else if (d.s <= 16) e = launch_sp<16, 1, false>(d, st, stream);
+    else e = launch_sp<32, 1, false>(d, st, stream);
+  }
   if (e != cudaSuccess) return e;
   note_launch(1);  // the exponent kernel
   const double K = (double)d.c, nw = (double)d.nouts * d.s;
