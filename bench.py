@@ -48,9 +48,9 @@ TRAFFIC_RATIO = {
     # profiles/gram_partial_kernel_m524288_256x32.md:
     # (1.208285 GB + 3.823 MB) / (524288 * 288 * 8 B + 304 * 256 * 32 * 8 B)
     "gram_partial_kernel": (1.208285e9 + 3.823104e6) / (524288 * 288 * 8 + 304 * 256 * 32 * 8),
-    # profiles/proj_store_kernel_m262144_n256_s16.md: (910.775 MB + 58.814 MB) / (8 * 262144 * 256 B);
+    # profiles/proj_store_kernel_m262144_n256_s16.md: (910.942 MB + 58.831 MB) / (8 * 262144 * 256 B);
     # the digit stream is 16 B per element of Q against 8 algorithmic bytes
-    "proj_store_kernel": (910.774528e6 + 58.814208e6) / (8 * 262144 * 256),
+    "proj_store_kernel": (910.941952e6 + 58.830592e6) / (8 * 262144 * 256),
     # profiles/gram_store_kernel_m262144_n256_s16.md: (944.189 MB + 9.524 MB) / (8 * 262144 * 256 B)
     "gram_store_kernel": (944.189440e6 + 9.524224e6) / (8 * 262144 * 256),
 }
