@@ -125,7 +125,8 @@ BCGS_API int bcgs_qr_factor(int64_t m, int32_t n, int32_t s, int variant, int pr
  * are host memory, page-locked for the copies to overlap (pageable memory
  * works, without overlap).  Everything is ordered on `stream`: the results
  * are on the host once `stream` has completed, and the status is read with
- * bcgs_qr_factor_status.  Returns BCGS_ERR_INVALID_ARG for a null pointer or
+ * bcgs_qr_factor_status.  Safe to call from several host threads (the copy
+ * streams are shared per device; calls enqueue one after the other).  Returns BCGS_ERR_INVALID_ARG for a null pointer or
  * a leading dimension below m (n for R). */
 BCGS_API int bcgs_qr_factor_host(int64_t m, int32_t n, int32_t s, int variant, int precision,
                    const void* X_host, int64_t ldxh, void* Q_host, int64_t ldqh, double* R_host,
@@ -207,7 +208,9 @@ BCGS_API int bcgs_qr_batched_workspace_size(int32_t count, const bcgs_problem* p
  * on 16 internal streams (created on the first call on a device and kept until
  * exit) that fork from and join back into `stream`, so capturing `stream` into
  * a CUDA graph captures the whole batch as one graph.  Each problem's result is
- * the same as bcgs_qr_factor's for it alone (fixed reduction order). */
+ * the same as bcgs_qr_factor's for it alone (fixed reduction order).  Safe to
+ * call from several host threads (the internal streams are shared per device;
+ * calls enqueue one after the other). */
 BCGS_API int bcgs_qr_factor_batched(int32_t count, const bcgs_problem* probs, void* workspace,
                            size_t ws_bytes, void* stream);
 

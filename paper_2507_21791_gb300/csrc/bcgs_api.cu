@@ -681,6 +681,7 @@ struct BatchStreams {
   cudaStream_t lane[kBatchLanes];
   cudaEvent_t fork;
   cudaEvent_t join[kBatchLanes];
+  std::mutex call;  // one batched call enqueues its fork, lanes and join at a time
 };
 std::mutex g_batch_mu;
 BatchStreams* g_batch[64] = {nullptr};
@@ -710,6 +711,7 @@ int batch_streams(BatchStreams** out) {
 struct CopyStreams {
   cudaStream_t h2d, d2h;
   cudaEvent_t start, in, out, done;
+  std::mutex call;  // one host call enqueues its copies and events at a time
 };
 std::mutex g_copy_mu;
 CopyStreams* g_copy[64] = {nullptr};
@@ -817,6 +819,8 @@ int bcgs_qr_factor_host(int64_t m, int32_t n, int32_t s, int variant, int precis
   CopyStreams* cs = nullptr;
   rc = copy_streams(&cs);
   if (rc != BCGS_OK) return rc;
+  // shared by every caller on this device: host threads enqueue one call at a time
+  std::lock_guard<std::mutex> lk(cs->call);
   const size_t esz = precision == BCGS_FP32_STORAGE ? 4 : 8;
   const int q = (n + s - 1) / s;  // the last block may be ragged
   const cudaStream_t main = h->stream;
@@ -1082,6 +1086,10 @@ int bcgs_qr_factor_batched(int32_t count, const bcgs_problem* probs, void* works
   BatchStreams* bs = nullptr;
   rc = batch_streams(&bs);
   if (rc != BCGS_OK) return rc;
+  // The lanes and events are shared by every caller on this device: calls from
+  // several host threads enqueue one after the other (a wait takes the event as
+  // recorded when the wait is enqueued, so nothing else needs ordering).
+  std::lock_guard<std::mutex> lk(bs->call);
   // Fork: every lane waits for the work already queued on the caller's stream.
   if (cudaEventRecord(bs->fork, origin) != cudaSuccess) return BCGS_ERR_CUDA;
   for (int l = 0; l < kBatchLanes; ++l)

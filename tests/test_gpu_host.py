@@ -70,3 +70,41 @@ def test_host_path_reports_breakdown(cuda):
     X[:, 8:16] = 0.0
     _, _, code, blk = run_host(cuda, X, 8, "bcgsi+p-2s")
     assert cuda.STATUS[code] == "rank_deficient" and blk == 2
+
+
+def test_host_path_from_several_threads(cuda):
+    """The copy streams are shared per device: calls from several host threads
+    (each on its own stream) still give each caller the bits of a serial call."""
+    import threading
+
+    import torch
+
+    shapes = [(20000, 48, 8, "bcgsi+p-1s"), (30000, 64, 16, "bcgsi+p-2s"), (25000, 40, 8, "bcgs-pipi+"),
+              (20000, 56, 8, "bcgsi+")]
+    Xs = [synth.make_matrix_np(m, n, 1e3, seed=90 + i) for i, (m, n, s, v) in enumerate(shapes)]
+    serial = [run_host(cuda, X, s, v)[:2] for X, (m, n, s, v) in zip(Xs, shapes)]
+    out = [None] * len(shapes)
+
+    def work(i):
+        m, n, s, v = shapes[i]
+        st = torch.cuda.Stream()
+        with torch.cuda.stream(st):
+            Xh = host_colmajor(torch, m, n, torch.float64, True)
+            Xh.copy_(torch.from_numpy(Xs[i]))
+            Qh = host_colmajor(torch, m, n, torch.float64, True)
+            Rh = host_colmajor(torch, n, n, torch.float64, True)
+            Xd, Qd = cuda.empty_colmajor(m, n, torch.float64), cuda.empty_colmajor(m, n, torch.float64)
+            Rd = cuda.empty_colmajor(n, n, torch.float64)
+            ws = torch.empty(cuda.workspace_size(m, n, s, v), dtype=torch.uint8, device="cuda")
+            cuda.factor_host_async(Xh, s, v, "fp64", Qh, Rh, Xd, Qd, Rd, ws, stream=st)
+            code, _ = cuda.factor_status(ws, stream=st)
+        out[i] = (Qh.numpy().copy(), Rh.numpy().copy(), code)
+
+    threads = [threading.Thread(target=work, args=(i,)) for i in range(len(shapes))]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    for (Qs, Rs), (Qt, Rt, code) in zip(serial, out):
+        assert code == 0
+        assert np.array_equal(Qs, Qt) and np.array_equal(Rs, Rt)
