@@ -190,7 +190,7 @@ BCGS_API int bcgs_qr_destroy(bcgs_qr_t handle);
  * ------------------------------------------------------------------------- */
 typedef struct {
   int64_t m;         /* rows                                 */
-  int32_t n, s;      /* columns and block size (n % s == 0)  */
+  int32_t n, s;      /* columns and block size (ragged last block when s does not divide n) */
   int32_t variant;   /* bcgs_variant                         */
   int32_t precision; /* bcgs_precision                        */
   const void* X; int64_t ldx;
