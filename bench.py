@@ -193,9 +193,9 @@ def main_ours(args):
     import torch
     import torch.distributed as dist
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    from paper_2507_21791_gb300.replicas import dist_env, max_over_ranks, whole_job_gbs
+
+    world, rank, local = dist_env()
     if world > 1:
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
@@ -267,11 +267,8 @@ def main_ours(args):
                 "Q": Q, "R": R}
 
     main = run_variant("bcgsi+p-1s", profile=True)
-    t = torch.tensor([main["ms"]], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = t.item()
-    value = world * alg_bytes_1s(Mr, N, S) / (ms_max * 1e-3) / 1e9
+    ms_max = max_over_ranks(main["ms"], dev)
+    value = whole_job_gbs(world, alg_bytes_1s(Mr, N, S), ms_max)
 
     # e2e through the public API with pinned host buffers
     Xh = torch.empty((N, Mr), dtype=torch.float64, pin_memory=True).T
@@ -297,10 +294,8 @@ def main_ours(args):
     e1.record(stream)
     barrier()
     ms_e2e = e0.elapsed_time(e1) / args.steps
-    te = torch.tensor([ms_e2e], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_value = world * alg_bytes_1s(Mr, N, S) / (te.item() * 1e-3) / 1e9
+    ms_e2e = max_over_ranks(ms_e2e, dev)
+    e2e_value = whole_job_gbs(world, alg_bytes_1s(Mr, N, S), ms_e2e)
     del ws, Xd, Xh, Qh, Rh
 
     compare = {}
@@ -372,7 +367,7 @@ def main_ours(args):
                    "variant": "bcgsi+p-1s", "parallelism": "replicas" if world > 1 else "single",
                    "l2": "inputs larger than L2 (X and Q 8.6 GB each); no flush"},
         "e2e": {"value": e2e_value, "unit": "GB/s", "h2d_bytes_per_step": Mr * N * 8,
-                "d2h_bytes_per_step": Mr * N * 8 + N * N * 8, "ms_per_step": te.item()},
+                "d2h_bytes_per_step": Mr * N * 8 + N * N * 8, "ms_per_step": ms_e2e},
         "gpu_launches": main["launches"],
         "roofline": roofline,
         "kernels": others,
