@@ -44,6 +44,10 @@ FP64_PEAK_TFLOPS = 1.25  # GB300 FP64 rate of the profiling recipe's table (nomi
 # of the current kernel on a smaller case (profiles/); traffic grows with the rows
 # processed, so a full launch moves this ratio times its algorithmic bytes.  A
 # kernel that changed since its capture has no entry (traffic reported as null).
+# nominal HBM3e bandwidth of a GB300 (the spec sheet); the roofline's peak is the
+# measured copy bandwidth, the spec fraction is reported beside it
+HBM_SPEC_GBS = 7900.0
+
 TRAFFIC_RATIO = {
     # profiles/gram_partial_kernel_m524288_256x32.md:
     # (1.208285 GB + 3.823 MB) / (524288 * 288 * 8 B + 304 * 256 * 32 * 8 B)
@@ -313,7 +317,8 @@ def main_ours(args):
     forms = None
     if not args.no_forms and world == 1:
         del main["Q"], main["R"]
-        forms = {"fp32_storage": bench_fp32(args, dev, stream),
+        forms = {"small_config": bench_small(args, dev, stream),
+                 "fp32_storage": bench_fp32(args, dev, stream),
                  "block_sizes": bench_block_sizes(args, dev, stream),
                  "batched": bench_batched(args, dev, stream),
                  "serving": bench_serving(args, dev)}
@@ -339,6 +344,7 @@ def main_ours(args):
                                                           "operands from the resident digit store)",
                     "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                     "frac": achieved / peaks["hbm_gbs"], "peak_source": peaks["source"],
+                    "frac_of_spec": achieved / HBM_SPEC_GBS,
                     "fp64_equivalent_tflops": gfl / (gms * 1e-3) / 1e12}
     roofline.update({
         "traffic": TRAFFIC_RATIO[kernel_name] * gby / max(gl, 1) if kernel_name in TRAFFIC_RATIO else None,
@@ -440,6 +446,47 @@ TABLE2_64_NODES = {
     "bcgs-pipi+": {1: 1.6, 2: 3.0, 4: 5.9, 8: 11.7, 16: 22.7},
     "bcgsi+": {1: 1.0, 2: 1.4, 4: 2.7, 8: 5.4, 16: 8.8},
 }
+
+
+def bench_small(args, dev, stream):
+    """Small configuration (m = 10^4, n = 64, s = 8, kappa = 1e4): the whole
+    factorization stays in L2, so it is bound by kernel launches and the
+    grid-wide reductions, the one-GPU analog of the synchronization-bound regime
+    of Sec. 4.  Per variant: microseconds per factorization (3 warm-ups, 20
+    timed), kernel launches and synchronizations (Gram reductions and TSQR trees)
+    per factorization."""
+    import torch
+
+    from paper_2507_21791_gb300 import bcgs, synth
+
+    m, n, s, kappa = 10_000, 64, 8, 1e4
+    X = synth.make_matrix_torch(m, n, kappa, seed=1000, device=str(dev))
+    Q = bcgs.empty_colmajor(m, n, torch.float64, dev)
+    R = bcgs.empty_colmajor(n, n, torch.float64, dev)
+    out = {}
+    for v in ("bcgsi+", "bcgsi+p-2s", "bcgsi+p-1s", "bcgs-pipi+"):
+        ws = torch.empty(bcgs.workspace_size(m, n, s, v), dtype=torch.uint8, device=dev)
+
+        def run():
+            bcgs.factor_async(X, s, v, "fp64", Q, R, ws)
+
+        run()
+        torch.cuda.synchronize()
+        l0 = bcgs.launch_count()
+        run()
+        torch.cuda.synchronize()
+        launches = bcgs.launch_count() - l0
+        bcgs.profile_enable(True)
+        run()
+        torch.cuda.synchronize()
+        syncs = bcgs.profile_read("gram_reduce")[0] + bcgs.profile_read("tsqr")[0]
+        bcgs.profile_enable(False)
+        ms = _timed(run, 3, 20, stream)
+        out[v] = {"us_per_factorization": ms * 1e3, "kernel_launches": launches, "synchronizations": int(syncs),
+                  "status": bcgs.STATUS[bcgs.factor_status(ws)[0]]}
+        del ws
+    return {"workload": f"m=10^4 n=64 s=8 kappa={kappa:g}, FP64, L2-resident", "variants": out,
+            "note": "launch- and synchronization-bound: no HBM fraction"}
 
 
 def bench_block_sizes(args, dev, stream):
