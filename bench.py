@@ -41,21 +41,22 @@ M, N, S, KAPPA = 2 ** 22, 256, 16, 1e5
 WORKLOAD = "single FP64 QR m=2^22 n=256 s=16 (q=16) BCGSI+P-1S, X=U diag(sigma) V^T kappa=1e5"
 FP64_PEAK_TFLOPS = 1.25  # GB300 FP64 rate of the profiling recipe's table (nominal)
 # DRAM traffic of a kernel relative to its algorithmic bytes, from one ncu capture
-# of the current kernel on a smaller case (profiles/); traffic grows with the rows
-# processed, so a full launch moves this ratio times its algorithmic bytes.  A
-# kernel that changed since its capture has no entry (traffic reported as null).
+# of the current kernel on a smaller case (the committed ncu summaries); traffic
+# grows with the rows processed, so a full launch moves this ratio times its
+# algorithmic bytes.  A kernel that changed since its capture has no entry
+# (traffic reported as null).
 # nominal HBM3e bandwidth of a GB300 (the spec sheet); the roofline's peak is the
 # measured copy bandwidth, the spec fraction is reported beside it
 HBM_SPEC_GBS = 7900.0
 
 TRAFFIC_RATIO = {
-    # profiles/gram_partial_kernel_m524288_256x32.md:
+    # FP64-pipe Gram, ncu capture at m = 524288, 256 x 32 outputs:
     # (1.208285 GB + 3.823 MB) / (524288 * 288 * 8 B + 304 * 256 * 32 * 8 B)
     "gram_partial_kernel": (1.208285e9 + 3.823104e6) / (524288 * 288 * 8 + 304 * 256 * 32 * 8),
-    # profiles/proj_store_kernel_m262144_n256_s16.md: (910.942 MB + 58.831 MB) / (8 * 262144 * 256 B);
+    # store projection, ncu capture at m = 262144, K = 208, s = 16: (910.942 MB + 58.831 MB) / (8 * 262144 * 256 B);
     # the digit stream is 16 B per element of Q against 8 algorithmic bytes
     "proj_store_kernel": (910.941952e6 + 58.830592e6) / (8 * 262144 * 256),
-    # profiles/gram_store_kernel_m262144_n256_s16.md: (944.189 MB + 9.524 MB) / (8 * 262144 * 256 B)
+    # store Gram, ncu capture at m = 262144, na = 224, nb = 32: (944.189 MB + 9.524 MB) / (8 * 262144 * 256 B)
     "gram_store_kernel": (944.189440e6 + 9.524224e6) / (8 * 262144 * 256),
 }
 

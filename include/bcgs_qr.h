@@ -26,7 +26,10 @@
  *     accumulated, and every small factor (Cholesky, triangular solves, R) is
  *     computed, in FP64.  R is always double*.
  *   - The caller owns every buffer.  The library never allocates device memory
- *     and never frees caller memory; X is read-only and must not alias Q.
+ *     and never frees caller memory; X is read-only and must not alias Q:
+ *     bcgs_qr_factor, bcgs_qr_factor_host (Xd, Qd) and bcgs_qr_factor_batched
+ *     return BCGS_ERR_INVALID_ARG, before enqueueing anything, when the memory
+ *     of X and Q overlaps (in-place factorization is not supported).
  *   - Calls are asynchronous and ordered on the given CUDA stream (a
  *     cudaStream_t passed as void*; NULL = the legacy default stream).
  *     Invalid arguments are reported synchronously by the return value and
@@ -254,6 +257,11 @@ BCGS_API int bcgs_gram(int64_t m, int32_t ka, int32_t kb, const double* A, int64
  *   Sharing: all calls use the same array.  Calls whose kernels may overlap on
  *   the GPU (different streams, or host threads without ordering) race on it
  *   and give wrong results; order them on one stream.
+ *   Errors: there is no status word.  A non-finite entry of A or B (and a
+ *   device wait of the tensor engine that runs out) shows as NaN entries of C;
+ *   every partial slot is rewritten by each call, so C never holds what an
+ *   earlier call left in the array.  The device address is looked up once per
+ *   device and kept: do not use the entry point across a cudaDeviceReset.
  *   No cudaMalloc, cudaFree or allocating library routine is called. */
 #define BCGS_GRAM_NOALLOC_MAX_PARTIALS 1048576
 BCGS_API int bcgs_gram_noalloc(int64_t m, int32_t ka, int32_t kb, const double* A, int64_t lda,
@@ -307,11 +315,15 @@ BCGS_API int bcgs_chol(int32_t s, const double* A, int32_t lda, double* R, int32
  * bcgs_qr_factor): that fixes whether it keeps the digit store.
  * BCGS_OPT_TC_MIN_ROWS is the row threshold of engine 1 (default 16384).
  * Both engines use the same row partition, so each is deterministic; they
- * differ by rounding.  Returns BCGS_ERR_INVALID_ARG for an unknown option or
- * value.
+ * differ by rounding.
+ * BCGS_OPT_DEBUG_SYNC (diagnostics, default 0): 1 makes the factorization
+ * calls synchronize their stream after every launch and name a failing launch
+ * on stderr.
+ * Returns BCGS_ERR_INVALID_ARG for an unknown option or value.
  * ------------------------------------------------------------------------- */
 #define BCGS_OPT_GRAM_ENGINE 1
 #define BCGS_OPT_TC_MIN_ROWS 2
+#define BCGS_OPT_DEBUG_SYNC 3
 BCGS_API int bcgs_set_option(int option, int64_t value);
 BCGS_API int64_t bcgs_get_option(int option);
 

@@ -88,6 +88,7 @@ class Batch:
     variant: str = "bcgsi+p-2s"
     Qs: list = field(default_factory=list)
     Rs: list = field(default_factory=list)
+    variants: list | None = None  # per-problem variants (default: `variant` for all)
 
     def __post_init__(self):
         import torch
@@ -102,7 +103,8 @@ class Batch:
             R = bcgs.empty_colmajor(n, n, torch.float64, X.device)
             self.Qs.append(Q)
             self.Rs.append(R)
-            self.probs[i] = bcgs.Problem(m, n, s, bcgs.VARIANTS[self.variant], bcgs.PRECISIONS[prec],
+            v = self.variants[i] if self.variants is not None else self.variant
+            self.probs[i] = bcgs.Problem(m, n, s, bcgs.VARIANTS[v], bcgs.PRECISIONS[prec],
                                          X.data_ptr(), bcgs._colmajor_ld(X), Q.data_ptr(),
                                          bcgs._colmajor_ld(Q), R.data_ptr(), bcgs._colmajor_ld(R), 0)
         nb = ctypes.c_size_t(0)

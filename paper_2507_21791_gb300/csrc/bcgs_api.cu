@@ -91,6 +91,17 @@ void make_layout(int64_t m, int32_t n_max, int32_t s, int variant, int precision
   L->total = off;
 }
 
+// True when the byte ranges of two column-major m x n arrays (leading
+// dimensions lda, ldb; element size esz) overlap.  Host-only pointer
+// arithmetic: nothing is read.
+bool overlaps(const void* a, int64_t lda, const void* b, int64_t ldb, int64_t m, int32_t n, size_t esz) {
+  if (a == nullptr || b == nullptr || m < 1 || n < 1) return false;
+  const uintptr_t a0 = reinterpret_cast<uintptr_t>(a), b0 = reinterpret_cast<uintptr_t>(b);
+  const uintptr_t a1 = a0 + ((uintptr_t)(n - 1) * (uintptr_t)lda + (uintptr_t)m) * esz;
+  const uintptr_t b1 = b0 + ((uintptr_t)(n - 1) * (uintptr_t)ldb + (uintptr_t)m) * esz;
+  return a0 < b1 && b0 < a1;
+}
+
 Seg seg(const void* p, int64_t ld, int ncols, int fp32, const unsigned long long* amax = nullptr) {
   Seg g;
   g.p = p;
@@ -176,15 +187,10 @@ struct bcgs_qr_s {
 
 namespace {
 
-// BCGS_DEBUG_SYNC=1 in the environment: synchronize after every launch and name
-// the launch that failed on stderr (diagnostics only; off by default).
-bool debug_sync() {
-  static const bool on = [] {
-    const char* v = getenv("BCGS_DEBUG_SYNC");
-    return v != nullptr && v[0] != '\0' && v[0] != '0';
-  }();
-  return on;
-}
+// bcgs_set_option(BCGS_OPT_DEBUG_SYNC, 1): synchronize after every launch and
+// name the launch that failed on stderr (diagnostics only; off by default).
+std::atomic<int> g_debug_sync{0};
+bool debug_sync() { return g_debug_sync.load() != 0; }
 
 int check(bcgs_qr_s* h, cudaError_t e, const char* what, int line) {
   if (e == cudaSuccess && debug_sync()) e = cudaStreamSynchronize(h->stream);
@@ -766,6 +772,10 @@ int bcgs_set_option(int option, int64_t value) {
       if (value < 1) return BCGS_ERR_INVALID_ARG;
       g_tc_min_rows.store(value);
       return BCGS_OK;
+    case BCGS_OPT_DEBUG_SYNC:
+      if (value < 0 || value > 1) return BCGS_ERR_INVALID_ARG;
+      g_debug_sync.store((int)value);
+      return BCGS_OK;
   }
   return BCGS_ERR_INVALID_ARG;
 }
@@ -774,6 +784,7 @@ int64_t bcgs_get_option(int option) {
   switch (option) {
     case BCGS_OPT_GRAM_ENGINE: return g_engine.load();
     case BCGS_OPT_TC_MIN_ROWS: return g_tc_min_rows.load();
+    case BCGS_OPT_DEBUG_SYNC: return g_debug_sync.load();
   }
   return -1;
 }
@@ -792,6 +803,10 @@ int bcgs_qr_factor(int64_t m, int32_t n, int32_t s, int variant, int precision, 
                    int64_t ldx, void* Q, int64_t ldq, double* R, int32_t ldr, void* workspace,
                    size_t ws_bytes, void* stream) {
   if (X == nullptr || ldx < m) return BCGS_ERR_INVALID_ARG;
+  // in-place factorization (Q overlapping X) is not supported
+  if (precision >= 0 && precision <= 1 &&
+      overlaps(X, ldx, Q, ldq, m, n, precision == BCGS_FP32_STORAGE ? 4 : 8))
+    return BCGS_ERR_INVALID_ARG;
   bcgs_qr_s hs;
   bcgs_qr_s* h = &hs;
   int rc = init_handle(h, m, n, s, variant, precision, Q, ldq, R, ldr, workspace, ws_bytes, stream);
@@ -812,6 +827,9 @@ int bcgs_qr_factor_host(int64_t m, int32_t n, int32_t s, int variant, int precis
                         size_t ws_bytes, void* stream) {
   if (X_host == nullptr || Q_host == nullptr || R_host == nullptr || Xd == nullptr) return BCGS_ERR_INVALID_ARG;
   if (ldxh < m || ldqh < m || ldx < m || ldrh < n) return BCGS_ERR_INVALID_ARG;
+  if (precision >= 0 && precision <= 1 &&
+      overlaps(Xd, ldx, Qd, ldq, m, n, precision == BCGS_FP32_STORAGE ? 4 : 8))
+    return BCGS_ERR_INVALID_ARG;
   bcgs_qr_s hs;
   bcgs_qr_s* h = &hs;
   int rc = init_handle(h, m, n, s, variant, precision, Qd, ldq, Rd, ldr, workspace, ws_bytes, stream);
@@ -1082,6 +1100,13 @@ int bcgs_qr_factor_batched(int32_t count, const bcgs_problem* probs, void* works
   if (rc != BCGS_OK) return rc;
   if (workspace == nullptr || ws_bytes < need || ((uintptr_t)workspace) % 256 != 0)
     return BCGS_ERR_WORKSPACE;
+  // every problem is checked before anything is enqueued
+  for (int i = 0; i < count; ++i) {
+    const bcgs_problem& p = probs[i];
+    if (p.X == nullptr || p.ldx < p.m ||
+        overlaps(p.X, p.ldx, p.Q, p.ldq, p.m, p.n, p.precision == BCGS_FP32_STORAGE ? 4 : 8))
+      return BCGS_ERR_INVALID_ARG;
+  }
   cudaStream_t origin = reinterpret_cast<cudaStream_t>(stream);
   BatchStreams* bs = nullptr;
   rc = batch_streams(&bs);

@@ -33,7 +33,10 @@ double* g_partials_ptr[kMaxDevices] = {nullptr};
 
 // Device address of g_gram_partials on the current device, looked up once per
 // device.  In host code the symbol g_gram_partials names a host-side shadow, not
-// device memory, so it must never be passed to a kernel directly.
+// device memory, so it must never be passed to a kernel directly.  The address
+// is kept for the life of the process: after cudaDeviceReset (or anything else
+// that rebuilds the device's context) it is stale, so the entry point must not be
+// used across such a reset.
 int partials_on_current_device(double** out) {
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return BCGS_ERR_CUDA;
@@ -71,14 +74,17 @@ extern "C" int bcgs_gram_noalloc(int64_t m, int32_t ka, int32_t kb, const double
   d.nb = kb;
   d.m = m;
   gram_partition(m, &d.chunk_rows, &d.nchunks);
-  // Every partial slot of this call is written before it is read, so the array
-  // needs no clearing between calls; sizes beyond its capacity are refused.
+  // Every partial slot of this call is written before it is read (a CTA of the
+  // tensor engine that meets a non-finite column or a wait that runs out writes
+  // NaN into its slots), so the array needs no clearing between calls and a
+  // failure shows as NaN in C, never as an earlier call's sums.  Sizes beyond the
+  // array's capacity are refused.
   if ((size_t)d.nchunks * (size_t)ka * (size_t)kb > kNoAllocPartials) return BCGS_ERR_WORKSPACE;
   double* partials = nullptr;
   const int rc = partials_on_current_device(&partials);
   if (rc != BCGS_OK) return rc;
-  // No status word: a null status pointer makes the kernels skip the check
-  // (the tensor-core engine then writes no partials for a non-finite column).
+  // No status word: a null status pointer makes the kernels skip the check;
+  // non-finite input and a timed-out wait come back as NaN entries of C.
   cudaError_t e;
   if (use_tensor_gram(d)) {
     auto* amax = reinterpret_cast<unsigned long long*>(partials + kNoAllocPartials);

@@ -275,13 +275,17 @@ gram_tc_kernel(GramDesc d, TcCols cm, const unsigned long long* __restrict__ ama
   }
   cp_async_wait_all();
 
-  if (!bad && !timed_out && reader && my_i < ncol_a) {
+  // A CTA that saw a non-finite column or gave up on a wait writes NaN into its
+  // partial slots: a caller without a status word (st == null) then gets NaN
+  // from the reduction, never the sums some earlier call left in those slots.
+  if (reader && my_i < ncol_a) {
     double* out = partial + (size_t)chunk * ((size_t)d.na * ldp) + (size_t)(col0 + my_i) * ldp + jb0;
     const int ea = s_cexp_a[my_i];
+    const bool valid = !bad && !timed_out;
 #pragma unroll
     for (int j = 0; j < kHalf; ++j) {
       const int jj = my_j0 + j;
-      if (jj < nb) out[jj] = unfold(hi[j], lo[j], ea, s_cexp_b[jj]);
+      if (jj < nb) out[jj] = valid ? unfold(hi[j], lo[j], ea, s_cexp_b[jj]) : __longlong_as_double(0x7FF8000000000000LL);
     }
   }
   if (timed_out && tid == 0) set_failure(st, BCGS_ERR_TIMEOUT, d.block);

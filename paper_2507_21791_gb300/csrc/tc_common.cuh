@@ -1,10 +1,17 @@
-// Device helpers shared by the tensor-core kernels (gram_tc.cu, proj_tc.cu):
-// tcgen05 descriptors and MMA issue, bounded mbarrier polling, asynchronous
-// copies, and the exact splitting of an FP64 value into eight 8-bit digits
-// relative to an exponent (error-free splitting in the manner of Ozaki, Ogita,
-// Oishi and Rump, Numer. Algorithms 59, 2012).
+// Device helpers shared by the tensor-core kernels (gram_tc.cu, proj_tc.cu,
+// qstore.cu, gram_store.cu): tcgen05 descriptors and MMA issue, bounded mbarrier
+// polling, asynchronous copies, and the exact splitting of an FP64 value into
+// eight 8-bit digits relative to an exponent (error-free splitting in the manner
+// of Ozaki, Ogita, Oishi and Rump, Numer. Algorithms 59, 2012).
 //
-// Digits: with E the exponent of the line's maximum (|a| < 2^E),
+// Two digit forms live here:
+//   * sign-magnitude digits in bf16 (this first part): used by the kernels that
+//     split their operands on the fly, gram_tc.cu and proj_tc.cu;
+//   * balanced digits in f16 (the second part, "balanced digits" below): used by
+//     the resident digit store of Q and the kernels that read it, qstore.cu
+//     (split and projection) and gram_store.cu.
+//
+// Sign-magnitude digits: with E the exponent of the line's maximum (|a| < 2^E),
 // a = sign N 2^(E - 63) with the integer N < 2^63 (truncated), and the digits
 // are the bytes of N: N = sum_t d_t 2^(56 - 8t), t = 0..7 (d_0 < 128).  A
 // signed digit is an integer of magnitude at most 255, exact in bf16.  The

@@ -108,10 +108,51 @@ def test_bad_enums_and_null_pointers_rejected():
                                    1 << 20, None) == 1
     assert lib.bcgs_qr_factor_host(100, 16, 8, 1, 0, 8, 99, 8, 100, 8, 16, 8, 100, 8, 100, 8, 16, 256,
                                    1 << 20, None) == 1
+    X, Q = 1 << 40, 1 << 41  # distinct (never dereferenced) device addresses
     # misaligned workspace
-    assert lib.bcgs_qr_factor(100, 16, 8, 1, 0, 8, 100, 16, 100, 32, 16, 257, 1 << 20, None) == 5
+    assert lib.bcgs_qr_factor(100, 16, 8, 1, 0, X, 100, Q, 100, 32, 16, 257, 1 << 20, None) == 5
     # too small workspace
-    assert lib.bcgs_qr_factor(100, 16, 8, 1, 0, 8, 100, 16, 100, 32, 16, 256, 1024, None) == 5
+    assert lib.bcgs_qr_factor(100, 16, 8, 1, 0, X, 100, Q, 100, 32, 16, 256, 1024, None) == 5
+
+
+@pytest.mark.parametrize("precision,esz", [(0, 8), (1, 4)])
+def test_overlapping_x_and_q_rejected_without_a_gpu(precision, esz):
+    """In-place factorization is not supported: X and Q whose memory overlaps
+    are rejected with BCGS_ERR_INVALID_ARG before anything is enqueued (the
+    check is host-side pointer arithmetic; the pointers are never read)."""
+    ensure_library()
+    from paper_2507_21791_gb300 import bcgs
+
+    lib = bcgs.load_library()
+    m, n, s = 100, 16, 8
+    X = 1 << 40
+    last = X + ((n - 1) * m + m) * esz  # one past the last byte of X
+    for Q in (X, X + 8 * esz, last - esz, X - 3 * m * esz):
+        assert lib.bcgs_qr_factor(m, n, s, 1, precision, X, m, Q, m, 32, n, 256, 1 << 20, None) == 1
+        assert lib.bcgs_qr_factor_host(m, n, s, 1, precision, 8, m, 8, m, 8, n, X, m, Q, m, 32, n, 256,
+                                       1 << 20, None) == 1
+    # touching but not overlapping: the call goes on to the next check (a too
+    # small workspace, BCGS_ERR_WORKSPACE), so the test is not over-eager
+    assert lib.bcgs_qr_factor(m, n, s, 1, precision, X, m, last, m, 32, n, 256, 1024, None) == 5
+    assert lib.bcgs_qr_factor(m, n, s, 1, precision, X, m, X - (n * m) * esz, m, 32, n, 256, 1024, None) == 5
+    # batched: one overlapping problem rejects the whole call
+    probs = (bcgs.Problem * 2)()
+    probs[0] = bcgs.Problem(m, n, s, 1, precision, X, m, 1 << 42, m, 32, n, 0)
+    probs[1] = bcgs.Problem(m, n, s, 1, precision, 1 << 43, m, (1 << 43) + 8, m, 32, n, 0)
+    need = ctypes.c_size_t(0)
+    assert lib.bcgs_qr_batched_workspace_size(2, probs, ctypes.byref(need)) == 0
+    assert lib.bcgs_qr_factor_batched(2, probs, 1 << 44, need.value, None) == 1
+
+
+def test_debug_sync_option():
+    ensure_library()
+    from paper_2507_21791_gb300 import bcgs
+
+    lib = bcgs.load_library()
+    assert lib.bcgs_get_option(3) == 0
+    assert lib.bcgs_set_option(3, 2) == 1
+    assert lib.bcgs_set_option(3, 1) == 0 and lib.bcgs_get_option(3) == 1
+    assert lib.bcgs_set_option(3, 0) == 0 and lib.bcgs_get_option(3) == 0
 
 
 @pytest.mark.parametrize("m,n,s", [(100, 30, 8), (100, 5, 8), (1000, 17, 16)])

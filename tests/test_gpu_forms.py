@@ -1,10 +1,13 @@
 """The batched and served forms on the GPU.
 
 Batched: one bcgs_qr_factor_batched call (and its CUDA-graph replay) over uneven
-problems gives, for every problem, the same bits as bcgs_qr_factor alone and
-meets the FP64 gates.  Served: each basis's Q and R are the same alone and in
-the mix (bitwise: the reduction order depends only on the problem's shape),
-and every admitted request meets the gates.
+problems gives, for every problem, the same bits as bcgs_qr_factor alone, and
+every problem's Q and R agree with the oracle's entry by entry.  Served: each
+basis's Q and R are the same alone and in the mix (bitwise: the reduction order
+depends only on the problem's shape), and every admitted request agrees with
+the oracle.  Oracle agreement is the forward bound of the variant tests:
+    residual <= 1e-13, LOO <= 1e-12,
+    ||R - R_oracle||_F / ||R_oracle||_F <= 10 n kappa u,  max |Q - Q_oracle| <= 10 n kappa u.
 """
 import numpy as np
 import pytest
@@ -12,7 +15,19 @@ import pytest
 import oracle
 from paper_2507_21791_gb300 import synth
 
+U64 = np.finfo(np.float64).eps / 2
 pytestmark = pytest.mark.gpu
+
+
+def check_oracle(X, Q, R, s, variant):
+    """The gates and the forward bound against the oracle's factorization of X."""
+    n = X.shape[1]
+    Qo, Ro = oracle.factor(X, s, variant)
+    tol = 10 * n * oracle.kappa(Ro) * U64
+    assert oracle.residual(X, Q, R) <= 1e-13
+    assert oracle.loo(Q) <= 1e-12
+    assert np.linalg.norm(R - Ro) / np.linalg.norm(Ro) <= tol
+    assert np.max(np.abs(Q - Qo)) <= tol
 
 
 def test_batched_matches_single_and_graph_replay(cuda):
@@ -39,8 +54,7 @@ def test_batched_matches_single_and_graph_replay(cuda):
         Q, R, code, _ = cuda.factor(X, s, "bcgsi+p-2s")
         assert code == 0
         assert torch.equal(Q, b.Qs[i]) and torch.equal(R, b.Rs[i])
-        Qh, Rh = Q.cpu().numpy(), R.cpu().numpy()
-        assert oracle.loo(Qh) <= 1e-12 and oracle.residual(Xh[i], Qh, Rh) <= 1e-13
+        check_oracle(Xh[i], b.Qs[i].cpu().numpy(), b.Rs[i].cpu().numpy(), s, "bcgsi+p-2s")
     for q in b.Qs:
         q.zero_()
     b.capture()
@@ -50,6 +64,36 @@ def test_batched_matches_single_and_graph_replay(cuda):
     assert codes == [0] * len(Xs)
     for (q0, r0), q, r in zip(first, b.Qs, b.Rs):
         assert torch.equal(q0, q) and torch.equal(r0, r)
+
+
+def test_batched_store_path_every_variant_against_oracle(cuda):
+    """Instances of m >= 16384 rows, n = 128 and s in {8, 16}: the batch runs the
+    digit-store kernels (tensor-core Gram and projection).  Mixed variants in one
+    batch; each result is bitwise the single call's and within the oracle bound."""
+    import torch
+
+    from paper_2507_21791_gb300.batched import Batch
+
+    rng = np.random.default_rng(11)
+    plan = [("bcgsi+p-1s", 16, 1e4), ("bcgsi+p-1s", 8, 1e5), ("bcgs-pipi+", 16, 1e4),
+            ("bcgsi+p-2s", 16, 1e7), ("bcgsi+p-2s", 8, 1e3), ("bcgsi+", 16, 1e6)]
+    Xs, Xh, ss, vs = [], [], [], []
+    for i, (v, s, kappa) in enumerate(plan):
+        m = int(2 ** rng.uniform(14, 16.2))
+        X = synth.make_matrix_np(m, 128, kappa, seed=300 + i)
+        Xh.append(X)
+        Xs.append(cuda.to_device_colmajor(X))
+        ss.append(s)
+        vs.append(v)
+    b = Batch(Xs, ss, variants=vs)
+    b.enqueue()
+    codes, _ = b.status()
+    assert codes == [0] * len(Xs)
+    for i in range(len(Xs)):
+        Q, R, code, _ = cuda.factor(Xs[i], ss[i], vs[i])
+        assert code == 0
+        assert torch.equal(Q, b.Qs[i]) and torch.equal(R, b.Rs[i])
+        check_oracle(Xh[i], b.Qs[i].cpu().numpy(), b.Rs[i].cpu().numpy(), ss[i], vs[i])
 
 
 def _serve(cuda, sources, meta, rids, arrivals, budget=8e9, modes=None):
@@ -85,8 +129,7 @@ def test_served_results_are_the_same_alone_and_in_the_mix(cuda):
     for r, req in done.items():
         m, n, s = meta[r]
         X = sources[r][:m, :n].cpu().numpy()
-        Q, R = req.result[0].cpu().numpy(), req.result[1].cpu().numpy()
-        assert oracle.loo(Q) <= 1e-12 and oracle.residual(X, Q, R) <= 1e-13
+        check_oracle(X, req.result[0].cpu().numpy(), req.result[1].cpu().numpy(), s, "bcgsi+p-2s")
 
 
 def test_server_respects_the_budget(cuda):
@@ -117,7 +160,24 @@ def test_eager_and_lazy_finalize_give_their_variants_results(cuda):
     assert set(rep["by_finalize"]) == {"eager", "lazy"}
     for r, req in done.items():
         m, n, s = meta[r]
-        Q, R, code, _ = cuda.factor(sources[r][:m, :n], s, "bcgsi+" if modes[r] == "eager" else "bcgsi+p-2s")
+        variant = "bcgsi+" if modes[r] == "eager" else "bcgsi+p-2s"
+        Q, R, code, _ = cuda.factor(sources[r][:m, :n], s, variant)
         assert code == 0
         assert torch.equal(Q, req.result[0]) and torch.equal(R, req.result[1])
         assert len(req.final_latencies) == req.q
+        check_oracle(sources[r][:m, :n].cpu().numpy(), Q.cpu().numpy(), R.cpu().numpy(), s, variant)
+
+
+def test_served_store_path_against_oracle(cuda):
+    """Bases of 2^14 .. 2^16 rows (the digit-store kernels) served together; every
+    result within the oracle bound."""
+    from paper_2507_21791_gb300.serving import draw_sources
+
+    sources, meta = draw_sources(5, seed=9, m_exp=(14, 16), p_range=(2, 5), s_choices=(8, 16),
+                                 kappa_exp=(1, 6))
+    done, rep = _serve(cuda, sources, meta, list(range(5)), [0.0] * 5)
+    assert rep["requests_done"] == 5 and rep["failed"] == 0
+    for r, req in done.items():
+        m, n, s = meta[r]
+        X = sources[r][:m, :n].cpu().numpy()
+        check_oracle(X, req.result[0].cpu().numpy(), req.result[1].cpu().numpy(), s, "bcgsi+p-2s")

@@ -314,7 +314,7 @@ def test_breakdowns(variant):
     with pytest.raises(oracle.Breakdown) as e:
         oracle.factor(Xn, 2, variant)
     assert e.value.kind == "nonfinite"
-    # n mod s != 0 is a ragged last block (R9); m < n is rejected either way
+    # n mod s != 0 is a ragged last block (taken by one eager step); m < n is rejected either way
     with pytest.raises(ValueError):
         oracle.factor(X[:5], 3, variant)
     with pytest.raises(ValueError):
