@@ -9,6 +9,7 @@ reference, special cases, invariants); no function is "parity unpinned".
 """
 from .bcgs import (Breakdown, householder_qr, tsqr, chol, solve_right_upper,  # noqa: F401
                    solve_left_upper_t, delayed_projection, gram, project_normalize,
-                   bcgsi_plus, bcgsi_plus_p_1s, bcgsi_plus_p_2s, bcgs_pipi_plus, eager_step, factor,
+                   bcgsi_plus, bcgsi_plus_p_1s, bcgsi_plus_p_2s, bcgs_pipi_plus, bcgsi_plus_1s,
+                   eager_step, factor,
                    VARIANTS, EAGER_FAMILY)
 from .metrics import loo, loo_from_gram, residual, kappa  # noqa: F401

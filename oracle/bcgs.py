@@ -28,7 +28,8 @@ import numpy as np
 __all__ = [
     "Breakdown", "householder_qr", "tsqr", "chol", "solve_right_upper",
     "solve_left_upper_t", "delayed_projection", "gram", "project_normalize",
-    "bcgsi_plus", "bcgsi_plus_p_1s", "bcgsi_plus_p_2s", "bcgs_pipi_plus", "eager_step", "factor",
+    "bcgsi_plus", "bcgsi_plus_p_1s", "bcgsi_plus_p_2s", "bcgs_pipi_plus", "bcgsi_plus_1s", "eager_step",
+    "factor",
     "VARIANTS", "EAGER_FAMILY",
 ]
 
@@ -388,19 +389,85 @@ def bcgs_pipi_plus(X: np.ndarray, s: int):
     return Q, R
 
 
+def bcgsi_plus_1s(X: np.ndarray, s: int):
+    """BCGSI+1s (also called BCGSI+LS), Sec. 2's one-sync subsection: delayed
+    normalization as in Alg. 2, but the first intraorthogonalization is not
+    done at all, so the Pythagorean Cholesky line of Alg. 2's loop (and of its
+    startup) is dropped: S_{k+1,k+1} = I, U_{k+1} = X_{k+1} - Q_k S_{1:k,k+1}
+    and T is never formed.  Table 1: O(u) kappa^2 loss of orthogonality,
+    assuming O(u) kappa^3 <= 1.  The paper prints no pseudocode; this is Alg. 2
+    with that line removed:
+        [Q_1, R_11] = TSQR(X_1);  S_12 = Q_1^T X_2;  U_2 = X_2 - Q_1 S_12
+        sync [Q_1 U_2]^T [U_2 X_3];  Y_22 = chol(Omega_2 - Y_12^T Y_12)
+        Q_2 = (U_2 - Q_1 Y_12) Y_22^{-1};  R_12 = S_12 + Y_12;  R_22 = Y_22
+        for k = 2..q-1:
+            S_{1:k,k+1} by eq. (1);  U_{k+1} = X_{k+1} - Q_k S_{1:k,k+1}
+            sync [Q_k U_{k+1}]^T [U_{k+1} X_{k+2}]  (no X_{k+2} at k = q-1)
+            Y_{k+1,k+1} = chol(Omega_{k+1} - Y^T Y);  Q_{k+1} = (U_{k+1} - Q_k Y) Y_{k+1,k+1}^{-1}
+            R_{1:k,k+1} = S_{1:k,k+1} + Y_{1:k,k+1};  R_{k+1,k+1} = Y_{k+1,k+1}
+    (Alg. 2's R update with S_{k+1,k+1} = I.)
+    """
+    X, m, n, q = _check(X, s)
+    Q = np.zeros((m, n))
+    R = np.zeros((n, n))
+    blk = lambda k: slice((k - 1) * s, k * s)
+    upto = lambda k: slice(0, k * s)
+    Xb = lambda k: X[:, blk(k)]
+
+    Q1, R11 = tsqr(Xb(1), 1)
+    Q[:, blk(1)], R[blk(1), blk(1)] = Q1, R11
+    if q == 1:
+        return Q, R
+    S12 = gram([Q1], [Xb(2)])
+    U = Xb(2) - Q1 @ S12                                             # U_2 (not normalized)
+
+    if q >= 3:
+        G = gram([Q1, U], [U, Xb(3)])
+        Y12, Z1, Om, P = G[:s, :s], G[:s, s:], G[s:, :s], G[s:, s:]
+    else:
+        G = gram([Q1, U], [U])
+        Y12, Om = G[:s], G[s:]
+        Z1 = P = None
+    Ykk = chol(Om - Y12.T @ Y12, 2)
+    Q[:, blk(2)] = project_normalize(U, Q1, Y12, Ykk)
+    R[blk(1), blk(2)] = S12 + Y12
+    R[blk(2), blk(2)] = Ykk
+    Yprev, Zprev = Y12, Z1
+
+    for k in range(2, q):
+        S = np.vstack([Zprev, delayed_projection(Ykk, P, Yprev, Zprev)])
+        Qk = Q[:, upto(k)]
+        U = Xb(k + 1) - Qk @ S                                       # U_{k+1}
+        if k < q - 1:
+            G = gram([Qk, U], [U, Xb(k + 2)])
+            Y, Z, Om, P = G[:k * s, :s], G[:k * s, s:], G[k * s:, :s], G[k * s:, s:]
+        else:
+            G = gram([Qk, U], [U])
+            Y, Om = G[:k * s], G[k * s:]
+            Z = P = None
+        Yd = chol(Om - Y.T @ Y, k + 1)
+        Q[:, blk(k + 1)] = project_normalize(U, Qk, Y, Yd)
+        R[upto(k), blk(k + 1)] = S + Y
+        R[blk(k + 1), blk(k + 1)] = Yd
+        Ykk, Yprev, Zprev = Yd, Y, Z
+    return Q, R
+
+
 VARIANTS = {
     "bcgsi+": bcgsi_plus,
     "bcgsi+p-1s": bcgsi_plus_p_1s,
     "bcgsi+p-2s": bcgsi_plus_p_2s,
     "bcgs-pipi+": bcgs_pipi_plus,
+    "bcgsi+1s": bcgsi_plus_1s,
 }
 
 
 # The variant whose step finalizes a block at once, in the stability range of
 # each variant (Table 1): BCGSI+ for BCGSI+ and BCGSI+P-2S, BCGS-PIPI+ for
-# BCGSI+P-1S and BCGS-PIPI+.
+# BCGSI+P-1S and BCGS-PIPI+, and BCGS-PIPI+ for BCGSI+1s (its range,
+# O(u) kappa^2 <= 1, contains BCGSI+1s's O(u) kappa^3 <= 1).
 EAGER_FAMILY = {"bcgsi+": "bcgsi+", "bcgsi+p-2s": "bcgsi+", "bcgsi+p-1s": "bcgs-pipi+",
-                "bcgs-pipi+": "bcgs-pipi+"}
+                "bcgs-pipi+": "bcgs-pipi+", "bcgsi+1s": "bcgs-pipi+"}
 
 
 def eager_step(Qk: np.ndarray, Xn: np.ndarray, family: str, block: int):
@@ -430,7 +497,8 @@ def eager_step(Qk: np.ndarray, Xn: np.ndarray, family: str, block: int):
 
 
 def factor(X: np.ndarray, s: int, variant: str):
-    """Dispatch by variant name ("bcgsi+", "bcgsi+p-1s", "bcgsi+p-2s", "bcgs-pipi+").
+    """Dispatch by variant name ("bcgsi+", "bcgsi+p-1s", "bcgsi+p-2s", "bcgs-pipi+",
+    "bcgsi+1s").
 
     n need not be a multiple of s (the paper assumes it is).  Reading for a
     ragged last block of r = n mod s columns: the first n - r columns are

@@ -197,15 +197,16 @@ def test_cross_variant_agreement(kappa):
 def test_invariants(variant, kappa):
     m, n, s = 3000, 64, 8
     X = synth.make_matrix_np(m, n, kappa, seed=19)
-    if variant in ("bcgsi+p-1s", "bcgs-pipi+") and kappa >= 1e8:
-        pytest.skip("outside Table 1's O(u) kappa^2 <= 1 range")
+    if variant in ("bcgsi+p-1s", "bcgs-pipi+", "bcgsi+1s") and kappa >= 1e8:
+        pytest.skip("outside Table 1's O(u) kappa^2 <= 1 (O(u) kappa^3 <= 1 for BCGSI+1s) range")
     Q, R = oracle.factor(X, s, variant)
     assert np.array_equal(np.tril(R, -1), np.zeros_like(R))
     assert np.all(np.diag(R) > 0)
     nx2 = np.linalg.norm(X, 2) ** 2
     assert np.linalg.norm(X.T @ X - R.T @ R, 2) / nx2 < 100 * n * U64
     assert oracle.residual(X, Q, R) < 1e-14
-    assert oracle.loo(Q) < 1e-13
+    # Table 1: O(u) loss of orthogonality, O(u) kappa^2 for BCGSI+1s
+    assert oracle.loo(Q) < (10 * n * U64 * kappa ** 2 if variant == "bcgsi+1s" else 1e-13)
 
 
 def test_pythagorean_identity():
@@ -252,7 +253,7 @@ def test_variants_use_eq1(monkeypatch):
         return good(*a)
     monkeypatch.setattr(ob, "delayed_projection", counting)
     X = synth.make_matrix_np(200, 20, 1e2, seed=71)
-    for v in ("bcgsi+p-1s", "bcgsi+p-2s"):
+    for v in ("bcgsi+p-1s", "bcgsi+p-2s", "bcgsi+1s"):
         calls.clear()
         oracle.factor(X, 4, v)
         assert len(calls) == 5 - 2  # k = 2..q-1
@@ -300,6 +301,54 @@ def test_table1_loo_ordering():
 
 
 # ---------------------------------------------------------------- degenerate inputs
+
+def test_bcgsi_plus_1s_has_no_first_pythagorean_cholesky():
+    """BCGSI+1s drops Alg. 2's first Cholesky line (Sec. 2): U_{k+1} = X_{k+1} -
+    Q_k S is formed explicitly and T - S^T S never is.  At kappa = 1e10, where
+    O(u) kappa^2 > 1 and BCGSI+P-1S's Pythagorean Cholesky of T - S^T S breaks
+    down (Table 1), BCGSI+1s still completes with a backward-stable R; a version
+    that kept the dropped line would break down like BCGSI+P-1S."""
+    X = synth.make_matrix_np(3000, 64, 1e10, seed=47)
+    with pytest.raises(oracle.Breakdown) as e:
+        oracle.factor(X, 8, "bcgsi+p-1s")
+    assert e.value.kind == "not_spd"
+    Q, R = oracle.factor(X, 8, "bcgsi+1s")
+    nx2 = np.linalg.norm(X, 2) ** 2
+    assert np.linalg.norm(X.T @ X - R.T @ R, 2) / nx2 < 100 * 64 * U64
+    assert oracle.residual(X, Q, R) < 1e-14
+    assert np.all(np.diag(R) > 0)
+
+
+def test_bcgsi_plus_1s_loss_of_orthogonality_grows_with_kappa():
+    """Table 1: BCGSI+1s's loss of orthogonality is O(u) kappa^2 (bounded by it
+    and growing with kappa), BCGSI+P-1S's stays O(u) over the same range."""
+    for seed in (19, 47):
+        loo = {}
+        for kappa in (1e2, 1e8):
+            X = synth.make_matrix_np(3000, 64, kappa, seed=seed)
+            loo[kappa] = oracle.loo(oracle.factor(X, 8, "bcgsi+1s")[0])
+            assert loo[kappa] <= 10 * 64 * U64 * kappa ** 2
+            assert oracle.loo(oracle.factor(X, 8, "bcgsi+p-1s")[0]) < 1e-14
+        assert loo[1e8] > 10 * loo[1e2]
+
+
+def test_bcgsi_plus_1s_r_has_identity_first_normalization():
+    """With S_{k+1,k+1} = I the R update of Alg. 2 reads R_{1:k,k+1} = S + Y and
+    R_{k+1,k+1} = Y_{k+1,k+1}: for q = 2 blocks the factors are TSQR(X_1),
+    S_12 = Q_1^T X_2, U_2 = X_2 - Q_1 S_12, [Y_12; Omega] = [Q_1 U_2]^T U_2 and the
+    Cholesky of Omega - Y^T Y, written out here from those definitions."""
+    X = synth.make_matrix_np(500, 8, 1e3, seed=83)
+    Q1, R11 = oracle.householder_qr(X[:, :4])
+    S12 = Q1.T @ X[:, 4:]
+    U2 = X[:, 4:] - Q1 @ S12
+    Y12 = Q1.T @ U2
+    L = np.linalg.cholesky(U2.T @ U2 - Y12.T @ Y12)  # lower, L L^T
+    Y22 = L.T
+    Q, R = oracle.factor(X, 4, "bcgsi+1s")
+    assert np.allclose(R[:4, :4], R11, rtol=0, atol=1e-13 * np.abs(R11).max())
+    assert np.abs(R[:4, 4:] - (S12 + Y12)).max() < 1e-13 * np.abs(R).max()
+    assert np.abs(R[4:, 4:] - Y22).max() < 1e-12 * np.abs(R).max()
+
 
 @pytest.mark.parametrize("variant", VARIANTS)
 def test_breakdowns(variant):
@@ -373,9 +422,12 @@ def test_mutation_wrong_sign_in_chol_is_caught(monkeypatch):
     monkeypatch.setattr(ob, "chol", bad_chol)
     assert np.abs(ob.chol(R0.T @ R0) - R0).max() > 1e-3
     # BCGSI+P-1S's and BCGS-PIPI+'s S_{k+1,k+1} = chol(T - S^T S) is far from
-    # identity; in BCGSI+P-2S chol only factors Omega - Y^T Y ~ I, and BCGSI+ has no chol.
+    # identity, and BCGSI+1s's R_{k+1,k+1} = Y_{k+1,k+1} = chol(Omega - Y^T Y) of
+    # its unnormalized U; in BCGSI+P-2S chol only factors Omega - Y^T Y ~ I, and
+    # BCGSI+ has no chol.
     assert _recovery_error("bcgsi+p-1s") > 1e-6
     assert _recovery_error("bcgs-pipi+") > 1e-6
+    assert _recovery_error("bcgsi+1s") > 1e-6
 
 
 def test_mutation_missing_sign_normalization_is_caught(monkeypatch):
@@ -410,7 +462,8 @@ def test_ragged_last_block_matches_lapack(variant, m, n, s):
     assert Q.shape == (m, n) and R.shape == (n, n)
     Rl = _lapack_r(X)
     assert np.linalg.norm(R - Rl) / np.linalg.norm(Rl) <= 10 * n * 1e3 * U64
-    assert oracle.loo(Q) <= 1e-13 and oracle.residual(X, Q, R) <= 1e-14
+    loo_gate = 10 * n * U64 * 1e3 ** 2 if variant == "bcgsi+1s" else 1e-13  # Table 1
+    assert oracle.loo(Q) <= loo_gate and oracle.residual(X, Q, R) <= 1e-14
     assert np.array_equal(np.tril(R, -1), np.zeros_like(R)) and np.all(np.diag(R) > 0)
 
 
@@ -435,7 +488,8 @@ def test_eager_step_families():
     Qn, Rt, Rd = oracle.eager_step(Q1, X[:, 8:], "bcgsi+", 2)
     assert np.array_equal(Q[:, 8:], Qn) and np.array_equal(R[:8, 8:], Rt) and np.array_equal(R[8:, 8:], Rd)
     assert oracle.EAGER_FAMILY == {"bcgsi+": "bcgsi+", "bcgsi+p-2s": "bcgsi+",
-                                   "bcgsi+p-1s": "bcgs-pipi+", "bcgs-pipi+": "bcgs-pipi+"}
+                                   "bcgsi+p-1s": "bcgs-pipi+", "bcgs-pipi+": "bcgs-pipi+",
+                                   "bcgsi+1s": "bcgs-pipi+"}
 
 
 def test_mutation_lost_coupling_block_in_the_ragged_step_is_caught(monkeypatch):
