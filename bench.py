@@ -305,7 +305,7 @@ def main_ours(args):
 
     compare = {}
     if not args.no_compare:
-        for v in ("bcgsi+", "bcgsi+p-2s", "bcgs-pipi+"):
+        for v in ("bcgsi+", "bcgsi+p-2s", "bcgs-pipi+", "bcgsi+1s"):
             r = run_variant(v)
             compare[v] = {"ms": r["ms"], "loo": r["loo"], "residual": r["residual"]}
             del r
@@ -313,7 +313,7 @@ def main_ours(args):
     speedup = None
     if "bcgsi+" in compare:
         speedup = {v: compare["bcgsi+"]["ms"] / compare[v]["ms"]
-                   for v in ("bcgsi+p-1s", "bcgsi+p-2s", "bcgs-pipi+")}
+                   for v in ("bcgsi+p-1s", "bcgsi+p-2s", "bcgs-pipi+", "bcgsi+1s")}
 
     forms = None
     if not args.no_forms and world == 1:
@@ -445,6 +445,7 @@ TABLE2_64_NODES = {
     "bcgsi+p-2s": {1: 1.3, 2: 2.6, 4: 5.2, 8: 10.2, 16: 15.9},
     "bcgsi+p-1s": {1: 2.8, 2: 5.4, 4: 10.8, 8: 20.0, 16: 37.5},
     "bcgs-pipi+": {1: 1.6, 2: 3.0, 4: 5.9, 8: 11.7, 16: 22.7},
+    "bcgsi+1s": {1: 2.9, 2: 5.8, 4: 10.6, 8: 21.2, 16: 37.8},
     "bcgsi+": {1: 1.0, 2: 1.4, 4: 2.7, 8: 5.4, 16: 8.8},
 }
 
@@ -465,7 +466,7 @@ def bench_small(args, dev, stream):
     Q = bcgs.empty_colmajor(m, n, torch.float64, dev)
     R = bcgs.empty_colmajor(n, n, torch.float64, dev)
     out = {}
-    for v in ("bcgsi+", "bcgsi+p-2s", "bcgsi+p-1s", "bcgs-pipi+"):
+    for v in ("bcgsi+", "bcgsi+p-2s", "bcgsi+p-1s", "bcgs-pipi+", "bcgsi+1s"):
         ws = torch.empty(bcgs.workspace_size(m, n, s, v), dtype=torch.uint8, device=dev)
 
         def run():

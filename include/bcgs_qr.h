@@ -13,6 +13,12 @@
  *   BCGS_BCGS_PIPI_PLUS   BCGS-PIPI+ (Alg. 1: both passes normalized by the
  *                         Pythagorean Cholesky, 2 synchronizations per block;
  *                         O(u) loss of orthogonality only while O(u) kappa^2 <= 1)
+ *   BCGS_BCGSI_PLUS_1S    BCGSI+1s, also called BCGSI+LS (Sec. 2, one-sync
+ *                         subsection; Table 1): Alg. 2 without its first
+ *                         Cholesky line, so the first pass is not normalized
+ *                         (S_{k+1,k+1} = I, no T); 1 synchronization per block,
+ *                         O(u) kappa^2 loss of orthogonality while
+ *                         O(u) kappa^3 <= 1
  * A synchronization point of the paper (one MPI_Allreduce, Sec. 3) is here one
  * streaming pass over HBM that ends in a deterministic grid-wide reduction.
  *
@@ -72,7 +78,8 @@ typedef enum {
   BCGS_BCGSI_PLUS = 0,
   BCGS_BCGSI_PLUS_P_1S = 1,
   BCGS_BCGSI_PLUS_P_2S = 2,
-  BCGS_BCGS_PIPI_PLUS = 3
+  BCGS_BCGS_PIPI_PLUS = 3,
+  BCGS_BCGSI_PLUS_1S = 4
 } bcgs_variant;
 
 typedef enum { BCGS_FP64 = 0, BCGS_FP32_STORAGE = 1 } bcgs_precision;

@@ -150,6 +150,6 @@ def alg_bytes(m: int, n: int, s: int, variant: str, b: int = 8) -> float:
     (1 per block for BCGSI+P-1S, 2 for -2S, 4 for BCGSI+ and BCGS-PIPI+) plus the
     block passes."""
     q = n // s
-    qpasses = {"bcgsi+p-1s": 1, "bcgsi+p-2s": 2, "bcgsi+": 4, "bcgs-pipi+": 4}[variant]
-    bpasses = {"bcgsi+p-1s": 5, "bcgsi+p-2s": 8, "bcgsi+": 10, "bcgs-pipi+": 6}[variant]
+    qpasses = {"bcgsi+p-1s": 1, "bcgsi+p-2s": 2, "bcgsi+": 4, "bcgs-pipi+": 4, "bcgsi+1s": 1}[variant]
+    bpasses = {"bcgsi+p-1s": 5, "bcgsi+p-2s": 8, "bcgsi+": 10, "bcgs-pipi+": 6, "bcgsi+1s": 5}[variant]
     return b * m * s * q * (q - 1) / 2 * qpasses + bpasses * b * m * n

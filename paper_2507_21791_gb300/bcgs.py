@@ -14,7 +14,7 @@ from dataclasses import dataclass
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libbcgs_qr.so")
 
-VARIANTS = {"bcgsi+": 0, "bcgsi+p-1s": 1, "bcgsi+p-2s": 2, "bcgs-pipi+": 3}
+VARIANTS = {"bcgsi+": 0, "bcgsi+p-1s": 1, "bcgsi+p-2s": 2, "bcgs-pipi+": 3, "bcgsi+1s": 4}
 PRECISIONS = {"fp64": 0, "fp32": 1}
 STATUS = {
     0: "ok", 1: "invalid_arg", 2: "not_spd", 3: "rank_deficient", 4: "nonfinite",

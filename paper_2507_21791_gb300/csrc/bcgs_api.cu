@@ -67,8 +67,9 @@ void make_layout(int64_t m, int32_t n_max, int32_t s, int variant, int precision
   L->ldg = n_max;
   L->G = take((size_t)n_max * 2 * s * sizeof(double));
   L->G2 = take((size_t)n_max * 2 * s * sizeof(double));
-  // (c + s) x 2s coefficients of the paired projection (BCGSI+P-1S / -2S)
-  const bool paired = variant == BCGS_BCGSI_PLUS_P_1S || variant == BCGS_BCGSI_PLUS_P_2S;
+  // (c + s) x 2s coefficients of the paired projection (BCGSI+P-1S / -2S, BCGSI+1s)
+  const bool paired = variant == BCGS_BCGSI_PLUS_P_1S || variant == BCGS_BCGSI_PLUS_P_2S ||
+                      variant == BCGS_BCGSI_PLUS_1S;
   L->Bp = paired ? take((size_t)n_max * 2 * s * sizeof(double)) : off;
   L->partial = take(gram_partial_doubles(m, n_max, 2 * s) * sizeof(double));
   L->amax = take(((size_t)n_max + 4 * (size_t)s) * sizeof(unsigned long long));
@@ -78,7 +79,7 @@ void make_layout(int64_t m, int32_t n_max, int32_t s, int variant, int precision
   L->rowmaxQ = take((size_t)m * sizeof(unsigned long long));
   L->ldu = round_up(m, 64);
   L->U = take((size_t)L->ldu * s * esz);
-  // the projected block TSQR reads (no TSQR after block 1 under 1S and PIPI+)
+  // the projected block TSQR reads (no TSQR after block 1 under 1S, PIPI+ and 1s)
   const bool tsqr_in = variant == BCGS_BCGSI_PLUS || variant == BCGS_BCGSI_PLUS_P_2S;
   L->V = tsqr_in ? take((size_t)L->ldu * s * esz) : off;
   tsqr_plan(m, s, &L->tp);
@@ -171,7 +172,9 @@ struct bcgs_qr_s {
   MaxOut Qmax_at(int col0) {
     return MaxOut{sgram ? nullptr : amaxQ() + col0, L.store ? nullptr : rowmaxQ()};
   }
-  bool delayed() const { return variant == BCGS_BCGSI_PLUS_P_1S || variant == BCGS_BCGSI_PLUS_P_2S; }
+  bool delayed() const {
+    return variant == BCGS_BCGSI_PLUS_P_1S || variant == BCGS_BCGSI_PLUS_P_2S || variant == BCGS_BCGSI_PLUS_1S;
+  }
   // width of block column j (1-based): s, or the ragged rest of n_max
   int width(int j) const { return (int)((int64_t)j * s <= n_max ? s : n_max - (int64_t)(j - 1) * s); }
   // maxima to keep when writing block k of Q, or U: the column maxima feed the
@@ -377,12 +380,15 @@ int finish_p(bcgs_qr_s* h) {
   return BCGS_OK;
 }
 
-// One block step of BCGSI+P-1S (Alg. 2) or BCGSI+P-2S for block j >= 3
-// (k = j - 1): the synchronization of block k, the tail, Q_k and U_{k+1}.
+// One block step of BCGSI+P-1S (Alg. 2), BCGSI+P-2S or BCGSI+1s for block
+// j >= 3 (k = j - 1): the synchronization of block k, the tail, Q_k and U_{k+1}.
+// BCGSI+1s is Alg. 2 without its first Cholesky line: U_{k+1} = X_{k+1} - Q_k S
+// is not normalized (S_{k+1,k+1} stays the identity) and T is not formed.
 int step_p(bcgs_qr_s* h, const void* X, int64_t ldx) {
   const int s = h->s, j = h->j + 1, k = j - 1;
   const int c = (k - 1) * s;
   const bool one_sync = h->variant == BCGS_BCGSI_PLUS_P_1S;
+  const bool unnormalized = h->variant == BCGS_BCGSI_PLUS_1S;
   const Seg Xs = seg(X, ldx, s, h->fp32);
   double* G = h->buf(h->L.G);
   const int ldg = h->L.ldg;
@@ -445,6 +451,9 @@ int step_p(bcgs_qr_s* h, const void* X, int64_t ldx) {
     if (one_sync)
       p.out[1] = ProjOut{reinterpret_cast<const double*>(X), ldx, h->buf(h->L.Sd[nxt]), s,
                          reinterpret_cast<double*>(h->U()), h->L.ldu, h->Umax()};
+    else if (unnormalized)
+      p.out[1] = ProjOut{reinterpret_cast<const double*>(X), ldx, nullptr, s,
+                         reinterpret_cast<double*>(h->U()), h->L.ldu, h->Umax()};
     else
       p.out[1] = ProjOut{reinterpret_cast<const double*>(X), ldx, nullptr, s,
                          reinterpret_cast<double*>(h->V()), h->L.ldu, MaxOut{nullptr, nullptr}};
@@ -454,7 +463,8 @@ int step_p(bcgs_qr_s* h, const void* X, int64_t ldx) {
     p.fp32 = h->fp32;
     TRY(launch_project_store(p, h->st(), h->stream));
     TRY(wrote_q(h, k));
-    if (!one_sync) TRY(tsqr(h, h->Vseg(), h->U(), h->L.ldu, h->buf(h->L.Sd[nxt]), s, k + 1, h->Umax()));
+    if (!one_sync && !unnormalized)
+      TRY(tsqr(h, h->Vseg(), h->U(), h->L.ldu, h->buf(h->L.Sd[nxt]), s, k + 1, h->Umax()));
     TRY(store_put(h, h->U(), h->L.ldu, k * s));
     h->cur = nxt;
     return BCGS_OK;
@@ -467,6 +477,9 @@ int step_p(bcgs_qr_s* h, const void* X, int64_t ldx) {
     // U_{k+1} = (X_{k+1} - Q_{1:k} S_{1:k,k+1}) S_{k+1,k+1}^{-1}
     TRY(project(h, Xs, c + s, h->buf(h->L.S[nxt]), h->n_max, h->buf(h->L.Sd[nxt]), h->U(),
                 h->L.ldu, h->Umax()));
+  } else if (unnormalized) {
+    // U_{k+1} = X_{k+1} - Q_{1:k} S_{1:k,k+1}  (BCGSI+1s: not normalized)
+    TRY(project(h, Xs, c + s, h->buf(h->L.S[nxt]), h->n_max, nullptr, h->U(), h->L.ldu, h->Umax()));
   } else {
     // [U_{k+1}, S_{k+1,k+1}] = TSQR(X_{k+1} - Q_{1:k} S_{1:k,k+1})
     TRY(project(h, Xs, c + s, h->buf(h->L.S[nxt]), h->n_max, nullptr, h->V(), h->L.ldu));
@@ -531,7 +544,7 @@ int step_pipi(bcgs_qr_s* h, const void* X, int64_t ldx, int j, int c, int sb) {
 // the delayed block of BCGSI+P-1S / -2S is finalized first (their last-block
 // branch), then the ragged block takes one step of the variant of the same
 // stability range whose step finalizes it at once: BCGS-PIPI+ for 1S and
-// PIPI+, BCGSI+ for BCGSI+ and 2S.  A first block that is already ragged
+// PIPI+ (and for BCGSI+1s, whose range it contains), BCGSI+ for BCGSI+ and 2S.  A first block that is already ragged
 // (n_max < s) is TSQR alone.
 int step_ragged(bcgs_qr_s* h, const void* X, int64_t ldx, int sb) {
   const int j = h->j + 1, c = h->j * h->s;
@@ -545,7 +558,7 @@ int step_ragged(bcgs_qr_s* h, const void* X, int64_t ldx, int sb) {
     if (rc != BCGS_OK) return rc;
   }
   h->flushed = 1;  // after the ragged step every block is final: nothing left for finish
-  if (h->variant == BCGS_BCGSI_PLUS_P_1S || h->variant == BCGS_BCGS_PIPI_PLUS)
+  if (h->variant == BCGS_BCGSI_PLUS_P_1S || h->variant == BCGS_BCGS_PIPI_PLUS || h->variant == BCGS_BCGSI_PLUS_1S)
     return step_pipi(h, X, ldx, j, c, sb);
   return step_bcgsi(h, X, ldx, j, c, sb);
 }
@@ -594,6 +607,18 @@ int do_step(bcgs_qr_s* h, const void* X, int64_t ldx) {
       return step_p(h, X, ldx);
     case BCGS_BCGS_PIPI_PLUS:
       return step_pipi(h, X, ldx, j, (j - 1) * s, s);
+    case BCGS_BCGSI_PLUS_1S:
+      if (j == 2) {
+        // S_12 = Q_1^T X_2, U_2 = X_2 - Q_1 S_12 (not normalized: S_22 = I)
+        TRY(store_put(h, X, ldx, s));
+        TRY(gram_cols(h, s, s, s, {h->Qseg(s)}, {Xs}, G));
+        TRY(launch_copy_small(s, s, G, ldg, h->buf(h->L.S[h->cur]), h->n_max, h->st(), h->stream));
+        TRY(zero_umax(h));
+        TRY(project(h, Xs, s, G, ldg, nullptr, h->U(), h->L.ldu, h->Umax()));
+        TRY(store_put(h, h->U(), h->L.ldu, s));
+        return BCGS_OK;
+      }
+      return step_p(h, X, ldx);
   }
   return BCGS_ERR_INVALID_ARG;
 }
@@ -602,7 +627,7 @@ int init_handle(bcgs_qr_s* h, int64_t m, int32_t n_max, int32_t s, int variant, 
                 void* Q, int64_t ldq, double* R, int32_t ldr, void* workspace, size_t ws_bytes,
                 void* stream) {
   if (!valid_shape(m, n_max, s)) return BCGS_ERR_INVALID_ARG;
-  if (variant < 0 || variant > 3 || precision < 0 || precision > 1) return BCGS_ERR_INVALID_ARG;
+  if (variant < 0 || variant > 4 || precision < 0 || precision > 1) return BCGS_ERR_INVALID_ARG;
   if (Q == nullptr || R == nullptr || workspace == nullptr) return BCGS_ERR_INVALID_ARG;
   if (ldq < m || ldr < n_max) return BCGS_ERR_INVALID_ARG;
   if (((uintptr_t)workspace) % 256 != 0) return BCGS_ERR_WORKSPACE;
@@ -626,7 +651,7 @@ int init_handle(bcgs_qr_s* h, int64_t m, int32_t n_max, int32_t s, int variant, 
   h->fp32 = precision == BCGS_FP32_STORAGE ? 1 : 0;
   h->esz = h->fp32 ? 4 : 8;
   // Grams from the store need whole 8-column groups per block and nb <= 32
-  const bool paired = variant == BCGS_BCGSI_PLUS_P_1S || variant == BCGS_BCGSI_PLUS_P_2S;
+  const bool paired = h->delayed();
   h->sgram = h->L.store && s % 8 == 0 && (paired ? s <= 16 : s <= 32);
   h->j = 0;
   h->cur = 0;
@@ -635,6 +660,8 @@ int init_handle(bcgs_qr_s* h, int64_t m, int32_t n_max, int32_t s, int variant, 
   TRY(launch_zero_lower(n_max, R, ldr, h->stream));
   TRY(launch_zero_u64(h->amaxQ(), n_max, h->stream));
   TRY(launch_zero_u64(h->rowmaxQ(), m, h->stream));
+  if (variant == BCGS_BCGSI_PLUS_1S)  // S_{k,k} = I for every block (no first normalization)
+    for (int i = 0; i < 2; ++i) TRY(launch_set_identity(s, h->buf(h->L.Sd[i]), h->stream));
   return BCGS_OK;
 }
 
@@ -647,8 +674,8 @@ struct StepRange {
 
 int step_handle(bcgs_qr_s* h, const void* X, int64_t ldx) {
   if (h->finished || (int64_t)h->j * h->s >= h->n_max) return BCGS_ERR_STATE;
-  static const char* kNames[4] = {"bcgs step (BCGSI+)", "bcgs step (BCGSI+P-1S)", "bcgs step (BCGSI+P-2S)",
-                                  "bcgs step (BCGS-PIPI+)"};
+  static const char* kNames[5] = {"bcgs step (BCGSI+)", "bcgs step (BCGSI+P-1S)", "bcgs step (BCGSI+P-2S)",
+                                  "bcgs step (BCGS-PIPI+)", "bcgs step (BCGSI+1s)"};
   StepRange range(kNames[h->variant]);
   if (X == nullptr || ldx < h->m) return BCGS_ERR_INVALID_ARG;
   const int rc = do_step(h, X, ldx);
@@ -792,7 +819,7 @@ int64_t bcgs_get_option(int option) {
 int bcgs_qr_workspace_size(int64_t m, int32_t n_max, int32_t s, int variant, int precision,
                            size_t* bytes) {
   if (bytes == nullptr || !valid_shape(m, n_max, s)) return BCGS_ERR_INVALID_ARG;
-  if (variant < 0 || variant > 3 || precision < 0 || precision > 1) return BCGS_ERR_INVALID_ARG;
+  if (variant < 0 || variant > 4 || precision < 0 || precision > 1) return BCGS_ERR_INVALID_ARG;
   Layout L;
   make_layout(m, n_max, s, variant, precision, want_store(m, s, precision), &L);
   *bytes = L.total;
@@ -866,7 +893,7 @@ int bcgs_qr_factor_host(int64_t m, int32_t n, int32_t s, int variant, int precis
   TRY(h2d(0, 1));
   TRY(cudaEventRecord(cs->in, cs->h2d));
   TRY(cudaStreamWaitEvent(main, cs->in, 0));
-  const bool delayed = variant == BCGS_BCGSI_PLUS_P_1S || variant == BCGS_BCGSI_PLUS_P_2S;
+  const bool delayed = h->delayed();
   int sent = 0;  // Q blocks already on their way to the host
   for (int k = 0; k < q; ++k) {
     if (k + 1 < q) TRY(h2d(k + 1, k + 2));  // travels while block k is factored

@@ -306,6 +306,12 @@ __global__ void zero_kernel(int32_t n, double* R, int32_t ldr) {
   }
 }
 
+// A = I (s x s, ld s): BCGSI+1s's S_{k+1,k+1}, the first intraorthogonalization
+// it does not perform (Sec. 2).
+__global__ void identity_kernel(int32_t s, double* A) {
+  for (int e = threadIdx.x; e < s * s; e += blockDim.x) A[e] = (e % s) == (e / s) ? 1.0 : 0.0;
+}
+
 __global__ void zero_u64_words(unsigned long long* p, int64_t n) {
   for (int64_t i = threadIdx.x + (int64_t)blockIdx.x * blockDim.x; i < n; i += (int64_t)blockDim.x * gridDim.x)
     p[i] = 0ull;
@@ -388,6 +394,12 @@ cudaError_t launch_zero_u64(unsigned long long* p, int64_t n, cudaStream_t strea
   int64_t grid = (n + 255) / 256;
   if (grid > 1024) grid = 1024;
   zero_u64_words<<<(unsigned)grid, 256, 0, stream>>>(p, n);
+  note_launch(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_set_identity(int32_t s, double* A, cudaStream_t stream) {
+  identity_kernel<<<1, 256, 0, stream>>>(s, A);
   note_launch(1);
   return cudaGetLastError();
 }

@@ -214,14 +214,15 @@ def _ms(x):
 
 # the variant of the same stability range (Table 1) whose blocks are final
 # after their own step, for the "eager" finalize mode
-EAGER = {"bcgsi+p-1s": "bcgs-pipi+", "bcgsi+p-2s": "bcgsi+", "bcgs-pipi+": "bcgs-pipi+", "bcgsi+": "bcgsi+"}
-DELAYED = ("bcgsi+p-1s", "bcgsi+p-2s")
+EAGER = {"bcgsi+p-1s": "bcgs-pipi+", "bcgsi+p-2s": "bcgsi+", "bcgs-pipi+": "bcgs-pipi+", "bcgsi+": "bcgsi+",
+         "bcgsi+1s": "bcgs-pipi+"}
+DELAYED = ("bcgsi+p-1s", "bcgsi+p-2s", "bcgsi+1s")
 
 
 def final_blocks_after(variant: str, steps: int) -> int:
     """Blocks of Q final after `steps` steps (before the finish call): delayed
     normalization (Sec. 2) keeps the newest block provisional under
-    BCGSI+P-1S/-2S, except that block 1 comes final from TSQR."""
+    BCGSI+P-1S/-2S and BCGSI+1s, except that block 1 comes final from TSQR."""
     if variant in DELAYED:
         return max(steps - 1, 1) if steps >= 1 else 0
     return steps

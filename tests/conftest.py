@@ -33,6 +33,17 @@ def load_golden(name):
     return out
 
 
+def loo_gate(variant, n, kappa, loo_oracle):
+    """Loss-of-orthogonality gate of a GPU result.  The O(u) variants meet the
+    FP64 gate 1e-12; BCGSI+1s has O(u) kappa^2 loss of orthogonality (Table 1),
+    so it is held to that bound with a modest constant and to at most ten
+    times the oracle's own loss of orthogonality on the same input."""
+    if variant != "bcgsi+1s":
+        return 1e-12
+    u = 2.0 ** -53
+    return min(10 * n * u * kappa ** 2, max(1e-12, 10 * loo_oracle))
+
+
 @pytest.fixture
 def golden():
     return load_golden

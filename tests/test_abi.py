@@ -95,7 +95,8 @@ def test_bad_enums_and_null_pointers_rejected():
 
     lib = bcgs.load_library()
     out = ctypes.c_size_t(0)
-    assert lib.bcgs_qr_workspace_size(100, 16, 8, 4, 0, ctypes.byref(out)) == 1
+    assert lib.bcgs_qr_workspace_size(100, 16, 8, 5, 0, ctypes.byref(out)) == 1
+    assert lib.bcgs_qr_workspace_size(100, 16, 8, 4, 0, ctypes.byref(out)) == 0  # BCGSI+1s
     assert lib.bcgs_qr_workspace_size(100, 16, 8, -1, 0, ctypes.byref(out)) == 1
     assert lib.bcgs_qr_workspace_size(100, 16, 8, 3, 0, ctypes.byref(out)) == 0
     assert lib.bcgs_qr_workspace_size(100, 16, 8, 1, 2, ctypes.byref(out)) == 1
@@ -163,7 +164,7 @@ def test_ragged_shapes_accepted(m, n, s):
 
     lib = bcgs.load_library()
     out = ctypes.c_size_t(0)
-    for variant in range(4):
+    for variant in range(5):
         assert lib.bcgs_qr_workspace_size(m, n, s, variant, 0, ctypes.byref(out)) == 0
         assert out.value > 0
 

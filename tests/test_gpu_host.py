@@ -9,7 +9,7 @@ import oracle
 from paper_2507_21791_gb300 import synth
 
 pytestmark = pytest.mark.gpu
-VARIANTS = ["bcgsi+", "bcgsi+p-1s", "bcgsi+p-2s", "bcgs-pipi+"]
+VARIANTS = ["bcgsi+", "bcgsi+p-1s", "bcgsi+p-2s", "bcgs-pipi+", "bcgsi+1s"]
 
 
 def host_colmajor(torch, m, n, dtype, pinned):

@@ -12,6 +12,7 @@ import numpy as np
 import pytest
 
 import oracle
+from conftest import loo_gate
 from paper_2507_21791_gb300 import synth
 
 U64 = np.finfo(np.float64).eps / 2
@@ -36,13 +37,13 @@ def check_against_oracle(X, s, variant, Q, R):
     Qh, Rh = Q.cpu().numpy(), R.cpu().numpy()
     Qo, Ro = oracle.factor(X, s, variant)
     assert oracle.residual(X, Qh, Rh) <= 1e-13
-    assert oracle.loo(Qh) <= 1e-12
+    assert oracle.loo(Qh) <= loo_gate(variant, n, oracle.kappa(Ro), oracle.loo(Qo))
     tol = 10 * n * oracle.kappa(Ro) * U64
     assert np.linalg.norm(Rh - Ro) / np.linalg.norm(Ro) <= tol
     assert np.max(np.abs(Qh - Qo)) <= tol
 
 
-@pytest.mark.parametrize("variant", ["bcgsi+", "bcgsi+p-1s", "bcgsi+p-2s", "bcgs-pipi+"])
+@pytest.mark.parametrize("variant", ["bcgsi+", "bcgsi+p-1s", "bcgsi+p-2s", "bcgs-pipi+", "bcgsi+1s"])
 @pytest.mark.parametrize("m,n,s,kappa", SHAPES)
 def test_store_path_matches_the_oracle(tensor, variant, m, n, s, kappa):
     if variant in ("bcgsi+p-1s", "bcgs-pipi+") and kappa > 1e5:
@@ -58,7 +59,7 @@ def test_store_path_matches_the_oracle(tensor, variant, m, n, s, kappa):
     assert np.array_equal(R.cpu().numpy(), R2.cpu().numpy())
 
 
-@pytest.mark.parametrize("variant", ["bcgsi+", "bcgsi+p-1s", "bcgsi+p-2s", "bcgs-pipi+"])
+@pytest.mark.parametrize("variant", ["bcgsi+", "bcgsi+p-1s", "bcgsi+p-2s", "bcgs-pipi+", "bcgsi+1s"])
 def test_store_and_on_the_fly_paths_agree(tensor, variant):
     """A workspace sized without the store runs the same factorization with the
     on-the-fly tensor projections; both meet the FP64 gates and agree to the
