@@ -71,7 +71,8 @@ typedef enum {
   BCGS_ERR_WORKSPACE = 5,      /* workspace too small or misaligned              */
   BCGS_ERR_TIMEOUT = 6,        /* a bounded device wait gave up                  */
   BCGS_ERR_STATE = 7,          /* call out of order (step after finish, ...)    */
-  BCGS_ERR_CUDA = 8            /* a CUDA runtime call failed                     */
+  BCGS_ERR_CUDA = 8,           /* a CUDA runtime call failed                     */
+  BCGS_ERR_COMM = 9            /* the all-gather callback of the row-partitioned form failed */
 } bcgs_status;
 
 typedef enum {
@@ -143,6 +144,64 @@ BCGS_API int bcgs_qr_factor_host(int64_t m, int32_t n, int32_t s, int variant, i
                    const void* X_host, int64_t ldxh, void* Q_host, int64_t ldqh, double* R_host,
                    int32_t ldrh, void* Xd, int64_t ldx, void* Qd, int64_t ldq, double* Rd,
                    int32_t ldr, void* workspace, size_t ws_bytes, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Row-partitioned form (Sec. 3: each of P processes holds a block of rows of
+ * X, Q and U and a replicated copy of every small matrix; the only global
+ * operations are the sums of the tall-skinny products, one MPI_Allreduce per
+ * synchronization on the paper's cluster, and the R-factor reduction of TSQR).
+ *
+ * Here each rank runs the same block steps on its own rows.  At every
+ * synchronization the library calls `allgather` once: every rank contributes
+ * `bytes` from the device buffer `send` and must receive all ranks'
+ * contributions, rank after rank, in the device buffer `recv` (P * bytes);
+ * both buffers lie inside the rank's workspace.  The library then adds the P
+ * copies in rank order with its own kernel, so the sum, and the replicated
+ * small tail after it, has the same bits on every rank and on every run.  TSQR
+ * (the first block, and every block of BCGSI+ and BCGSI+P-2S) factors the
+ * local rows, gathers the P local R factors the same way, factors their stack
+ * (the same bits on every rank) and forms this rank's rows of Q from its
+ * block of the stacked factor's Q.
+ *
+ * The callback runs on the calling host thread, between launches on `stream`:
+ * it must order the exchange on `stream` (after the work enqueued before the
+ * call, before the work enqueued after it) and return 0, or nonzero to stop the
+ * factorization with BCGS_ERR_COMM (the other ranks then wait in their own
+ * callbacks: a collective with a timeout, such as a process group's, ends them).
+ * With NCCL it is one all-gather on `stream`.  No device code waits on another
+ * rank: every exchange happens through the callback.
+ *
+ * A rank whose factorization has failed (a non-finite local value, ...) sends
+ * NaN, so every rank reports a failure, at a block index within one of the
+ * failing rank's (the block whose small factors the NaN reaches first).
+ * ------------------------------------------------------------------------- */
+typedef int (*bcgs_allgather_fn)(void* ctx, const void* send, void* recv, size_t bytes, void* stream);
+
+/* The rows [*row0, *row0 + *rows) of an m-row matrix that rank `rank` of
+ * `nranks` owns: whole 128-row blocks, as even as possible (the first
+ * ceil(m / 128) mod nranks ranks get one block more; the last block may be
+ * ragged; a rank may get none when m is small).  Host only. */
+BCGS_API int bcgs_row_partition(int64_t m, int32_t nranks, int32_t rank, int64_t* row0, int64_t* rows);
+
+/* Workspace of bcgs_qr_factor_rows for a rank with m_local rows.  With
+ * nranks = 1 the same as bcgs_qr_workspace_size; with nranks > 1 the slab
+ * needs m_local >= s rows (not n), and the workspace adds the gathered copies
+ * (nranks * n * 2s doubles), the stacked R factors and a local TSQR block. */
+BCGS_API int bcgs_qr_workspace_size_rows(int64_t m_local, int32_t n, int32_t s, int variant, int precision,
+                                         int32_t nranks, size_t* bytes);
+
+/* This rank's part of the factorization of the m x n matrix whose rows
+ * [row0, row0 + m_local) are X (m_local x n, ldx): Q gets the same rows of the
+ * global Q (m_local x n, ldq) and R (n x n, ldr) the whole R, the same bits on
+ * every rank.  All ranks call it with the same n, s, variant and precision.
+ * The arguments are as for bcgs_qr_factor, plus rank, nranks (1..4096) and the
+ * callback (may be NULL only for nranks = 1, which is bcgs_qr_factor).  Returns
+ * after the whole factorization is enqueued; read the outcome with
+ * bcgs_qr_factor_status; BCGS_ERR_COMM when a callback returned nonzero. */
+BCGS_API int bcgs_qr_factor_rows(int64_t m_local, int32_t n, int32_t s, int variant, int precision,
+                                 const void* X, int64_t ldx, void* Q, int64_t ldq, double* R, int32_t ldr,
+                                 void* workspace, size_t ws_bytes, void* stream, int32_t rank, int32_t nranks,
+                                 bcgs_allgather_fn allgather, void* ctx);
 
 /* Self-test of the timeout path, with no fault involved: one bounded device
  * wait on a barrier that nothing completes gives up after `cycles` SM clock

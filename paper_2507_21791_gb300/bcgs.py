@@ -18,7 +18,7 @@ VARIANTS = {"bcgsi+": 0, "bcgsi+p-1s": 1, "bcgsi+p-2s": 2, "bcgs-pipi+": 3, "bcg
 PRECISIONS = {"fp64": 0, "fp32": 1}
 STATUS = {
     0: "ok", 1: "invalid_arg", 2: "not_spd", 3: "rank_deficient", 4: "nonfinite",
-    5: "workspace", 6: "timeout", 7: "state", 8: "cuda",
+    5: "workspace", 6: "timeout", 7: "state", 8: "cuda", 9: "comm",
 }
 
 # Every symbol declared in include/bcgs_qr.h: (name, restype, argtypes).
@@ -61,6 +61,10 @@ SIGNATURES = [
     ("bcgs_tsqr", ctypes.c_int, [_i64, _i32, _vp, _i64, _vp, _i64, _vp, _i32, _vp, _sz, _vp]),
     ("bcgs_chol", ctypes.c_int, [_i32, _vp, _i32, _vp, _i32, _vp, _sz, _vp]),
     ("bcgs_gram_noalloc", ctypes.c_int, [_i64, _i32, _i32, _vp, _i64, _vp, _i64, _vp, _i32, _vp]),
+    ("bcgs_row_partition", ctypes.c_int, [_i64, _i32, _i32, ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
+    ("bcgs_qr_workspace_size_rows", ctypes.c_int, [_i64, _i32, _i32, ctypes.c_int, ctypes.c_int, _i32, _psz]),
+    ("bcgs_qr_factor_rows", ctypes.c_int, [_i64, _i32, _i32, ctypes.c_int, ctypes.c_int, _vp, _i64, _vp, _i64,
+                                           _vp, _i32, _vp, _sz, _vp, _i32, _i32, _vp, _vp]),
     ("bcgs_set_option", ctypes.c_int, [ctypes.c_int, ctypes.c_int64]),
     ("bcgs_get_option", ctypes.c_int64, [ctypes.c_int]),
     ("bcgs_launch_count", ctypes.c_int64, []),

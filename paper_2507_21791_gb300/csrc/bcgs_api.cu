@@ -26,6 +26,11 @@ constexpr int kMaxN = 2048;
 struct Layout {
   size_t status, S[2], Sd[2], Yd, Rt1, Rt2, G, G2, Bp, partial, amax, amaxQ, amaxU, rowmaxQ, U, V, tsqr,
       qstore, fexp, total;
+  // row-partitioned form (nranks > 1): gathered copies, the stacked R factors,
+  // the stacked factor's Q, the local TSQR factor and R, and the stacked TSQR's work
+  size_t comm_recv, stack, stackq, Tq, Rloc, tsqr_stack;
+  int nranks;
+  TsqrPlan tp_stack, tp_stack_last;
   int store;    // the digit store of Q is part of the workspace
   int ldg;      // leading dimension of G, G2 (= n_max)
   int64_t ldu;  // leading dimension of U, V
@@ -49,7 +54,7 @@ bool want_store(int64_t m, int32_t s, int precision) {
 }
 
 void make_layout(int64_t m, int32_t n_max, int32_t s, int variant, int precision, int store,
-                 Layout* L) {
+                 Layout* L, int nranks = 1) {
   const size_t esz = precision == BCGS_FP32_STORAGE ? 4 : 8;
   size_t off = 0;
   auto take = [&](size_t bytes) {
@@ -89,6 +94,21 @@ void make_layout(int64_t m, int32_t n_max, int32_t s, int variant, int precision
   L->store = store;
   L->qstore = store ? take(qstore_bytes(m, n_max)) : off;
   L->fexp = store ? take((size_t)ceil_div(m, kStoreRows) * 32 * sizeof(int32_t)) : off;
+  L->nranks = nranks;
+  if (nranks > 1) {
+    const size_t per = (size_t)n_max * 2 * s > (size_t)s * s ? (size_t)n_max * 2 * s : (size_t)s * s;
+    L->comm_recv = take((size_t)nranks * per * sizeof(double));
+    L->stack = take((size_t)nranks * s * s * sizeof(double));
+    L->stackq = take((size_t)nranks * s * s * sizeof(double));
+    L->Tq = take((size_t)L->ldu * s * esz);
+    L->Rloc = take(ss);
+    tsqr_plan((int64_t)nranks * s, s, &L->tp_stack);
+    tsqr_plan((int64_t)nranks * (s_last > 0 ? s_last : s), s_last > 0 ? s_last : s, &L->tp_stack_last);
+    const size_t d1 = L->tp_stack.doubles, d2 = L->tp_stack_last.doubles;
+    L->tsqr_stack = take((d1 > d2 ? d1 : d2) * sizeof(double));
+  } else {
+    L->comm_recv = L->stack = L->stackq = L->Tq = L->Rloc = L->tsqr_stack = off;
+  }
   L->total = off;
 }
 
@@ -153,6 +173,12 @@ struct bcgs_qr_s {
   int32_t sgram;  // Grams read the digit store (the current U and X blocks are split into it)
   int32_t flushed;  // a ragged last block was stepped: every block is final, finish does nothing
   cudaError_t last_cuda;
+  // row-partitioned form: this process's rank among nranks and the all-gather
+  // it calls once per synchronization (nranks = 1: no collective)
+  int32_t rank, nranks;
+  bcgs_allgather_fn allgather;
+  void* ag_ctx;
+  int32_t comm_failed;
 
   DevStatus* st() { return reinterpret_cast<DevStatus*>(ws + L.status); }
   double* buf(size_t off) { return reinterpret_cast<double*>(ws + off); }
@@ -296,8 +322,35 @@ cudaError_t store_put(bcgs_qr_s* h, const void* src, int64_t ld, int k0, int sb 
 
 // G = A^T B: from the store (A = store columns [0, na), B = [b0, b0 + nb)) when
 // the factorization keeps its Grams there, else from the segments.
+// Row-partitioned form: G holds this rank's Gram of its rows; every rank sends
+// its copy (NaN if its factorization has failed), receives all copies and adds
+// them in rank order, so G becomes the Gram of the whole matrix, the same bits
+// on every rank.
+cudaError_t sum_over_ranks(bcgs_qr_s* h, double* G, int na, int nb) {
+  const size_t elems = (size_t)h->L.ldg * nb;
+  cudaError_t e = launch_poison_if_failed(G, (int64_t)elems, h->st(), h->stream);
+  if (e != cudaSuccess) return e;
+  double* recv = h->buf(h->L.comm_recv);
+  if (h->allgather(h->ag_ctx, G, recv, elems * sizeof(double), h->stream) != 0) {
+    h->comm_failed = 1;
+    return cudaErrorUnknown;
+  }
+  return launch_rank_sum(recv, h->nranks, na, nb, h->L.ldg, G, h->st(), h->stream);
+}
+
+cudaError_t gram_local(bcgs_qr_s* h, int na, int b0, int nb, std::initializer_list<Seg> A,
+                       std::initializer_list<Seg> B, double* G);
+
 cudaError_t gram_cols(bcgs_qr_s* h, int na, int b0, int nb, std::initializer_list<Seg> A,
                       std::initializer_list<Seg> B, double* G) {
+  const cudaError_t e = gram_local(h, na, b0, nb, A, B, G);
+  if (e != cudaSuccess || h->nranks <= 1) return e;
+  return sum_over_ranks(h, G, na, nb);
+}
+
+// The Gram of this process's rows only.
+cudaError_t gram_local(bcgs_qr_s* h, int na, int b0, int nb, std::initializer_list<Seg> A,
+                       std::initializer_list<Seg> B, double* G) {
   if (!h->sgram) return gram(h, A, B, G);
   GramStoreDesc d;
   memset(&d, 0, sizeof(d));
@@ -315,7 +368,37 @@ cudaError_t tsqr(bcgs_qr_s* h, Seg a, void* q, int64_t ldq, double* R, int ldr, 
                  MaxOut qmax = MaxOut{nullptr, nullptr}) {
   // the plan of the block's width (a.ncols is s or the ragged rest)
   const TsqrPlan& tp = a.ncols == h->s ? h->L.tp : h->L.tp_last;
-  return launch_tsqr(tp, a, q, ldq, h->fp32, R, ldr, h->buf(h->L.tsqr), h->st(), block, h->stream, qmax);
+  if (h->nranks <= 1)
+    return launch_tsqr(tp, a, q, ldq, h->fp32, R, ldr, h->buf(h->L.tsqr), h->st(), block, h->stream, qmax);
+  // Row-partitioned TSQR: the local rows' TSQR gives Tq and R_loc; the ranks'
+  // R_loc are gathered, stacked and factored again (the same bits on every
+  // rank), [R_0; ...; R_{P-1}] = Qs R; this rank's rows of Q are Tq times its
+  // s x s block of Qs.  The local factor carries no status word: a rank's rows
+  // may be rank deficient while the whole block is not (and a NaN reaches the
+  // stacked factor, which reports it).
+  const int w = a.ncols, P = h->nranks;
+  const TsqrPlan& tps = w == h->s ? h->L.tp_stack : h->L.tp_stack_last;
+  double* Rloc = h->buf(h->L.Rloc);
+  void* Tq = h->ws + h->L.Tq;
+  cudaError_t e = launch_tsqr(tp, a, Tq, h->L.ldu, h->fp32, Rloc, w, h->buf(h->L.tsqr), nullptr, block, h->stream,
+                              MaxOut{nullptr, nullptr});
+  if (e != cudaSuccess) return e;
+  e = launch_poison_if_failed(Rloc, (int64_t)w * w, h->st(), h->stream);
+  if (e != cudaSuccess) return e;
+  double* recv = h->buf(h->L.comm_recv);
+  if (h->allgather(h->ag_ctx, Rloc, recv, (size_t)w * w * sizeof(double), h->stream) != 0) {
+    h->comm_failed = 1;
+    return cudaErrorUnknown;
+  }
+  double* stack = h->buf(h->L.stack);
+  double* stackq = h->buf(h->L.stackq);
+  e = launch_stack_r(recv, P, w, stack, h->st(), h->stream);
+  if (e != cudaSuccess) return e;
+  e = launch_tsqr(tps, seg(stack, (int64_t)P * w, w, 0), stackq, (int64_t)P * w, 0, R, ldr,
+                  h->buf(h->L.tsqr_stack), h->st(), block, h->stream, MaxOut{nullptr, nullptr});
+  if (e != cudaSuccess) return e;
+  return launch_rows_times_small(h->m, w, Tq, h->L.ldu, stackq + (size_t)h->rank * w, P * w, q, ldq, h->fp32, qmax,
+                                 h->st(), h->stream);
 }
 cudaError_t zero_umax(bcgs_qr_s* h, int sb = 0) { return launch_zero_u64(h->amaxU(), sb ? sb : h->s, h->stream); }
 
@@ -623,18 +706,25 @@ int do_step(bcgs_qr_s* h, const void* X, int64_t ldx) {
   return BCGS_ERR_INVALID_ARG;
 }
 
+// Row-partitioned form: a rank's slab needs s rows (its local TSQR), not n.
+bool valid_local_shape(int64_t m, int32_t n, int32_t s) {
+  return s >= 1 && s <= kMaxS && n >= 1 && n <= kMaxN && m >= s;
+}
+
 int init_handle(bcgs_qr_s* h, int64_t m, int32_t n_max, int32_t s, int variant, int precision,
                 void* Q, int64_t ldq, double* R, int32_t ldr, void* workspace, size_t ws_bytes,
-                void* stream) {
-  if (!valid_shape(m, n_max, s)) return BCGS_ERR_INVALID_ARG;
+                void* stream, int32_t rank = 0, int32_t nranks = 1, bcgs_allgather_fn allgather = nullptr,
+                void* ag_ctx = nullptr) {
+  if (nranks < 1 || rank < 0 || rank >= nranks || (nranks > 1 && allgather == nullptr)) return BCGS_ERR_INVALID_ARG;
+  if (nranks > 1 ? !valid_local_shape(m, n_max, s) : !valid_shape(m, n_max, s)) return BCGS_ERR_INVALID_ARG;
   if (variant < 0 || variant > 4 || precision < 0 || precision > 1) return BCGS_ERR_INVALID_ARG;
   if (Q == nullptr || R == nullptr || workspace == nullptr) return BCGS_ERR_INVALID_ARG;
   if (ldq < m || ldr < n_max) return BCGS_ERR_INVALID_ARG;
   if (((uintptr_t)workspace) % 256 != 0) return BCGS_ERR_WORKSPACE;
   memset(h, 0, sizeof(*h));
-  make_layout(m, n_max, s, variant, precision, want_store(m, s, precision), &h->L);
+  make_layout(m, n_max, s, variant, precision, want_store(m, s, precision), &h->L, nranks);
   if (ws_bytes < h->L.total && h->L.store)  // sized without the store: run without it
-    make_layout(m, n_max, s, variant, precision, 0, &h->L);
+    make_layout(m, n_max, s, variant, precision, 0, &h->L, nranks);
   if (ws_bytes < h->L.total) return BCGS_ERR_WORKSPACE;
   h->m = m;
   h->n_max = n_max;
@@ -650,6 +740,10 @@ int init_handle(bcgs_qr_s* h, int64_t m, int32_t n_max, int32_t s, int variant, 
   h->stream = reinterpret_cast<cudaStream_t>(stream);
   h->fp32 = precision == BCGS_FP32_STORAGE ? 1 : 0;
   h->esz = h->fp32 ? 4 : 8;
+  h->rank = rank;
+  h->nranks = nranks;
+  h->allgather = allgather;
+  h->ag_ctx = ag_ctx;
   // Grams from the store need whole 8-column groups per block and nb <= 32
   const bool paired = h->delayed();
   h->sgram = h->L.store && s % 8 == 0 && (paired ? s <= 16 : s <= 32);
@@ -783,6 +877,7 @@ const char* bcgs_status_string(int status) {
     case BCGS_ERR_TIMEOUT: return "device wait timed out";
     case BCGS_ERR_STATE: return "call out of order";
     case BCGS_ERR_CUDA: return "CUDA runtime error";
+    case BCGS_ERR_COMM: return "the all-gather callback of the row-partitioned form failed";
   }
   return "unknown status";
 }
@@ -846,6 +941,56 @@ int bcgs_qr_factor(int64_t m, int32_t n, int32_t s, int variant, int precision, 
     if (rc != BCGS_OK) return rc;
   }
   return finish_handle(h);
+}
+
+int bcgs_row_partition(int64_t m, int32_t nranks, int32_t rank, int64_t* row0, int64_t* rows) {
+  if (m < 1 || nranks < 1 || rank < 0 || rank >= nranks || row0 == nullptr || rows == nullptr)
+    return BCGS_ERR_INVALID_ARG;
+  // whole 128-row blocks, as even as possible, the first nblk mod nranks ranks one more
+  const int64_t nblk = ceil_div(m, kStoreRows);
+  const int64_t base = nblk / nranks, extra = nblk % nranks;
+  const int64_t b0 = (int64_t)rank * base + (rank < extra ? rank : extra);
+  const int64_t nb = base + (rank < extra ? 1 : 0);
+  const int64_t r0 = b0 * kStoreRows;
+  int64_t r1 = (b0 + nb) * kStoreRows;
+  if (r1 > m) r1 = m;
+  *row0 = r0 < m ? r0 : m;
+  *rows = r1 > r0 ? r1 - r0 : 0;
+  return BCGS_OK;
+}
+
+int bcgs_qr_workspace_size_rows(int64_t m_local, int32_t n, int32_t s, int variant, int precision, int32_t nranks,
+                                size_t* bytes) {
+  if (bytes == nullptr || nranks < 1 || nranks > 4096) return BCGS_ERR_INVALID_ARG;
+  if (nranks > 1 ? !valid_local_shape(m_local, n, s) : !valid_shape(m_local, n, s)) return BCGS_ERR_INVALID_ARG;
+  if (variant < 0 || variant > 4 || precision < 0 || precision > 1) return BCGS_ERR_INVALID_ARG;
+  Layout L;
+  make_layout(m_local, n, s, variant, precision, want_store(m_local, s, precision), &L, nranks);
+  *bytes = L.total;
+  return BCGS_OK;
+}
+
+int bcgs_qr_factor_rows(int64_t m_local, int32_t n, int32_t s, int variant, int precision, const void* X, int64_t ldx,
+                        void* Q, int64_t ldq, double* R, int32_t ldr, void* workspace, size_t ws_bytes, void* stream,
+                        int32_t rank, int32_t nranks, bcgs_allgather_fn allgather, void* ctx) {
+  if (X == nullptr || ldx < m_local || nranks > 4096) return BCGS_ERR_INVALID_ARG;
+  if (precision >= 0 && precision <= 1 &&
+      overlaps(X, ldx, Q, ldq, m_local, n, precision == BCGS_FP32_STORAGE ? 4 : 8))
+    return BCGS_ERR_INVALID_ARG;
+  bcgs_qr_s hs;
+  bcgs_qr_s* h = &hs;
+  int rc = init_handle(h, m_local, n, s, variant, precision, Q, ldq, R, ldr, workspace, ws_bytes, stream, rank,
+                       nranks, allgather, ctx);
+  if (rc != BCGS_OK) return rc;
+  const size_t esz = precision == BCGS_FP32_STORAGE ? 4 : 8;
+  const char* Xc = reinterpret_cast<const char*>(X);
+  const int q = (n + s - 1) / s;
+  for (int k = 0; k < q; ++k) {
+    rc = step_handle(h, Xc + (size_t)k * s * ldx * esz, ldx);
+    if (rc != BCGS_OK) return h->comm_failed ? BCGS_ERR_COMM : rc;
+  }
+  rc = finish_handle(h);
+  return (rc != BCGS_OK && h->comm_failed) ? BCGS_ERR_COMM : rc;
 }
 
 int bcgs_qr_factor_host(int64_t m, int32_t n, int32_t s, int variant, int precision, const void* X_host,

@@ -226,6 +226,18 @@ cudaError_t launch_tsqr(const TsqrPlan& plan, Seg a, void* q, int64_t ldq, int32
                         double* R, int32_t ldr, double* work, DevStatus* st, int32_t block,
                         cudaStream_t stream, MaxOut qmax = MaxOut{nullptr, nullptr});
 
+// Row-partitioned form (Sec. 3): the rank-ordered sum of the gathered local
+// Grams, NaN into a buffer of a failed factorization, the stacked R factors of
+// the cross-rank TSQR level and W = A B for the local rows.
+cudaError_t launch_rank_sum(const double* recv, int32_t nranks, int32_t na, int32_t nb, int32_t ld, double* G,
+                            const DevStatus* st, cudaStream_t stream);
+cudaError_t launch_poison_if_failed(double* p, int64_t n, const DevStatus* st, cudaStream_t stream);
+cudaError_t launch_stack_r(const double* recv, int32_t nranks, int32_t s, double* out, const DevStatus* st,
+                           cudaStream_t stream);
+cudaError_t launch_rows_times_small(int64_t m, int32_t s, const void* A, int64_t lda, const double* B, int32_t ldb,
+                                    void* W, int64_t ldw, int32_t fp32, MaxOut wmax, const DevStatus* st,
+                                    cudaStream_t stream);
+
 // Small FP64 tails (one CTA each); see tail.cu for the exact formulas.
 struct TailDesc {
   int32_t s, c;         // block size; rows of the Y / Z blocks (columns of the previous basis)

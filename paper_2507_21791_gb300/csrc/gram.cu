@@ -118,6 +118,33 @@ __global__ void gram_reduce_kernel(const double* __restrict__ partial, int32_t n
   G[i + (size_t)j * ldg] = sum;
 }
 
+// G = the sum over ranks, in rank order, of the gathered copies of the local
+// Grams (rank-major; each column-major with leading dimension ld over nb
+// columns): the cross-rank part of one synchronization of the row-partitioned
+// form (Sec. 3: each process holds a block of rows and the Gram is summed over
+// the processes).  A fixed order makes the sum, and so the replicated tail
+// after it, the same on every rank and on every run.
+__global__ void rank_sum_kernel(const double* __restrict__ recv, int32_t nranks, int32_t na, int32_t nb,
+                                int32_t ld, double* __restrict__ G, const DevStatus* st) {
+  if (failed(st)) return;
+  const int o = blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= na * nb) return;
+  const int i = o % na, j = o / na;
+  const size_t per = (size_t)ld * nb;
+  double sum = recv[i + (size_t)j * ld];
+  for (int r = 1; r < nranks; ++r) sum += recv[(size_t)r * per + i + (size_t)j * ld];
+  G[i + (size_t)j * ld] = sum;
+}
+
+// p[0 .. n) = NaN when the factorization has failed: a rank that stopped
+// working sends NaN, so the failure reaches every rank through the next sum
+// instead of a stale buffer being added in.
+__global__ void poison_kernel(double* p, int64_t n, const DevStatus* st) {
+  if (!failed(st)) return;
+  for (int64_t e = threadIdx.x + (int64_t)blockIdx.x * blockDim.x; e < n; e += (int64_t)blockDim.x * gridDim.x)
+    p[e] = __longlong_as_double(0x7FF8000000000000LL);
+}
+
 template <typename T>
 cudaError_t launch_gram_t(const GramDesc& d, double* partial, double* G, int ldg, DevStatus* st,
                           cudaStream_t stream) {
@@ -169,6 +196,24 @@ cudaError_t launch_gram_reduce(const double* partial, int32_t nchunks, int32_t n
                                                                   st);
   prof_end(slot2, kProfGramReduce, stream, (double)nchunks * nout_all,
            (double)nchunks * nout_all * 8.0 + nout_all * 8.0);
+  note_launch(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rank_sum(const double* recv, int32_t nranks, int32_t na, int32_t nb, int32_t ld, double* G,
+                            const DevStatus* st, cudaStream_t stream) {
+  const int n = na * nb;
+  if (n <= 0) return cudaSuccess;
+  rank_sum_kernel<<<(n + 255) / 256, 256, 0, stream>>>(recv, nranks, na, nb, ld, G, st);
+  note_launch(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_poison_if_failed(double* p, int64_t n, const DevStatus* st, cudaStream_t stream) {
+  if (n <= 0) return cudaSuccess;
+  int64_t grid = (n + 255) / 256;
+  if (grid > 256) grid = 256;
+  poison_kernel<<<(unsigned)grid, 256, 0, stream>>>(p, n, st);
   note_launch(1);
   return cudaGetLastError();
 }

@@ -347,6 +347,61 @@ tsqr_leaf_apply(TsqrPlan p, const double* work, void* q, int64_t ldq, const DevS
   }
 }
 
+// The ranks' s x s R factors, gathered rank-major (each column-major, ld s),
+// stacked into one (nranks s) x s column-major matrix: the cross-rank level of
+// the row-partitioned TSQR (Sec. 3, Sec. 4: TSQR reduces the R factors of the
+// row blocks).
+__global__ void stack_r_kernel(const double* __restrict__ recv, int32_t nranks, int32_t s, double* __restrict__ out,
+                               const DevStatus* st) {
+  if (failed(st)) return;
+  const int ld = nranks * s;
+  for (int e = threadIdx.x + blockIdx.x * blockDim.x; e < nranks * s * s; e += blockDim.x * gridDim.x) {
+    const int r = e / (s * s), rem = e - r * s * s, i = rem % s, j = rem / s;
+    out[(r * s + i) + (size_t)j * ld] = recv[e];
+  }
+}
+
+// W = A B, A m x s (storage type T, lda), B s x s FP64 (ldb), W m x s (T, ldw):
+// one thread per row, B in shared memory; the maxima of the stored W.  Used to
+// turn a rank's local TSQR factor into its rows of the global Q (the local Q
+// times the rank's s x s block of the stacked factor's Q).
+template <typename T>
+__global__ void __launch_bounds__(256) rows_times_small_kernel(int64_t m, int32_t s, const T* __restrict__ A,
+                                                               int64_t lda, const double* __restrict__ B,
+                                                               int32_t ldb, T* __restrict__ W, int64_t ldw,
+                                                               MaxOut wmax, const DevStatus* st) {
+  if (failed(st)) return;
+  __shared__ double Bs[64 * 64];
+  for (int e = threadIdx.x; e < s * s; e += blockDim.x) Bs[e] = B[(e % s) + (size_t)(e / s) * ldb];
+  __syncthreads();
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool live = r < m;
+  unsigned long long rmax = 0ull;
+  for (int c0 = 0; c0 < s; c0 += 16) {
+    const int nc = s - c0 < 16 ? s - c0 : 16;
+    double e[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) e[c] = 0.0;
+    if (live)
+      for (int l = 0; l < s; ++l) {
+        const double a = (double)A[r + (int64_t)l * lda];
+#pragma unroll
+        for (int c = 0; c < 16; ++c)
+          if (c < nc) e[c] = fma(a, Bs[l + (c0 + c) * s], e[c]);
+      }
+#pragma unroll
+    for (int c = 0; c < 16; ++c) {
+      if (c >= nc) break;
+      const T v = (T)e[c];
+      if (live) W[r + (int64_t)(c0 + c) * ldw] = v;
+      const unsigned long long b = live ? abs_bits64((double)v) : 0ull;
+      rmax = umax64(rmax, b);
+      if (wmax.col != nullptr) warp_max_to(b, wmax.col + c0 + c);
+    }
+  }
+  if (live && wmax.row != nullptr) wmax.row[r] = umax64(wmax.row[r], rmax);
+}
+
 template <typename T>
 cudaError_t launch_tsqr_t(const TsqrPlan& p, Seg a, void* q, int64_t ldq, double* R, int32_t ldr,
                           double* work, DevStatus* st, int32_t block, cudaStream_t stream, MaxOut qmax) {
@@ -415,6 +470,29 @@ void tsqr_plan(int64_t m, int32_t s, TsqrPlan* p) {
     }
   }
   p->doubles = round_up(off, 32);
+}
+
+cudaError_t launch_stack_r(const double* recv, int32_t nranks, int32_t s, double* out, const DevStatus* st,
+                           cudaStream_t stream) {
+  stack_r_kernel<<<(nranks * s * s + 255) / 256, 256, 0, stream>>>(recv, nranks, s, out, st);
+  note_launch(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rows_times_small(int64_t m, int32_t s, const void* A, int64_t lda, const double* B, int32_t ldb,
+                                    void* W, int64_t ldw, int32_t fp32, MaxOut wmax, const DevStatus* st,
+                                    cudaStream_t stream) {
+  if (m <= 0) return cudaSuccess;
+  if (s < 1 || s > 64) return cudaErrorInvalidValue;
+  const unsigned grid = (unsigned)ceil_div(m, 256);
+  if (fp32)
+    rows_times_small_kernel<float><<<grid, 256, 0, stream>>>(m, s, reinterpret_cast<const float*>(A), lda, B, ldb,
+                                                              reinterpret_cast<float*>(W), ldw, wmax, st);
+  else
+    rows_times_small_kernel<double><<<grid, 256, 0, stream>>>(m, s, reinterpret_cast<const double*>(A), lda, B, ldb,
+                                                               reinterpret_cast<double*>(W), ldw, wmax, st);
+  note_launch(1);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_tsqr(const TsqrPlan& p, Seg a, void* q, int64_t ldq, int32_t q_fp32, double* R,
