@@ -484,11 +484,20 @@ def bench_small(args, dev, stream):
         syncs = bcgs.profile_read("gram_reduce")[0] + bcgs.profile_read("tsqr")[0]
         bcgs.profile_enable(False)
         ms = _timed(run, 3, 20, stream)
-        out[v] = {"us_per_factorization": ms * 1e3, "kernel_launches": launches, "synchronizations": int(syncs),
-                  "status": bcgs.STATUS[bcgs.factor_status(ws)[0]]}
+        # the same factorization captured once into a CUDA graph and replayed
+        # (one graph launch per factorization: no host launch overhead per kernel)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            run()
+        gms = _timed(g.replay, 3, 50, stream)
+        out[v] = {"us_per_factorization": ms * 1e3, "us_per_factorization_graph": gms * 1e3,
+                  "us_per_block_step_graph": gms * 1e3 / (n // s), "kernel_launches": launches,
+                  "synchronizations": int(syncs), "status": bcgs.STATUS[bcgs.factor_status(ws)[0]]}
+        del g
         del ws
     return {"workload": f"m=10^4 n=64 s=8 kappa={kappa:g}, FP64, L2-resident", "variants": out,
-            "note": "launch- and synchronization-bound: no HBM fraction"}
+            "note": "launch- and synchronization-bound: no HBM fraction; *_graph: one CUDA graph replay "
+                    "per factorization"}
 
 
 def bench_block_sizes(args, dev, stream):

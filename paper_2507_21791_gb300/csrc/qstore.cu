@@ -177,10 +177,13 @@ __global__ void __launch_bounds__(kStoreRows) qsplit_reg_kernel(QStore qs, const
 
 // ---------------------------------------------------------------- projection
 // Persistent, one CTA per SM, warp-specialized:
-//   warp 0      bulk copies of the A digit chunks and the MMAs (one thread);
-//   warps 1..3  per row block: its exponents, the column exponents F_j of B',
-//               and the B' digits of every chunk;
-//   warps 4..11 read-back of the accumulators and the FP64 epilogue.
+//   warp 0       bulk copies of the A digit chunks and the MMAs (one thread);
+//   warps 1..3   per row block: its exponents, the column exponents F_j of B',
+//                and the B' digits of every chunk;
+//   warps 4..11  read-back of the accumulators and the FP64 epilogue;
+//   warps 12..15 (paired form only) the epilogue of the second output: V minus
+//                the products, the triangular solve and the stores, so that the
+//                FP64 solve of block b runs while warps 4..11 read back block b+1.
 // Chunks, B' splits, read-backs and epilogues of consecutive row blocks overlap
 // through mbarriers; two accumulator sets in tensor memory alternate per group
 // of 128 K-values.
@@ -190,18 +193,36 @@ constexpr int kStages = 3;                       // chunks in flight
 constexpr int kATileT = kRows * kK * 2;          // one digit of one chunk: 4 KB
 constexpr int kAStage = kDigits * kATileT;       // 32 KB
 constexpr int kGroupChunks = 8;                  // 128 K-values between read-backs
-constexpr int kExpInts = 2048 + 64;              // s_exp: K <= 2048 + 16
+constexpr int kMaxK = 2048;                      // store columns of one projection at most
 constexpr size_t kDigTile = (size_t)kStoreRows * kStoreCols * 2;  // one digit of a store tile
 constexpr int kCtl = 0;                          // warp roles
 constexpr int kSplit0 = 1, kSplitWarps = 3;
 constexpr int kRead0 = 4, kReadWarps = 8;
-constexpr int kThreads = 32 * (kRead0 + kReadWarps);
-constexpr int kRegsLow = 104, kRegsHigh = 192;   // registers per thread after the split
+constexpr int kEpi0 = 12, kEpiWarps = 4;         // paired form only
+// s_exp (the K block exponents of a row block), rounded to 16 bytes
+__host__ __device__ constexpr size_t exp_bytes(int K) { return ((size_t)(K + 16) * 4 + 15) / 16 * 16; }
+
+// Threads and the register split per warpgroup (setmaxnreg; warpgroup 0 =
+// control + splitters, 1 and 2 = read-back, 3 = epilogue of the paired form).
+// The shares, times 128 threads each, add up to at most the launch's registers
+// (threads x kLaunchRegs); launch_sp checks that against the compiled kernel.
+template <int NOUT>
+struct Roles {
+  static constexpr int kThreads = 32 * (NOUT == 2 ? kEpi0 + kEpiWarps : kRead0 + kReadWarps);
+  static constexpr int kLaunchRegs = NOUT == 2 ? 128 : 168;  // 65536 / threads, a multiple of 8
+  static constexpr int kRegsLow = NOUT == 2 ? 96 : 104;       // control + splitters
+  static constexpr int kRegsHigh = NOUT == 2 ? 168 : 192;     // read-back
+  static constexpr int kRegsEpi = 80;                         // epilogue warps (paired form)
+  static constexpr int kSplitTotal = 128 * (kRegsLow + 2 * kRegsHigh + (NOUT == 2 ? kRegsEpi : 0));
+  static_assert(kSplitTotal <= kThreads * kLaunchRegs, "register split above the launch's registers");
+};
 
 // Output o occupies tile columns [o SMAX, o SMAX + s) (B column o s + jj); with
-// two outputs each read-back thread holds one output of its row, so the
-// epilogue runs from registers and only the single form stages products in P.
-// B itself is staged in shared memory when it fits (kSmemLimit).
+// two outputs each read-back thread holds one output of its row: the first
+// output's epilogue runs from its registers, the second output's products go
+// through W (128 rows x SMAX doubles, column-major) to the epilogue warps; the
+// single form stages products in P.  B itself is staged in shared memory when it
+// fits (kSmemLimit).
 template <int NBT, int NOUT>
 struct SPCfg {
   static constexpr int kBTileT = NBT * kK * 2;   // one digit of one B chunk
@@ -210,9 +231,10 @@ struct SPCfg {
   static constexpr int kAcc = kDigits * NBT;     // TMEM columns of one accumulator set
   static constexpr int kTmem = 2 * kAcc;
   static constexpr int kSmax = NBT / NOUT;       // columns per output
-  static constexpr size_t kPBytes = NOUT == 1 ? (size_t)kRows * NBT * 8 : 0;
-  static constexpr size_t kFixed = 1024 + (size_t)kStages * kAStage + (size_t)kBRing * kBStage + kExpInts * 4 +
-                                   kPBytes + 32 * 32 * 8;
+  static constexpr size_t kPBytes = (size_t)kRows * (NOUT == 1 ? NBT : kSmax) * 8;  // P, or W (paired)
+  // everything but s_exp (exp_bytes(K)) and the staged B
+  static constexpr size_t kFixed = 1024 + (size_t)kStages * kAStage + (size_t)kBRing * kBStage + kPBytes +
+                                   32 * 32 * 8;
 };
 constexpr size_t kSmemLimit = 232448 - 4096;     // dynamic shared memory we ask for at most
 
@@ -269,10 +291,12 @@ __device__ __forceinline__ bool wait_or_abort(uint64_t* mbar, uint32_t parity, v
 }
 
 template <int NBT, int NOUT, bool F32>
-__global__ void __launch_bounds__(kThreads, 1) proj_store_kernel(StoreProjDesc d, int32_t b_staged,
-                                                                  const __grid_constant__ CUtensorMap amap,
-                                                                  int32_t use_amap, DevStatus* st) {
+__global__ void __launch_bounds__(Roles<NOUT>::kThreads, 1) proj_store_kernel(StoreProjDesc d, int32_t b_staged,
+                                                                               const __grid_constant__ CUtensorMap amap,
+                                                                               int32_t use_amap, DevStatus* st) {
   using C = SPCfg<NBT, NOUT>;
+  using Rl = Roles<NOUT>;
+  constexpr int kThreads = Rl::kThreads;
   static_assert(NBT == 16 || NBT == 32, "N tile");
   constexpr int kHalf = NBT / 2;                 // read-back columns per thread
   constexpr int SMAX = C::kSmax;
@@ -286,6 +310,8 @@ __global__ void __launch_bounds__(kThreads, 1) proj_store_kernel(StoreProjDesc d
   __shared__ __align__(8) uint64_t accfree[2];        // accumulator set read (8 warps)
   __shared__ __align__(8) uint64_t fready[2];         // F_j of a block written
   __shared__ __align__(8) uint64_t ffree[2];          // F_j of a block used
+  __shared__ __align__(8) uint64_t wfull;             // paired: W holds the block's second-output products
+  __shared__ __align__(8) uint64_t wempty;            // paired: W read by the epilogue warps
   __shared__ uint32_t tmem_base_s;
   __shared__ int s_F[2][NBT];
   __shared__ double s_inv[32];
@@ -293,19 +319,18 @@ __global__ void __launch_bounds__(kThreads, 1) proj_store_kernel(StoreProjDesc d
   __shared__ int s_bad;
 
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(dyn) + 1023) & ~uintptr_t(1023));
+  const int K = d.c, s = d.s;
   uint8_t* Aring = base;
   uint8_t* Bring = Aring + kStages * kAStage;
-  int* s_exp = reinterpret_cast<int*>(Bring + C::kBRing * C::kBStage);
-  double* P = reinterpret_cast<double*>(reinterpret_cast<uint8_t*>(s_exp) + kExpInts * 4);
+  double* P = reinterpret_cast<double*>(Bring + C::kBRing * C::kBStage);  // W in the paired form
   double* s_T = reinterpret_cast<double*>(reinterpret_cast<uint8_t*>(P) + C::kPBytes);
+  int* s_exp = reinterpret_cast<int*>(s_T + 32 * 32);
   // staged B (b_staged != 0), row-major by tile column: B'_(k, j) at Bsm[k * kLdj + j]; a pitch
   // of NBT + 4 doubles keeps the column-per-lane and pair-per-lane reads at two wavefronts
   constexpr int kLdj = NBT + 4;
-  double* Bsm = s_T + 32 * 32;
+  double* Bsm = reinterpret_cast<double*>(reinterpret_cast<uint8_t*>(s_exp) + exp_bytes(K));
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int K = d.c, s = d.s;
-  const int ncolsB = NOUT * s;
   const int nch = (K + kK - 1) / kK;
   const int ngrp = (nch + kGroupChunks - 1) / kGroupChunks;
   const int64_t nblk = d.qs.nblk;
@@ -332,6 +357,8 @@ __global__ void __launch_bounds__(kThreads, 1) proj_store_kernel(StoreProjDesc d
       mbar_init(&fready[i]);
       mbar_init(&ffree[i]);
     }
+    mbar_init_count(&wfull, 32 * kReadWarps / 2);  // the second output's 128 read-back threads
+    mbar_init_count(&wempty, 32 * kEpiWarps);      // the 128 epilogue threads
   }
   if (has_t) {
     for (int e = tid; e < s * s; e += kThreads) {
@@ -356,7 +383,6 @@ __global__ void __launch_bounds__(kThreads, 1) proj_store_kernel(StoreProjDesc d
   };
   // X and the outputs in the storage type (float when F32; the products and the
   // epilogue stay FP64); the maxima are those of the stored values
-  constexpr int64_t io_size = F32 ? 4 : 8;
   auto vload = [&](const ProjOut& o, int64_t idx) -> double {
     if constexpr (F32)
       return (double)reinterpret_cast<const float*>(o.v)[idx];
@@ -384,12 +410,12 @@ __global__ void __launch_bounds__(kThreads, 1) proj_store_kernel(StoreProjDesc d
   __syncthreads();
   const uint32_t tmem = tmem_base_s;
 
-  // Warpgroup 0 (control + splitters) hands registers to the two read-back
-  // warpgroups: launched 12 warps x 168 = 64512, then 4 warps x kRegsLow +
-  // 8 warps x kRegsHigh = 62464 <= 64512.
-  static_assert(4 * 32 * kRegsLow + 8 * 32 * kRegsHigh <= kThreads * 168, "register split");
-  if (warp < kRead0) setmaxnreg_dec<kRegsLow>();
-  else setmaxnreg_inc<kRegsHigh>();
+  // Warpgroup 0 (control + splitters), and the epilogue warpgroup of the paired
+  // form, hand registers to the two read-back warpgroups (Roles: the shares add
+  // up to at most the launch's registers).
+  if (warp < kRead0) setmaxnreg_dec<Rl::kRegsLow>();
+  else if (warp < kRead0 + kReadWarps) setmaxnreg_inc<Rl::kRegsHigh>();
+  else setmaxnreg_dec<Rl::kRegsEpi>();
 
   if (warp == kCtl) {
     // ------------------------------------------------ copies and MMAs
@@ -472,7 +498,6 @@ __global__ void __launch_bounds__(kThreads, 1) proj_store_kernel(StoreProjDesc d
     // named barriers are still passed by all splitter threads)
     constexpr int kSp = 32 * kSplitWarps;
     const int sp = tid - 32 * kSplit0;          // 0..kSp-1
-    const int sw = warp - kSplit0;
     // F pass: column j = lane, rows k = sw, sw + kSplitWarps, ...
     for (int bi = 0; bi < nbl; ++bi) {
       const int64_t b = blk_of(bi);
@@ -534,7 +559,7 @@ __global__ void __launch_bounds__(kThreads, 1) proj_store_kernel(StoreProjDesc d
         if (lane == 0) mbar_arrive(&bready[slot]);
       }
     }
-  } else {
+  } else if (warp < kRead0 + kReadWarps) {
     // ------------------------------------------------ read-back and epilogue
     // (same rule: after an abort the work is skipped, the named barriers are not)
     const int rt = tid - 32 * kRead0;           // 0..255; TMEM quadrant warp % 4
@@ -543,14 +568,6 @@ __global__ void __launch_bounds__(kThreads, 1) proj_store_kernel(StoreProjDesc d
     const int my_j0 = half * kHalf;
     for (int bi = 0; bi < nbl; ++bi) {
       const int64_t b = blk_of(bi), r0 = b * kRows;
-      if constexpr (NOUT == 2) {
-        // this block's rows of V_1 toward L2 while the accumulators fill
-        const ProjOut& o1 = d.out[1];
-        if (half == 1 && o1.v != nullptr && r0 + qrow < d.m)
-          for (int j = 0; j < s; ++j)
-            asm volatile("prefetch.global.L2 [%0];\n" ::"l"(reinterpret_cast<const char*>(o1.v) +
-                                                            (r0 + qrow + (int64_t)j * o1.ldv) * io_size));
-      }
       long long hi[kHalf], lo[kHalf];
 #pragma unroll
       for (int j = 0; j < kHalf; ++j) hi[j] = lo[j] = 0;
@@ -610,49 +627,48 @@ __global__ void __launch_bounds__(kThreads, 1) proj_store_kernel(StoreProjDesc d
       const int* sF = s_F[bi & 1];
       if constexpr (NOUT == 2) {
         // this warp's output (half) of row qrow, straight from the accumulators
-        const int o = half;
         const int64_t r = r0 + qrow;
         const bool live = fok && !s_abort && r < d.m;
-        const ProjOut& out = d.out[o];
         double w[kHalf];
 #pragma unroll
         for (int j = 0; j < kHalf; ++j)
           w[j] = (live && j < s) ? fixed_to_double(hi[j], lo[j], sF[my_j0 + j]) : 0.0;
         named_bar_sync(2, 32 * kReadWarps);
         if (rt == 0) mbar_arrive(&ffree[bi & 1]);
-        if (live) {
-          if (out.v != nullptr) {
+        if (half == 1) {
+          // the second output's epilogue runs on the epilogue warps: hand them
+          // the products once they have taken the previous block's
+          if (bi >= 1) wait_or_abort(&wempty, (bi - 1) & 1, &s_abort);
+          if (!s_abort) {
+#pragma unroll
+            for (int j = 0; j < kHalf; ++j) P[j * kRows + qrow] = w[j];
+          }
+          mbar_arrive(&wfull);
+        } else {
+          // the first output has no triangular solve (launch_project_store checks)
+          const ProjOut& out = d.out[0];
+          if (live) {
+            if (out.v != nullptr) {
+#pragma unroll
+              for (int j = 0; j < kHalf; ++j)
+                if (j < s) w[j] = vload(out, r + (int64_t)j * out.ldv) - w[j];
+            }
 #pragma unroll
             for (int j = 0; j < kHalf; ++j)
-              if (j < s) w[j] = vload(out, r + (int64_t)j * out.ldv) - w[j];
-          }
-          if (o == NOUT - 1 && has_t) {
+              if (j < s) wstore(out, r + (int64_t)j * out.ldw, w[j]);
+            if (out.wmax.row != nullptr) {
+              unsigned long long mx = 0ull;
 #pragma unroll
-            for (int j = 0; j < kHalf; ++j) {
-              if (j < s) {
-                double x = w[j];
-#pragma unroll
-                for (int l = 0; l < kHalf; ++l)
-                  if (l < j) x = fma(-w[l], s_T[l * 32 + j], x);
-                w[j] = x * s_inv[j];
-              }
+              for (int j = 0; j < kHalf; ++j)
+                if (j < s) mx = umax64(mx, abs_bits64(stored(w[j])));
+              out.wmax.row[r] = umax64(out.wmax.row[r], mx);
             }
           }
-#pragma unroll
-          for (int j = 0; j < kHalf; ++j)
-            if (j < s) wstore(out, r + (int64_t)j * out.ldw, w[j]);
-          if (out.wmax.row != nullptr) {
-            unsigned long long mx = 0ull;
+          if (out.wmax.col != nullptr) {  // warp-uniform
 #pragma unroll
             for (int j = 0; j < kHalf; ++j)
-              if (j < s) mx = umax64(mx, abs_bits64(stored(w[j])));
-            out.wmax.row[r] = umax64(out.wmax.row[r], mx);
+              if (j < s) warp_max_to(live ? abs_bits64(stored(w[j])) : 0ull, out.wmax.col + j);
           }
-        }
-        if (out.wmax.col != nullptr) {  // warp-uniform: o is
-#pragma unroll
-          for (int j = 0; j < kHalf; ++j)
-            if (j < s) warp_max_to(live ? abs_bits64(stored(w[j])) : 0ull, out.wmax.col + j);
         }
       } else {
         // one output: the two halves of a row meet in P, one thread per row
@@ -709,6 +725,61 @@ __global__ void __launch_bounds__(kThreads, 1) proj_store_kernel(StoreProjDesc d
         }
       }
     }
+  } else if constexpr (NOUT == 2) {
+    // ------------------------------------------------ epilogue of the second output (paired form)
+    // One thread per row of the block: V minus the products (from W), the
+    // triangular solve, the stores and the maxima.  Only bounded mbarrier waits;
+    // after an abort the work is skipped.
+    constexpr int kSm = C::kSmax;
+    const int i = tid - 32 * kEpi0;
+    const ProjOut& out = d.out[1];
+    for (int bi = 0; bi < nbl; ++bi) {
+      const int64_t r = blk_of(bi) * kRows + i;
+      const bool inrow = r < d.m;
+      // V of this row is loaded while the read-back finishes the block
+      double v[kSm];
+#pragma unroll
+      for (int j = 0; j < kSm; ++j) v[j] = (out.v != nullptr && inrow && j < s) ? vload(out, r + (int64_t)j * out.ldv) : 0.0;
+      const bool ok = wait_or_abort(&wfull, bi & 1, &s_abort);
+      double w[kSm];
+#pragma unroll
+      for (int j = 0; j < kSm; ++j) w[j] = P[j * kRows + i];
+      mbar_arrive(&wempty);
+      const bool live = ok && !s_abort && inrow;
+      if (live) {
+        if (out.v != nullptr) {
+#pragma unroll
+          for (int j = 0; j < kSm; ++j) w[j] = v[j] - w[j];
+        }
+        if (has_t) {
+#pragma unroll
+          for (int j = 0; j < kSm; ++j) {
+            if (j < s) {
+              double x = w[j];
+#pragma unroll
+              for (int l = 0; l < kSm; ++l)
+                if (l < j) x = fma(-w[l], s_T[l * 32 + j], x);
+              w[j] = x * s_inv[j];
+            }
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < kSm; ++j)
+          if (j < s) wstore(out, r + (int64_t)j * out.ldw, w[j]);
+        if (out.wmax.row != nullptr) {
+          unsigned long long mx = 0ull;
+#pragma unroll
+          for (int j = 0; j < kSm; ++j)
+            if (j < s) mx = umax64(mx, abs_bits64(stored(w[j])));
+          out.wmax.row[r] = umax64(out.wmax.row[r], mx);
+        }
+      }
+      if (out.wmax.col != nullptr) {  // warp-uniform
+#pragma unroll
+        for (int j = 0; j < kSm; ++j)
+          if (j < s) warp_max_to(live ? abs_bits64(stored(w[j])) : 0ull, out.wmax.col + j);
+      }
+    }
   }
   tc_before_sync();
   __syncthreads();
@@ -753,12 +824,26 @@ bool store_tensor_map(const QStore& qs, CUtensorMap* map) {
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// The kernel was compiled with at least the registers its split hands out.
+template <int NBT, int NOUT, bool F32>
+bool split_regs_ok() {
+  cudaFuncAttributes fa;
+  return cudaFuncGetAttributes(&fa, proj_store_kernel<NBT, NOUT, F32>) == cudaSuccess &&
+         (int64_t)fa.numRegs * Roles<NOUT>::kThreads >= Roles<NOUT>::kSplitTotal;
+}
+
 template <int NBT, int NOUT, bool F32>
 cudaError_t launch_sp(const StoreProjDesc& d, DevStatus* st, cudaStream_t stream) {
   using C = SPCfg<NBT, NOUT>;
+  using Rl = Roles<NOUT>;
   const size_t bbytes = (size_t)(NBT + 4) * (size_t)d.c * sizeof(double);
-  const int32_t staged = C::kFixed + bbytes <= kSmemLimit ? 1 : 0;
-  const size_t smem = C::kFixed + (staged ? bbytes : 0);
+  const size_t fixed = C::kFixed + exp_bytes(d.c);
+  const int32_t staged = fixed + bbytes <= kSmemLimit ? 1 : 0;
+  const size_t smem = fixed + (staged ? bbytes : 0);
+  // the register split draws on the registers the CTA is launched with: refuse a
+  // build whose kernel was compiled with fewer than the split adds up to
+  static const bool regs_ok = split_regs_ok<NBT, NOUT, F32>();
+  if (!regs_ok) return cudaErrorInvalidConfiguration;
   cudaError_t e = ensure_dyn_smem(proj_store_kernel<NBT, NOUT, F32>, smem);
   if (e != cudaSuccess) return e;
   int sms = g_sm_count;
@@ -777,7 +862,7 @@ cudaError_t launch_sp(const StoreProjDesc& d, DevStatus* st, cudaStream_t stream
   CUtensorMap amap;
   memset(&amap, 0, sizeof(amap));
   const int32_t use_amap = store_tensor_map(d.qs, &amap) ? 1 : 0;
-  proj_store_kernel<NBT, NOUT, F32><<<grid, kThreads, smem, stream>>>(d, staged, amap, use_amap, st);
+  proj_store_kernel<NBT, NOUT, F32><<<grid, Rl::kThreads, smem, stream>>>(d, staged, amap, use_amap, st);
   return cudaSuccess;
 }
 
@@ -815,7 +900,7 @@ bool project_store_supported(int32_t s, int32_t nouts) {
 }
 
 cudaError_t launch_project_store(const StoreProjDesc& d, DevStatus* st, cudaStream_t stream) {
-  if (!project_store_supported(d.s, d.nouts) || d.c < 0 || d.c > kExpInts - 64 || d.c > d.qs.ld_exp ||
+  if (!project_store_supported(d.s, d.nouts) || d.c < 0 || d.c > kMaxK || d.c > d.qs.ld_exp ||
       d.qs.nblk < ceil_div(d.m, kRows) || d.fexp == nullptr)
     return cudaErrorInvalidValue;
   for (int o = 0; o + 1 < d.nouts; ++o)
