@@ -90,6 +90,8 @@ def parse():
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     p.add_argument("--no-forms", action="store_true",
                    help="skip the FP32-storage, batched and serving forms")
+    p.add_argument("--forms", default="small_config,fp32_storage,block_sizes,batched,serving",
+                   help="comma-separated forms to time (default: all)")
     p.add_argument("--kernel", default=None, choices=["gram", "project", "tsqr"],
                    help="time one building block alone (for profiling on small cases)")
     p.add_argument("--m", type=int, default=2 ** 19, help="rows for --kernel")
@@ -318,11 +320,16 @@ def main_ours(args):
     forms = None
     if not args.no_forms and world == 1:
         del main["Q"], main["R"]
-        forms = {"small_config": bench_small(args, dev, stream),
-                 "fp32_storage": bench_fp32(args, dev, stream),
-                 "block_sizes": bench_block_sizes(args, dev, stream),
-                 "batched": bench_batched(args, dev, stream),
-                 "serving": bench_serving(args, dev)}
+        runners = {"small_config": lambda: bench_small(args, dev, stream),
+                   "fp32_storage": lambda: bench_fp32(args, dev, stream),
+                   "block_sizes": lambda: bench_block_sizes(args, dev, stream),
+                   "batched": lambda: bench_batched(args, dev, stream),
+                   "serving": lambda: bench_serving(args, dev)}
+        wanted = [f for f in args.forms.split(",") if f]
+        unknown = [f for f in wanted if f not in runners]
+        if unknown:
+            raise SystemExit(f"unknown forms: {unknown}")
+        forms = {f: runners[f]() for f in wanted}
 
     prof = main["prof"]
     peaks = measured_peaks()
@@ -386,7 +393,7 @@ def main_ours(args):
         "cpu_baseline": cpu,
         "forms": forms,
         "p99_latency_ms": (forms["serving"]["lambda_2000"]["call_latency_ms"]["p99"]
-                           if forms else None),
+                           if forms and "serving" in forms else None),
     }
     print(json.dumps(line), flush=True)
     if world > 1:
@@ -482,6 +489,7 @@ def bench_small(args, dev, stream):
         run()
         torch.cuda.synchronize()
         syncs = bcgs.profile_read("gram_reduce")[0] + bcgs.profile_read("tsqr")[0]
+        classes = {k: round(bcgs.profile_read(k)[1] * 1e3, 1) for k in bcgs.PROFILE_CLASSES}
         bcgs.profile_enable(False)
         ms = _timed(run, 3, 20, stream)
         # the same factorization captured once into a CUDA graph and replayed
@@ -491,7 +499,8 @@ def bench_small(args, dev, stream):
             run()
         gms = _timed(g.replay, 3, 50, stream)
         out[v] = {"us_per_factorization": ms * 1e3, "us_per_factorization_graph": gms * 1e3,
-                  "us_per_block_step_graph": gms * 1e3 / (n // s), "kernel_launches": launches,
+                  "us_per_block_step_graph": gms * 1e3 / (n // s), "us_per_class_eager": classes,
+                  "kernel_launches": launches,
                   "synchronizations": int(syncs), "status": bcgs.STATUS[bcgs.factor_status(ws)[0]]}
         del g
         del ws
@@ -530,9 +539,10 @@ def bench_block_sizes(args, dev, stream):
 
 def bench_batched(args, dev, stream):
     """Batched form: 512 FP64 QRs, m = round(2^U(12,18)), n in {32, 64, 128},
-    kappa = 10^U(1,8), s picked by the autotuner from {4, 8, 16}; BCGSI+P-2S
-    (kappa up to 1e8 is outside BCGSI+P-1S's O(u) kappa^2 <= 1 range); the
-    batch is one CUDA-graph launch."""
+    kappa = 10^U(1,8), s and the product engine (FP64 pipe or tensor cores)
+    picked per shape by the autotuner from {4, 8, 16} x {fp64, tensor};
+    BCGSI+P-2S (kappa up to 1e8 is outside BCGSI+P-1S's O(u) kappa^2 <= 1
+    range); the batch is one CUDA-graph launch."""
     import numpy as np
     import torch
 
@@ -540,8 +550,8 @@ def bench_batched(args, dev, stream):
     from paper_2507_21791_gb300.batched import Batch, BlockSizeTuner, alg_bytes
 
     rng = np.random.default_rng(1300)
-    tuner = BlockSizeTuner(candidates=(4, 8, 16), variant="bcgsi+p-2s")
-    Xs, ss, total = [], [], 0.0
+    tuner = BlockSizeTuner(candidates=(4, 8, 16), variant="bcgsi+p-2s", engines=("fp64", "tensor"))
+    Xs, ss, engs, total = [], [], [], 0.0
     for i in range(512):
         m = synth.log_uniform_int(rng, 12, 18)
         n = int(rng.choice([32, 64, 128]))
@@ -549,16 +559,19 @@ def bench_batched(args, dev, stream):
         Xs.append(synth.make_matrix_torch(m, n, kappa, seed=1300 + i, device=str(dev)))
     for X in Xs:
         m, n = X.shape
-        ss.append(tuner.pick(m, n, device=str(dev)))
+        s_, e_ = tuner.choose(m, n, device=str(dev))
+        ss.append(s_)
+        engs.append(e_)
         total += alg_bytes(m, n, ss[-1], "bcgsi+p-2s")
-    b = Batch(Xs, ss, variant="bcgsi+p-2s")
+    b = Batch(Xs, ss, variant="bcgsi+p-2s", engines=engs)
     b.capture()
     ms = _timed(b.replay, args.warmup, args.steps, stream)
     codes, _ = b.status()
     return {"workload": "512 FP64 QRs m=2^U(12,18) n in {32,64,128} kappa=10^U(1,8) BCGSI+P-2S, "
                         "one CUDA-graph launch", "value": total / (ms * 1e-3) / 1e9, "unit": "GB/s",
             "instances_per_s": 512 / (ms * 1e-3), "ms_per_batch": ms,
-            "failed": sum(1 for c in codes if c != 0), "autotuned_s": tuner.table}
+            "failed": sum(1 for c in codes if c != 0),
+            "autotuned_s_engine": {k: list(v) for k, v in sorted(tuner.table.items())}}
 
 
 def bench_serving(args, dev):

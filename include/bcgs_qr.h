@@ -266,7 +266,10 @@ typedef struct {
   const void* X; int64_t ldx;
   void* Q; int64_t ldq;
   double* R; int32_t ldr;
-  int32_t pad_;
+  int32_t engine;    /* product engine of this problem: 0 = the BCGS_OPT_GRAM_ENGINE option;
+                        otherwise 1 + an option value (1 FP64 pipe, 2 tensor cores from
+                        BCGS_OPT_TC_MIN_ROWS rows, 3 tensor cores always); other values
+                        are INVALID_ARG.  It decides the workspace (the digit store) too. */
 } bcgs_problem;
 
 /* Workspace for a batch (host array `probs` of `count` problems). */

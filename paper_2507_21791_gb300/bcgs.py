@@ -30,7 +30,10 @@ class Problem(ctypes.Structure):
     """bcgs_problem."""
     _fields_ = [("m", _i64), ("n", _i32), ("s", _i32), ("variant", _i32), ("precision", _i32),
                 ("X", _vp), ("ldx", _i64), ("Q", _vp), ("ldq", _i64), ("R", _vp), ("ldr", _i32),
-                ("pad_", _i32)]
+                ("engine", _i32)]
+
+# bcgs_problem.engine: 0 = the global option, else 1 + the option value
+PROBLEM_ENGINES = {"default": 0, "fp64": 1, "auto": 2, "tensor": 3}
 
 
 SIGNATURES = [

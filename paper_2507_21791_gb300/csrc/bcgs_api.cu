@@ -139,8 +139,21 @@ namespace bcgs {
 namespace {
 std::atomic<int> g_engine{1};
 std::atomic<long long> g_tc_min_rows{16384};
+// Engine of the factorization being enqueued on this thread when a batched
+// problem names its own (-1: the BCGS_OPT_GRAM_ENGINE option).
+thread_local int t_engine = -1;
 }  // namespace
-int gram_engine() { return g_engine.load(); }
+int gram_engine() {
+  const int t = t_engine;
+  return t >= 0 ? t : g_engine.load();
+}
+// Sets the engine of this thread's enqueues for a scope (bcgs_problem::engine:
+// 0 = the option, 1 + the option's value otherwise).
+struct EngineScope {
+  int prev;
+  explicit EngineScope(int problem_engine) : prev(t_engine) { t_engine = problem_engine > 0 ? problem_engine - 1 : -1; }
+  ~EngineScope() { t_engine = prev; }
+};
 int64_t gram_tc_min_rows() { return g_tc_min_rows.load(); }
 bool use_tensor_gram(const GramDesc& d) {
   const int e = gram_engine();
@@ -1257,6 +1270,8 @@ int bcgs_qr_batched_workspace_size(int32_t count, const bcgs_problem* probs, siz
   for (int i = 0; i < count; ++i) {
     size_t b = 0;
     const bcgs_problem& p = probs[i];
+    if (p.engine < 0 || p.engine > 3) return BCGS_ERR_INVALID_ARG;
+    const EngineScope es(p.engine);  // the engine decides whether the workspace holds a digit store
     if (bcgs_qr_workspace_size(p.m, p.n, p.s, p.variant, p.precision, &b) != BCGS_OK)
       return BCGS_ERR_INVALID_ARG;
     total += align256(b);
@@ -1306,6 +1321,7 @@ int bcgs_qr_factor_batched(int32_t count, const bcgs_problem* probs, void* works
     work[i] = (double)probs[i].m * probs[i].n * probs[i].n;
     offs[i] = off;
     size_t b = 0;
+    const EngineScope es(probs[i].engine);
     bcgs_qr_workspace_size(probs[i].m, probs[i].n, probs[i].s, probs[i].variant, probs[i].precision, &b);
     off += align256(b);
   }
@@ -1324,6 +1340,7 @@ int bcgs_qr_factor_batched(int32_t count, const bcgs_problem* probs, void* works
       if (load[l] < load[lane]) lane = l;
     load[lane] += work[i] + 1e7;  // + a per-problem launch cost
     const bcgs_problem& p = probs[i];
+    const EngineScope es(p.engine);
     size_t b = 0;
     bcgs_qr_workspace_size(p.m, p.n, p.s, p.variant, p.precision, &b);
     cudaStream_t ls = bs->lane[lane];

@@ -145,6 +145,31 @@ def test_overlapping_x_and_q_rejected_without_a_gpu(precision, esz):
     assert lib.bcgs_qr_factor_batched(2, probs, 1 << 44, need.value, None) == 1
 
 
+def test_batched_problem_engine_field():
+    """bcgs_problem.engine: 0..3 accepted, anything else INVALID_ARG; with the
+    tensor engine for every size the workspace holds the digit store (larger),
+    with the FP64 pipe it does not (host-only: no GPU needed)."""
+    ensure_library()
+    from paper_2507_21791_gb300 import bcgs
+
+    lib = bcgs.load_library()
+    m, n, s = 4096, 64, 16
+    sizes = {}
+    for name, eng in bcgs.PROBLEM_ENGINES.items():
+        probs = (bcgs.Problem * 1)()
+        probs[0] = bcgs.Problem(m, n, s, 1, 0, 1 << 40, m, 1 << 42, m, 1 << 44, n, eng)
+        need = ctypes.c_size_t(0)
+        assert lib.bcgs_qr_batched_workspace_size(1, probs, ctypes.byref(need)) == 0
+        sizes[name] = need.value
+    assert sizes["tensor"] > sizes["fp64"]
+    assert sizes["auto"] == sizes["fp64"]  # 4096 rows: below the default tensor-core threshold
+    for bad in (-1, 4):
+        probs = (bcgs.Problem * 1)()
+        probs[0] = bcgs.Problem(m, n, s, 1, 0, 1 << 40, m, 1 << 42, m, 1 << 44, n, bad)
+        need = ctypes.c_size_t(0)
+        assert lib.bcgs_qr_batched_workspace_size(1, probs, ctypes.byref(need)) == 1
+
+
 def test_debug_sync_option():
     ensure_library()
     from paper_2507_21791_gb300 import bcgs

@@ -66,6 +66,38 @@ def test_batched_matches_single_and_graph_replay(cuda):
         assert torch.equal(q0, q) and torch.equal(r0, r)
 
 
+def test_batched_per_problem_engines(cuda):
+    """Problems that name their own engine (FP64 pipe, tensor cores from the
+    threshold, tensor cores always) in one batch: each gives the bits of
+    bcgs_qr_factor under that engine alone, and agrees with the oracle; the
+    global option is left as it was."""
+    import torch
+
+    from paper_2507_21791_gb300.batched import Batch
+
+    shapes = [(5000, 32, 8, "tensor"), (5000, 32, 8, "fp64"), (20000, 64, 16, "fp64"),
+              (20000, 64, 16, "auto"), (9000, 64, 16, "tensor"), (3000, 32, 4, "tensor")]
+    Xh = [synth.make_matrix_np(m, n, 1e4, seed=900 + i) for i, (m, n, _, _) in enumerate(shapes)]
+    Xs = [cuda.to_device_colmajor(X) for X in Xh]
+    ss = [s for _, _, s, _ in shapes]
+    engines = [e for _, _, _, e in shapes]
+    before = cuda.get_gram_engine()
+    b = Batch(Xs, ss, variant="bcgsi+p-2s", engines=engines)
+    b.enqueue()
+    codes, _ = b.status()
+    assert codes == [0] * len(Xs)
+    assert cuda.get_gram_engine() == before
+    for i, (X, s, eng) in enumerate(zip(Xs, ss, engines)):
+        cuda.set_gram_engine(eng)
+        try:
+            Q, R, code, _ = cuda.factor(X, s, "bcgsi+p-2s")
+        finally:
+            cuda.set_gram_engine(before)
+        assert code == 0
+        assert torch.equal(Q, b.Qs[i]) and torch.equal(R, b.Rs[i])
+        check_oracle(Xh[i], b.Qs[i].cpu().numpy(), b.Rs[i].cpu().numpy(), s, "bcgsi+p-2s")
+
+
 def test_batched_store_path_every_variant_against_oracle(cuda):
     """Instances of m >= 16384 rows, n = 128 and s in {8, 16}: the batch runs the
     digit-store kernels (tensor-core Gram and projection).  Mixed variants in one

@@ -131,10 +131,13 @@ def test_block_size_tuner_keys_and_persistence(tmp_path):
 
     t = BlockSizeTuner(path=str(tmp_path / "t.json"))
     assert t.key(4096, 64) == "12:64" and t.key(5000, 64) == "12:64" and t.key(6000, 64) == "13:64"
-    t.table["12:64"] = 8
+    t.table["12:64"] = (8, "fp64")
     t.save()
     t2 = BlockSizeTuner(path=str(tmp_path / "t.json"))
-    assert t2.pick(4096, 64) == 8  # cached, no GPU needed
+    assert t2.pick(4096, 64) == 8 and t2.pick_engine(4096, 64) == "fp64"  # cached, no GPU needed
+    # a table saved with s only reads as the default engine
+    (tmp_path / "old.json").write_text('{"13:32": 16}')
+    assert BlockSizeTuner(path=str(tmp_path / "old.json")).choose(8192, 32) == (16, "auto")
     assert alg_bytes(1000, 64, 8, "bcgsi+") > alg_bytes(1000, 64, 8, "bcgsi+p-2s") > alg_bytes(1000, 64, 8, "bcgsi+p-1s")
 
 
