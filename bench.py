@@ -498,8 +498,24 @@ def bench_small(args, dev, stream):
         with torch.cuda.graph(g):
             run()
         gms = _timed(g.replay, 3, 50, stream)
+        # the same with the tensor-core engine at this size (digit store, exact digit products)
+        saved = bcgs.get_gram_engine()
+        bcgs.set_gram_engine("tensor")
+        try:
+            ws_t = torch.empty(bcgs.workspace_size(m, n, s, v), dtype=torch.uint8, device=dev)
+            gt = torch.cuda.CUDAGraph()
+            bcgs.factor_async(X, s, v, "fp64", Q, R, ws_t)
+            torch.cuda.synchronize()
+            with torch.cuda.graph(gt):
+                bcgs.factor_async(X, s, v, "fp64", Q, R, ws_t)
+            tms = _timed(gt.replay, 3, 50, stream)
+            tstatus = bcgs.STATUS[bcgs.factor_status(ws_t)[0]]
+            del gt, ws_t
+        finally:
+            bcgs.set_gram_engine(saved)
         out[v] = {"us_per_factorization": ms * 1e3, "us_per_factorization_graph": gms * 1e3,
                   "us_per_block_step_graph": gms * 1e3 / (n // s), "us_per_class_eager": classes,
+                  "us_per_factorization_graph_tensor_engine": tms * 1e3, "status_tensor_engine": tstatus,
                   "kernel_launches": launches,
                   "synchronizations": int(syncs), "status": bcgs.STATUS[bcgs.factor_status(ws)[0]]}
         del g

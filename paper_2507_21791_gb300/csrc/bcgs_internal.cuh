@@ -104,7 +104,7 @@ size_t gram_partial_doubles(int64_t m, int32_t na, int32_t nb);
 // Launchers (return cudaError_t of the launch).
 cudaError_t launch_gram(const GramDesc& d, double* partial, double* G, int ldg,
                         DevStatus* st, cudaStream_t stream);
-// Chunk partials -> G, added in chunk order.
+// Chunk partials -> G, added in a fixed order that depends on the chunk count only.
 cudaError_t launch_gram_reduce(const double* partial, int32_t nchunks, int32_t na, int32_t nb,
                                double* G, int32_t ldg, const DevStatus* st, cudaStream_t stream);
 // Tensor-core Gram (gram_tc.cu): same partition and partial layout; needs

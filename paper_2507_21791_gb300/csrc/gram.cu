@@ -103,19 +103,32 @@ gram_partial_kernel(GramDesc d, ColMap cm, int32_t na_g, int32_t tr, double* __r
   }
 }
 
-// G[i + j*ldg] = sum over chunks, in chunk order.
-__global__ void gram_reduce_kernel(const double* __restrict__ partial, int32_t nchunks, int32_t na,
-                                   int32_t nb, double* __restrict__ G, int32_t ldg,
-                                   const DevStatus* st) {
-  if (failed(st)) return;
-  const int o = blockIdx.x * blockDim.x + threadIdx.x;
+// G[i + j*ldg] = sum over chunks in a fixed order that depends on nchunks only:
+// warp w of a CTA adds the chunks c = w, w + 8, ... in turn, then the eight
+// warp sums are added as a fixed tree.  One CTA per 32 consecutive outputs (each
+// warp load is 256 contiguous bytes of one chunk), so the FP64 additions spread
+// over many SMs instead of one long chain per output.
+constexpr int kReduceWarps = 8;
+__global__ void __launch_bounds__(32 * kReduceWarps)
+gram_reduce_kernel(const double* __restrict__ partial, int32_t nchunks, int32_t na, int32_t nb,
+                   double* __restrict__ G, int32_t ldg, const DevStatus* st) {
+  if (failed(st)) return;  // the same for every thread: nothing sets it during this kernel
+  __shared__ double part[kReduceWarps][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int nout = na * nb;
-  if (o >= nout) return;
+  const int o = blockIdx.x * 32 + lane;
   double sum = 0.0;
-  for (int c = 0; c < nchunks; ++c) sum += __ldcg(partial + (size_t)c * nout + o);
-  const int i = o / nb;
-  const int j = o - i * nb;
-  G[i + (size_t)j * ldg] = sum;
+  if (o < nout)
+    for (int c = w; c < nchunks; c += kReduceWarps) sum += __ldcg(partial + (size_t)c * nout + o);
+  part[w][lane] = sum;
+  __syncthreads();
+  if (w == 0 && o < nout) {
+    const double t = ((part[0][lane] + part[1][lane]) + (part[2][lane] + part[3][lane])) +
+                     ((part[4][lane] + part[5][lane]) + (part[6][lane] + part[7][lane]));
+    const int i = o / nb;
+    const int j = o - i * nb;
+    G[i + (size_t)j * ldg] = t;
+  }
 }
 
 // G = the sum over ranks, in rank order, of the gathered copies of the local
@@ -192,8 +205,8 @@ cudaError_t launch_gram_reduce(const double* partial, int32_t nchunks, int32_t n
                                double* G, int32_t ldg, const DevStatus* st, cudaStream_t stream) {
   const int nout_all = na * nb;
   const int slot2 = prof_begin(stream);
-  gram_reduce_kernel<<<(nout_all + 255) / 256, 256, 0, stream>>>(partial, nchunks, na, nb, G, ldg,
-                                                                  st);
+  gram_reduce_kernel<<<(nout_all + 31) / 32, 32 * kReduceWarps, 0, stream>>>(partial, nchunks, na, nb, G, ldg,
+                                                                              st);
   prof_end(slot2, kProfGramReduce, stream, (double)nchunks * nout_all,
            (double)nchunks * nout_all * 8.0 + nout_all * 8.0);
   note_launch(1);

@@ -21,8 +21,8 @@
 //
 // The error of one product term is at most 2^-57.1 max|a_i| max|b_j| (dropped
 // digit pairs and truncation); the integer sums are exact, so the chunk
-// partial carries one FP64 rounding.  The partials are added in chunk order by
-// the reduction kernel of gram.cu.  (Fixed point relative to the column maximum
+// partial carries one FP64 rounding.  The partials are added in a fixed order
+// (a function of the chunk count) by the reduction kernel of gram.cu.  (Fixed point relative to the column maximum
 // loses log2(max|a_i| / |a_ri|) bits on small entries; 64 bits keep heavy-tailed
 // columns, such as rows with lognormal norms, at FP64-level accuracy.)
 //

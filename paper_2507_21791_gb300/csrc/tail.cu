@@ -15,20 +15,46 @@ namespace bcgs {
 
 namespace {
 
-constexpr int kTailThreads = 256;
+constexpr int kTailThreads = 1024;
 constexpr int kMaxS = 64;
 
 // C (s x s, smem, ld s) = A^T B over `rows` rows; A, B column-major (lda, ldb).
+// With s^2 <= blockDim / 2 each entry takes g = blockDim / s^2 threads: thread
+// part p adds the rows p, p + g, ... and the g sums are added in part order (a
+// fixed order: the result depends on the shape and blockDim only), so the FP64
+// chains are g times shorter.  Called by every thread of the CTA.
 __device__ void small_tn(int rows, int s, const double* A, int lda, const double* B, int ldb,
                          double* C) {
-  for (int e = threadIdx.x; e < s * s; e += blockDim.x) {
+  __shared__ double red[kTailThreads];
+  const int ss = s * s;
+  const int g = (int)blockDim.x / ss;
+  if (g < 2) {
+    for (int e = threadIdx.x; e < ss; e += blockDim.x) {
+      const int i = e % s, j = e / s;
+      const double* a = A + (size_t)i * lda;
+      const double* b = B + (size_t)j * ldb;
+      double acc = 0.0;
+      for (int r = 0; r < rows; ++r) acc = fma(a[r], b[r], acc);
+      C[e] = acc;
+    }
+    return;
+  }
+  const int e = threadIdx.x % ss, part = threadIdx.x / ss;
+  double acc = 0.0;
+  if (part < g) {
     const int i = e % s, j = e / s;
     const double* a = A + (size_t)i * lda;
     const double* b = B + (size_t)j * ldb;
-    double acc = 0.0;
-    for (int r = 0; r < rows; ++r) acc = fma(a[r], b[r], acc);
-    C[e] = acc;
+    for (int r = part; r < rows; r += g) acc = fma(a[r], b[r], acc);
   }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  if (threadIdx.x < ss) {
+    double t = red[threadIdx.x];
+    for (int p = 1; p < g; ++p) t += red[threadIdx.x + p * ss];
+    C[threadIdx.x] = t;
+  }
+  __syncthreads();
 }
 
 // Upper Cholesky factor of the s x s matrix M (smem, ld s, upper triangle read)

@@ -214,26 +214,32 @@ tsqr_node_factor(TsqrPlan p, int32_t level, double* work, double* R, int32_t ldr
   const int s = p.s, fan = p.fan, rows = fan * s;
   const int n = blockIdx.x;
   const int nchild = min(fan, p.nodes[level - 1] - n * fan);
+  // only the nchild stacked factors: the rows past them are zero and would
+  // change nothing but the work (compact in shared memory, ld = re)
+  const int re = nchild * s;
   double* A = sm;
   double* G = work + p.off_lvl[level] + (size_t)n * rows * s;
-  for (int e = threadIdx.x; e < rows * s; e += kTsqrThreads) {
-    const int r = e % rows;
-    A[e] = r < nchild * s ? G[e] : 0.0;
+  for (int e = threadIdx.x; e < re * s; e += kTsqrThreads) {
+    const int r = e % re, j = e / re;
+    A[e] = G[r + (size_t)j * rows];
   }
   __syncthreads();
-  block_householder(A, rows, s, tau);
-  for (int e = threadIdx.x; e < rows * s; e += kTsqrThreads) G[e] = A[e];
+  block_householder(A, re, s, tau);
+  for (int e = threadIdx.x; e < re * s; e += kTsqrThreads) {
+    const int r = e % re, j = e / re;
+    G[r + (size_t)j * rows] = A[e];
+  }
   double* tg = work + p.off_tau[level] + (size_t)n * s;
   for (int j = threadIdx.x; j < s; j += kTsqrThreads) tg[j] = tau[j];
   if (level == p.nlevels - 1) {
-    finish_root(A, rows, s, R, ldr, work + p.off_b[level], st, block);
+    finish_root(A, re, s, R, ldr, work + p.off_b[level], st, block);
     return;
   }
   double* P = work + p.off_lvl[level + 1] + (size_t)(n / fan) * rows * s;
   const int rbase = (n % fan) * s;
   for (int e = threadIdx.x; e < s * s; e += kTsqrThreads) {
     const int i = e % s, j = e / s;
-    P[rbase + i + (size_t)j * rows] = i <= j ? A[i + (size_t)j * rows] : 0.0;
+    P[rbase + i + (size_t)j * rows] = i <= j ? A[i + (size_t)j * re] : 0.0;
   }
 }
 
@@ -245,23 +251,24 @@ tsqr_node_apply(TsqrPlan p, int32_t level, double* work, const DevStatus* st) {
   const int s = p.s, fan = p.fan, rows = fan * s;
   const int n = blockIdx.x;
   const int nchild = min(fan, p.nodes[level - 1] - n * fan);
+  const int re = nchild * s;  // the rows tsqr_node_factor factored (compact, ld = re)
   double* V = sm;
-  double* E = sm + (size_t)rows * s;
+  double* E = sm + (size_t)re * s;
   const double* G = work + p.off_lvl[level] + (size_t)n * rows * s;
   const double* B = work + p.off_b[level] + (size_t)n * s * s;
-  for (int e = threadIdx.x; e < rows * s; e += kTsqrThreads) {
-    const int r = e % rows, j = e / rows;
-    V[e] = G[e];
+  for (int e = threadIdx.x; e < re * s; e += kTsqrThreads) {
+    const int r = e % re, j = e / re;
+    V[e] = G[r + (size_t)j * rows];
     E[e] = r < s ? B[r + (size_t)j * s] : 0.0;
   }
   for (int j = threadIdx.x; j < s; j += kTsqrThreads) tau[j] = work[p.off_tau[level] + (size_t)n * s + j];
   __syncthreads();
-  block_apply_q(V, tau, E, rows, s);
+  block_apply_q(V, tau, E, re, s);
   for (int e = threadIdx.x; e < nchild * s * s; e += kTsqrThreads) {
     const int g = e / (s * s), rem = e % (s * s);
     const int i = rem % s, j = rem / s;
     work[p.off_b[level - 1] + (size_t)(n * fan + g) * s * s + i + (size_t)j * s] =
-        E[g * s + i + (size_t)j * rows];
+        E[g * s + i + (size_t)j * re];
   }
 }
 
@@ -436,10 +443,16 @@ cudaError_t launch_tsqr_t(const TsqrPlan& p, Seg a, void* q, int64_t ldq, double
 void tsqr_plan(int64_t m, int32_t s, TsqrPlan* p) {
   p->m = m;
   p->s = s;
-  // Leaf tiles of about 8192 doubles (64 KB of shared memory), at least s rows.
+  // Leaf tiles of at most about 8192 doubles (64 KB of shared memory), and no
+  // taller than needed for about two tiles per SM of a 152-SM GB300: a tile's
+  // Householder runs its columns one after the other on the FP64 pipe of one
+  // SM, so a few tall tiles would leave most SMs idle on small blocks.  At
+  // least 2s rows (a fan-in of two), a multiple of 32.
   int64_t mt = round_up(8192 / s, 32);
   if (mt > 1024) mt = 1024;
-  if (mt < round_up(s, 32)) mt = round_up(s, 32);
+  const int64_t spread = round_up(ceil_div(m, 304), 32);
+  if (mt > spread) mt = spread;
+  if (mt < round_up(2 * s, 32)) mt = round_up(2 * s, 32);
   if (mt > round_up(m, 32)) mt = round_up(m, 32) < s ? s : round_up(m, 32);
   p->mt = (int32_t)mt;
   int fan = (int)(mt / s);
