@@ -97,6 +97,10 @@ def parse():
     p.add_argument("--m", type=int, default=2 ** 19, help="rows for --kernel")
     p.add_argument("--rows", type=int, default=None,
                    help="rows of the factorization (default 2^22; smaller for profiling captures)")
+    p.add_argument("--partition", default="rows", choices=["rows", "replicas"],
+                   help="with N > 1 GPUs: rows = one factorization of the stacked N x 2^22-row matrix, each "
+                        "rank holding 2^22 rows (Sec. 3, one all-gather per synchronization over NCCL); "
+                        "replicas = N independent factorizations")
     p.add_argument("--engine", default="auto", choices=["auto", "fp64", "tensor"],
                    help="inner-product engine of the Gram and projection kernels")
     return p.parse_args()
@@ -231,12 +235,39 @@ def main_ours(args):
     X = synth.make_matrix_torch(Mr, N, KAPPA, seed=1000 + 1 * 100 + rank, device=str(dev))
     torch.cuda.synchronize()
 
+    # N > 1 GPUs, row partition (Sec. 3): this rank's X is its 2^22-row slab of the
+    # stacked matrix, and every synchronization all-gathers the ranks' local Grams
+    # (or TSQR factors) over NCCL; the library adds them in rank order
+    by_rows = world > 1 and args.partition == "rows"
+    if by_rows:
+        from paper_2507_21791_gb300 import rows as rows_mod
+
+        comm = rows_mod.TorchAllGather()
+
+    def workspace_for(variant):
+        if by_rows:
+            return torch.empty(rows_mod.workspace_size_rows(Mr, N, S, variant, world), dtype=torch.uint8,
+                               device=dev)
+        return torch.empty(bcgs.workspace_size(Mr, N, S, variant), dtype=torch.uint8, device=dev)
+
+    def factor_enqueue(Xd_, variant, Q, R, ws):
+        if by_rows:
+            rows_mod.factor_rows(Xd_, S, variant, rank, world, comm, "fp64", Q, R, ws, check_status=False)
+        else:
+            bcgs.factor_async(Xd_, S, variant, "fp64", Q, R, ws)
+
+    def global_sum(x: float) -> float:
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        if world > 1 and by_rows:
+            dist.all_reduce(t)
+        return float(t.item())
+
     def run_variant(variant, profile=False):
         Q = bcgs.empty_colmajor(Mr, N, torch.float64, dev)
         R = bcgs.empty_colmajor(N, N, torch.float64, dev)
-        ws = torch.empty(bcgs.workspace_size(Mr, N, S, variant), dtype=torch.uint8, device=dev)
+        ws = workspace_for(variant)
         for _ in range(args.warmup):
-            bcgs.factor_async(X, S, variant, "fp64", Q, R, ws)
+            factor_enqueue(X, variant, Q, R, ws)
         code, blk = bcgs.factor_status(ws)
         if code != 0:
             raise RuntimeError(f"{variant}: status {bcgs.STATUS[code]} at block {blk}")
@@ -250,7 +281,7 @@ def main_ours(args):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(args.steps):
-            bcgs.factor_async(X, S, variant, "fp64", Q, R, ws)
+            factor_enqueue(X, variant, Q, R, ws)
         e1.record(stream)
         barrier()
         launches = bcgs.launch_count() - l0
@@ -264,10 +295,13 @@ def main_ours(args):
         if code != 0:
             raise RuntimeError(f"{variant}: status {bcgs.STATUS[code]} at block {blk}")
         eye = torch.eye(N, dtype=torch.float64, device=dev)
-        G = (eye - Q.T @ Q).cpu().numpy()
+        QtQ = Q.T @ Q
+        if by_rows:  # the Gram of the whole Q: the sum over the ranks' rows
+            dist.all_reduce(QtQ)
+        G = (eye - QtQ).cpu().numpy()
         loo = float(np.linalg.norm(G, 2))
         D = X - Q @ R
-        res = math.sqrt((D * D).sum().item() / (X * X).sum().item())
+        res = math.sqrt(global_sum((D * D).sum().item()) / global_sum((X * X).sum().item()))
         del D
         del ws
         return {"ms": ms, "launches": launches, "loo": loo, "residual": res, "prof": prof,
@@ -284,9 +318,16 @@ def main_ours(args):
     Rh = torch.empty((N, N), dtype=torch.float64, pin_memory=True).T
     Xd = bcgs.empty_colmajor(Mr, N, torch.float64, dev)
     Qd, Rd = main["Q"], main["R"]
-    ws = torch.empty(bcgs.workspace_size(Mr, N, S, "bcgsi+p-1s"), dtype=torch.uint8, device=dev)
+    ws = workspace_for("bcgsi+p-1s")
 
     def e2e_step():
+        if by_rows:
+            # this rank's slab in, the row-partitioned factorization, its rows of Q and R out
+            Xd.copy_(Xh, non_blocking=True)
+            factor_enqueue(Xd, "bcgsi+p-1s", Qd, Rd, ws)
+            Qh.copy_(Qd, non_blocking=True)
+            Rh.copy_(Rd, non_blocking=True)
+            return
         # bcgs_qr_factor_host: X streams in block by block while earlier blocks are
         # factored, final blocks of Q stream back, R at the end
         bcgs.factor_host_async(Xh, S, "bcgsi+p-1s", "fp64", Qh, Rh, Xd, Qd, Rd, ws)
@@ -306,7 +347,7 @@ def main_ours(args):
     del ws, Xd, Xh, Qh, Rh
 
     compare = {}
-    if not args.no_compare:
+    if not args.no_compare and not by_rows:
         for v in ("bcgsi+", "bcgsi+p-2s", "bcgs-pipi+", "bcgsi+1s"):
             r = run_variant(v)
             compare[v] = {"ms": r["ms"], "loo": r["loo"], "residual": r["residual"]}
@@ -378,7 +419,9 @@ def main_ours(args):
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD if Mr == M else WORKLOAD.replace("m=2^22", f"m={Mr}"),
                    "m": Mr, "n": N, "s": S, "kappa": KAPPA,
-                   "variant": "bcgsi+p-1s", "parallelism": "replicas" if world > 1 else "single",
+                   "variant": "bcgsi+p-1s",
+                   "parallelism": (f"rows{world}" if by_rows else "replicas") if world > 1 else "single",
+                   "global_rows": Mr * world if by_rows else Mr,
                    "l2": "inputs larger than L2 (X and Q 8.6 GB each); no flush"},
         "e2e": {"value": e2e_value, "unit": "GB/s", "h2d_bytes_per_step": Mr * N * 8,
                 "d2h_bytes_per_step": Mr * N * 8 + N * N * 8, "ms_per_step": ms_e2e},

@@ -127,11 +127,12 @@ class ThreadAllGather:
 
 
 def factor_rows(X_local, s: int, variant: str, rank: int, nranks: int, allgather=None, precision: str | None = None,
-                Q=None, R=None, workspace=None, stream=None):
+                Q=None, R=None, workspace=None, stream=None, check_status: bool = True):
     """This rank's part of the row-partitioned factorization: X_local is the
     rank's block of rows (column-major device tensor).  `allgather(ws, send,
     recv, nbytes, stream) -> 0` is called at every synchronization (not needed
-    for nranks = 1).  Returns (Q_local, R, status_code, fail_block)."""
+    for nranks = 1).  Returns (Q_local, R, status_code, fail_block); with
+    check_status False the call only enqueues (status code and block are None)."""
     import torch
 
     lib = bcgs.load_library()
@@ -163,6 +164,8 @@ def factor_rows(X_local, s: int, variant: str, rank: int, nranks: int, allgather
     if errors:
         raise RuntimeError(f"all-gather failed: {errors[0]!r}")
     bcgs._check(rc, "bcgs_qr_factor_rows")
+    if not check_status:
+        return Q, R, None, None
     blk = ctypes.c_int32(0)
     code = lib.bcgs_qr_factor_status(workspace.data_ptr(), sp, ctypes.byref(blk))
     return Q, R, code, blk.value
