@@ -1,10 +1,11 @@
-"""Replica bookkeeping for runs on several GPUs of one node.
+"""Rank bookkeeping for runs on several GPUs of one node.
 
-The factorization does not shard here (every call gets one GPU), so a run on N
-GPUs is N independent factorizations, one process per GPU: no collective on the
-data path.  This module holds the host-side pieces of such a run: the process's
-place in it, the slowest rank's time (all ranks report the max) and the
-whole-job throughput (units all ranks processed / that time, weak scaling).
+A run on N GPUs is one process per GPU: either N independent factorizations
+(replicas: no collective on the data path) or one row-partitioned factorization
+(rows.py: one all-gather per synchronization).  This module holds the host-side
+pieces both share: the process's place in the run, the slowest rank's time (all
+ranks report the max) and the whole-job throughput (units all ranks processed /
+that time, weak scaling).
 """
 from __future__ import annotations
 
