@@ -476,6 +476,12 @@ def bench_fp32(args, dev, stream):
     ws = torch.empty(bcgs.workspace_size(m, n, s, "bcgsi+p-1s", "fp32"), dtype=torch.uint8, device=dev)
     ms = _timed(lambda: bcgs.factor_async(X, s, "bcgsi+p-1s", "fp32", Q, R, ws), args.warmup,
                 args.steps, stream)
+    # one more factorization with the per-class event profile
+    bcgs.profile_enable(True)
+    bcgs.factor_async(X, s, "bcgsi+p-1s", "fp32", Q, R, ws)
+    torch.cuda.synchronize()
+    classes = {k: round(bcgs.profile_read(k)[1], 2) for k in bcgs.PROFILE_CLASSES}
+    bcgs.profile_enable(False)
     code, blk = bcgs.factor_status(ws)
     Qd = Q.double()
     eye = torch.eye(n, dtype=torch.float64, device=dev)
@@ -486,7 +492,8 @@ def bench_fp32(args, dev, stream):
     return {"workload": f"FP32 storage m=2^24 n=128 s=32 BCGSI+P-1S kappa={kappa:g}",
             "value": alg_bytes_1s(m, n, s, b=4) / (ms * 1e-3) / 1e9, "unit": "GB/s",
             "ms_per_step": ms, "status": bcgs.STATUS[code], "loo": loo,
-            "residual_vs_fp64_x": res, "bound": "FP64 ALU (products accumulated in FP64)"}
+            "residual_vs_fp64_x": res, "ms_per_class": classes,
+            "bound": "FP64 ALU (products accumulated in FP64)"}
 
 
 # Table 2 of the paper: speedup over CGSI+ (BCGSI+ with s = 1) at 10^6 x 400 on

@@ -365,16 +365,23 @@ cudaError_t gram_cols(bcgs_qr_s* h, int na, int b0, int nb, std::initializer_lis
 cudaError_t gram_local(bcgs_qr_s* h, int na, int b0, int nb, std::initializer_list<Seg> A,
                        std::initializer_list<Seg> B, double* G) {
   if (!h->sgram) return gram(h, A, B, G);
-  GramStoreDesc d;
-  memset(&d, 0, sizeof(d));
-  d.qs = h->qs();
-  d.na = na;
-  d.b0 = b0;
-  d.nb = nb;
-  gram_store_partition(h->m, &d.nchunks, &d.bpc);
-  d.m = h->m;
-  d.block = h->j + 1;
-  return launch_gram_store(d, h->buf(h->L.partial), G, h->L.ldg, h->st(), h->stream);
+  // the store Gram takes at most 32 B columns per launch: wider B (the 2s
+  // columns [U X] of 1S / 2S at s = 32) in groups of 32, each into its columns of G
+  for (int j0 = 0; j0 < nb; j0 += 32) {
+    GramStoreDesc d;
+    memset(&d, 0, sizeof(d));
+    d.qs = h->qs();
+    d.na = na;
+    d.b0 = b0 + j0;
+    d.nb = nb - j0 < 32 ? nb - j0 : 32;
+    gram_store_partition(h->m, &d.nchunks, &d.bpc);
+    d.m = h->m;
+    d.block = h->j + 1;
+    const cudaError_t e = launch_gram_store(d, h->buf(h->L.partial), G + (size_t)j0 * h->L.ldg, h->L.ldg, h->st(),
+                                            h->stream);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 cudaError_t tsqr(bcgs_qr_s* h, Seg a, void* q, int64_t ldq, double* R, int ldr, int block,
@@ -527,12 +534,15 @@ int step_p(bcgs_qr_s* h, const void* X, int64_t ldx) {
   probe.s = s;
   // [Q_{1:k-1} U_k] from the store: U_k is there when the Grams use it
   const bool paired = h->sgram && use_tensor_project(probe) && project_store_supported(s, 2);
-  if (paired) {
+  // s = 32 (past the paired kernel's tensor memory): the same coefficients,
+  // applied by two single-output passes over [Q_{1:k-1} U_k]
+  const bool two_pass = !paired && h->sgram && use_tensor_project(probe) && project_store_supported(s, 1);
+  if (paired || two_pass) {
     t.Bpair = h->buf(h->L.Bp);
     t.ldb = h->n_max;
   }
   TRY(launch_tail_1s2s(t, h->st(), h->stream));
-  if (paired) {
+  if (paired || two_pass) {
     TRY(zero_umax(h));
     StoreProjDesc p;
     memset(&p, 0, sizeof(p));
@@ -557,7 +567,20 @@ int step_p(bcgs_qr_s* h, const void* X, int64_t ldx) {
     p.block = k;
     p.fexp = h->fexp();
     p.fp32 = h->fp32;
-    TRY(launch_project_store(p, h->st(), h->stream));
+    if (paired) {
+      TRY(launch_project_store(p, h->st(), h->stream));
+    } else {
+      // Q_k with B[:, 0:s], then the next block with B[:, s:2s] (both read U_k's
+      // digits, so Q_k's replace them only afterwards)
+      StoreProjDesc p1 = p;
+      p1.nouts = 1;
+      TRY(launch_project_store(p1, h->st(), h->stream));
+      StoreProjDesc p2 = p;
+      p2.nouts = 1;
+      p2.B = p.B + (size_t)s * p.ldb;
+      p2.out[0] = p.out[1];
+      TRY(launch_project_store(p2, h->st(), h->stream));
+    }
     TRY(wrote_q(h, k));
     if (!one_sync && !unnormalized)
       TRY(tsqr(h, h->Vseg(), h->U(), h->L.ldu, h->buf(h->L.Sd[nxt]), s, k + 1, h->Umax()));
@@ -757,9 +780,9 @@ int init_handle(bcgs_qr_s* h, int64_t m, int32_t n_max, int32_t s, int variant, 
   h->nranks = nranks;
   h->allgather = allgather;
   h->ag_ctx = ag_ctx;
-  // Grams from the store need whole 8-column groups per block and nb <= 32
-  const bool paired = h->delayed();
-  h->sgram = h->L.store && s % 8 == 0 && (paired ? s <= 16 : s <= 32);
+  // Grams from the store need whole 8-column groups per block (a Gram with more
+  // than 32 B columns runs as several launches of at most 32, gram_local)
+  h->sgram = h->L.store && s % 8 == 0 && s <= 32;
   h->j = 0;
   h->cur = 0;
   h->finished = 0;
