@@ -15,6 +15,8 @@
 // The Householder step per column follows the oracle's convention
 // (beta = -sign(a_jj) ||a_j||, v_j = 1, tau = (beta - a_jj) / beta), so the
 // sign-normalized factors agree with a plain Householder QR up to rounding.
+#include <type_traits>
+
 #include "bcgs_internal.cuh"
 
 namespace bcgs {
@@ -409,28 +411,312 @@ __global__ void __launch_bounds__(256) rows_times_small_kernel(int64_t m, int32_
   if (live && wmax.row != nullptr) wmax.row[r] = umax64(wmax.row[r], rmax);
 }
 
+// ------------------------------------------------------------ double-float tiles
+// FP32-storage blocks: the tile arithmetic of the leaves (the column updates,
+// V^T V and the explicit-Q product) runs in unevaluated pairs of floats
+// hi + lo (|lo| <= ulp(hi) / 2), built from the error-free transformations of
+// Knuth (TwoSum) and Dekker (the exact product error, here through fmaf), with
+// the single-rounding-pair ("sloppy") addition of Dekker's double-length
+// arithmetic (Numer. Math. 18, 1971): about 44 bits per operation, 2^20 times
+// finer than the FP32 storage, on the FP32 pipe, which GB300 runs about 60
+// times faster than FP64.  Column norms, the reflector scalars, the WY
+// triangle and the tree levels stay FP64; the exponent range is float's (the
+// column norms, computed in FP64, do not overflow).
+struct df {
+  float hi, lo;
+};
+__device__ __forceinline__ double df_dbl(df a) { return (double)a.hi + (double)a.lo; }
+__device__ __forceinline__ df df_from(double x) {
+  const float h = __double2float_rn(x);
+  return df{h, __double2float_rn(x - (double)h)};
+}
+__device__ __forceinline__ df two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  return df{s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+__device__ __forceinline__ df quick_two_sum(float a, float b) {  // |a| >= |b| or a = 0
+  const float s = __fadd_rn(a, b);
+  return df{s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ df df_add(df x, df y) {
+  df s = two_sum(x.hi, y.hi);
+  s.lo = __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo));
+  return quick_two_sum(s.hi, s.lo);
+}
+__device__ __forceinline__ df df_mul(df x, df y) {
+  const float p = __fmul_rn(x.hi, y.hi);
+  float e = fmaf(x.hi, y.hi, -p);
+  e = fmaf(x.hi, y.lo, e);
+  e = fmaf(x.lo, y.hi, e);
+  return quick_two_sum(p, e);
+}
+__device__ __forceinline__ df df_fma(df a, df b, df c) { return df_add(df_mul(a, b), c); }  // a b + c
+__device__ __forceinline__ df df_neg(df a) { return df{-a.hi, -a.lo}; }
+
+__device__ __forceinline__ df warp_sum_df(df v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+    v = df_add(v, df{__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)});
+  return v;
+}
+
+// sum over r = r0, r0 + 32, ... < rows of a[r] b[r]: four interleaved
+// accumulators, as dot4 (the order depends on the shape only)
+__device__ __forceinline__ df dot4_df(const df* a, const df* b, int r0, int rows) {
+  df w0{0.f, 0.f}, w1{0.f, 0.f}, w2{0.f, 0.f}, w3{0.f, 0.f};
+  int r = r0;
+  for (; r + 96 < rows; r += 128) {
+    w0 = df_fma(a[r], b[r], w0);
+    w1 = df_fma(a[r + 32], b[r + 32], w1);
+    w2 = df_fma(a[r + 64], b[r + 64], w2);
+    w3 = df_fma(a[r + 96], b[r + 96], w3);
+  }
+  for (; r < rows; r += 32) w0 = df_fma(a[r], b[r], w0);
+  return df_add(df_add(w0, w1), df_add(w2, w3));
+}
+
+// block_householder in double-float (the same steps, look-ahead and barriers);
+// the column's sum of squares, beta, tau and 1 / (x0 - beta) in FP64.
+__device__ void block_householder_df(df* A, int rows, int s, double* tau) {
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int nwarps = blockDim.x / 32;
+  auto reflect = [&](int j) {
+    df* aj = A + (size_t)j * rows;
+    double ssq = 0.0;
+    for (int r = j + 1 + lane; r < rows; r += 32) {
+      const double v = df_dbl(aj[r]);
+      ssq = fma(v, v, ssq);
+    }
+    const double sum = warp_sum(ssq);
+    const double x0 = df_dbl(aj[j]);
+    const double alpha = sqrt(fma(x0, x0, sum));
+    double t = 0.0, beta = 0.0, denom = 1.0;
+    if (alpha != 0.0) {
+      beta = x0 >= 0.0 ? -alpha : alpha;
+      denom = x0 - beta;
+      t = (beta - x0) / beta;
+    }
+    if (alpha != 0.0) {
+      const df rden = df_from(1.0 / denom);
+      for (int r = j + 1 + lane; r < rows; r += 32) aj[r] = df_mul(aj[r], rden);
+    }
+    __syncwarp();
+    if (lane == 0) {
+      tau[j] = t;
+      if (alpha != 0.0) aj[j] = df_from(beta);
+    }
+  };
+  if (warp == 0) reflect(0);
+  __syncthreads();
+  for (int j = 0; j < s; ++j) {
+    const df* aj = A + (size_t)j * rows;
+    const double t = tau[j];
+    for (int l = j + 1 + warp; l < s; l += nwarps) {
+      df* al = A + (size_t)l * rows;
+      if (t != 0.0) {
+        df w = df_add(warp_sum_df(dot4_df(aj, al, j + 1 + lane, rows)), al[j]);
+        w = df_mul(w, df_from(t));
+        __syncwarp();  // every lane has read al[j] before lane 0 updates it
+        if (lane == 0) al[j] = df_add(al[j], df_neg(w));
+        const df nw = df_neg(w);
+        for (int r = j + 1 + lane; r < rows; r += 32) al[r] = df_fma(aj[r], nw, al[r]);
+        __syncwarp();
+      }
+      if (l == j + 1) reflect(l);
+    }
+    __syncthreads();
+  }
+}
+
+// tsqr_leaf_factor for an FP32 block: the tile in double-float, the reflectors
+// kept as double-float pairs (8 bytes, in the same workspace slots), tau, the
+// WY triangle and the R factor in FP64.
+constexpr int kDfThreads = 512;  // twice the FP64 kernels' warps: the double-float chains need more in flight
+
+__global__ void __launch_bounds__(kDfThreads)
+tsqr_leaf_factor_df(TsqrPlan p, Seg a, double* work, double* R, int32_t ldr, DevStatus* st, int32_t block) {
+  if (failed(st)) return;
+  extern __shared__ double sm[];
+  __shared__ double tau[64];
+  const int mt = p.mt, s = p.s;
+  df* A = reinterpret_cast<df*>(sm);  // mt x s
+  const int t = blockIdx.x;
+  const int64_t row0 = (int64_t)t * mt;
+  const int rows_here = (int)(p.m - row0 < (int64_t)mt ? p.m - row0 : (int64_t)mt);
+  const float* src = reinterpret_cast<const float*>(a.p);
+  for (int e = threadIdx.x; e < mt * s; e += kDfThreads) {
+    const int r = e % mt, j = e / mt;
+    A[e] = df{r < rows_here ? src[row0 + r + (int64_t)j * a.ld] : 0.0f, 0.0f};
+  }
+  __syncthreads();
+  block_householder_df(A, mt, s, tau);
+  df* H = reinterpret_cast<df*>(work + p.off_h) + (size_t)t * mt * s;
+  for (int e = threadIdx.x; e < mt * s; e += kDfThreads) H[e] = A[e];
+  double* tg = work + p.off_tau[0] + (size_t)t * s;
+  for (int j = threadIdx.x; j < s; j += kDfThreads) tg[j] = tau[j];
+  double* VV = sm + (size_t)mt * s;  // s x s: (V^T V)_{ij} for i < j, later the root's R
+  double* Tl = VV + (size_t)s * s;
+  {
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    for (int e = warp; e < s * s; e += kDfThreads / 32) {
+      const int i = e % s, j = e / s;
+      if (i < j) {
+        const df* vi = A + (size_t)i * mt;
+        const df* vj = A + (size_t)j * mt;
+        const df d = warp_sum_df(dot4_df(vi, vj, j + 1 + lane, mt));
+        if (lane == 0) VV[i + (size_t)j * s] = df_dbl(df_add(d, vi[j]));
+      }
+    }
+    __syncthreads();
+    for (int j = 0; j < s; ++j) {
+      for (int i = threadIdx.x; i < s; i += kDfThreads) {
+        double x = 0.0;
+        if (i < j)
+          for (int l = i; l < j; ++l) x = fma(Tl[i + (size_t)l * s], VV[l + (size_t)j * s], x);
+        Tl[i + (size_t)j * s] = i < j ? -tau[j] * x : (i == j ? tau[j] : 0.0);
+      }
+      __syncthreads();
+    }
+    double* tw = work + p.off_t0 + (size_t)t * s * s;
+    for (int e = threadIdx.x; e < s * s; e += kDfThreads) tw[e] = Tl[e];
+  }
+  if (p.nlevels == 1) {
+    // the R factor (upper triangle of the tile) in FP64, then the root's signs
+    __syncthreads();
+    for (int e = threadIdx.x; e < s * s; e += kDfThreads) {
+      const int i = e % s, j = e / s;
+      VV[e] = df_dbl(A[i + (size_t)j * mt]);
+    }
+    __syncthreads();
+    finish_root(VV, s, s, R, ldr, work + p.off_b[0], st, block);
+    return;
+  }
+  const int fan = p.fan, ldp = fan * s;
+  double* P = work + p.off_lvl[1] + (size_t)(t / fan) * ldp * s;
+  const int rbase = (t % fan) * s;
+  for (int e = threadIdx.x; e < s * s; e += kDfThreads) {
+    const int i = e % s, j = e / s;
+    P[rbase + i + (size_t)j * ldp] = i <= j ? df_dbl(A[i + (size_t)j * mt]) : 0.0;
+  }
+}
+
+// tsqr_leaf_apply for an FP32 block: E = [B; 0] - V (T (V_top^T B)) entirely
+// in double-float (one thread per row and 16-column group for the mt x s
+// product), each result rounded once to float; the maxima of the stored values
+// from registers.
+__global__ void __launch_bounds__(kDfThreads)
+tsqr_leaf_apply_df(TsqrPlan p, const double* work, void* q, int64_t ldq, const DevStatus* st, MaxOut qmax) {
+  if (failed(st)) return;
+  extern __shared__ double sm[];
+  const int mt = p.mt, s = p.s;
+  const int t = blockIdx.x;
+  df* V = reinterpret_cast<df*>(sm);                  // mt x s
+  double* Bs = sm + (size_t)mt * s;                   // s x s coefficient block from the parent, then W
+  double* Tl = Bs + (size_t)s * s;                    // s x s WY triangle, then M = T W
+  double* W = Tl + (size_t)s * s;                     // s x s: B in double-float
+  df* Md = reinterpret_cast<df*>(W + (size_t)s * s);  // s x s: T in double-float
+  const df* H = reinterpret_cast<const df*>(work + p.off_h) + (size_t)t * mt * s;
+  const double* B = work + p.off_b[0] + (size_t)t * s * s;
+  const double* Tg = work + p.off_t0 + (size_t)t * s * s;
+  for (int e = threadIdx.x; e < mt * s; e += kDfThreads) V[e] = H[e];
+  for (int e = threadIdx.x; e < s * s; e += kDfThreads) {
+    Bs[e] = B[e];
+    Tl[e] = Tg[e];
+  }
+  __syncthreads();
+  // W = V_top^T B and M = T W in double-float too (no FP64 work in this kernel:
+  // GB300's FP64 rate would make these s^3 products its slowest part); B and T
+  // go to double-float once, into the s x s slots of W (as Bd) and Md (as Td)
+  df* Bd = reinterpret_cast<df*>(W);
+  df* Td = Md;
+  for (int e = threadIdx.x; e < s * s; e += kDfThreads) {
+    Bd[e] = df_from(Bs[e]);
+    Td[e] = df_from(Tl[e]);
+  }
+  __syncthreads();
+  df* Wd = reinterpret_cast<df*>(Bs);  // B itself is read again below from Bd
+  for (int e = threadIdx.x; e < s * s; e += kDfThreads) {
+    const int l = e % s, c = e / s;
+    df x = Bd[l + (size_t)c * s];
+    for (int i = l + 1; i < s; ++i) x = df_fma(V[i + (size_t)l * mt], Bd[i + (size_t)c * s], x);
+    Wd[e] = x;
+  }
+  __syncthreads();
+  df* Mw = reinterpret_cast<df*>(Tl);  // T is read from Td
+  for (int e = threadIdx.x; e < s * s; e += kDfThreads) {
+    const int l = e % s, c = e / s;
+    df x{0.0f, 0.0f};
+    for (int i = l; i < s; ++i) x = df_fma(Td[l + (size_t)i * s], Wd[i + (size_t)c * s], x);
+    Mw[e] = x;
+  }
+  __syncthreads();
+  const int64_t row0 = (int64_t)t * mt;
+  const int rows_here = (int)(p.m - row0 < (int64_t)mt ? p.m - row0 : (int64_t)mt);
+  float* dst = reinterpret_cast<float*>(q);
+  const int ngr = (s + 15) / 16;
+  // mt is a multiple of 32, so each warp's lanes share one column group (the
+  // column maxima are warp reductions)
+  for (int w = threadIdx.x; w < mt * ngr; w += kDfThreads) {
+    const int r = w % mt, c0 = (w / mt) * 16;
+    const int nc = s - c0 < 16 ? s - c0 : 16;
+    df e[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) e[c] = (c < nc && r < s) ? Bd[r + (size_t)(c0 + c) * s] : df{0.0f, 0.0f};
+    const int lmax = r < s ? r + 1 : s;  // V(r, l) = 0 for l > r
+    for (int l = 0; l < lmax; ++l) {
+      const df nv = l == r ? df{-1.0f, 0.0f} : df_neg(V[r + (size_t)l * mt]);
+#pragma unroll
+      for (int c = 0; c < 16; ++c)
+        if (c < nc) e[c] = df_fma(nv, Mw[l + (size_t)(c0 + c) * s], e[c]);
+    }
+    const bool live = r < rows_here;
+    unsigned long long rmax = 0ull;
+#pragma unroll
+    for (int c = 0; c < 16; ++c) {
+      if (c < nc) {
+        const float f = __fadd_rn(e[c].hi, e[c].lo);
+        if (live) dst[row0 + r + (int64_t)(c0 + c) * ldq] = f;
+        const unsigned long long b = live ? abs_bits64((double)f) : 0ull;
+        rmax = umax64(rmax, b);
+        if (qmax.col != nullptr) warp_max_to(b, qmax.col + c0 + c);
+      }
+    }
+    if (live && qmax.row != nullptr) atomicMax(qmax.row + row0 + r, rmax);
+  }
+}
+
 template <typename T>
 cudaError_t launch_tsqr_t(const TsqrPlan& p, Seg a, void* q, int64_t ldq, double* R, int32_t ldr,
                           double* work, DevStatus* st, int32_t block, cudaStream_t stream, MaxOut qmax) {
   const size_t leaf_f = (size_t)p.mt * p.s * sizeof(double);
   const size_t ss = (size_t)p.s * p.s * sizeof(double);
   const size_t node_f = (size_t)p.fan * p.s * p.s * sizeof(double);
+  // FP32 blocks: the leaves in double-float (their E buffer holds floats)
+  constexpr bool kDf = std::is_same<T, float>::value;
+  const size_t apply_f = kDf ? leaf_f + 4 * ss : 2 * leaf_f + 3 * ss;
   cudaError_t e;
-  e = ensure_dyn_smem(tsqr_leaf_factor<T>, leaf_f + 2 * ss);
+  e = kDf ? ensure_dyn_smem(tsqr_leaf_factor_df, leaf_f + 2 * ss) : ensure_dyn_smem(tsqr_leaf_factor<T>, leaf_f + 2 * ss);
   if (e != cudaSuccess) return e;
-  e = ensure_dyn_smem(tsqr_leaf_apply<T>, 2 * leaf_f + 3 * ss);
+  e = kDf ? ensure_dyn_smem(tsqr_leaf_apply_df, apply_f) : ensure_dyn_smem(tsqr_leaf_apply<T>, apply_f);
   if (e != cudaSuccess) return e;
   e = ensure_dyn_smem(tsqr_node_factor, (size_t)(node_f));
   if (e != cudaSuccess) return e;
   e = ensure_dyn_smem(tsqr_node_apply, (size_t)(2 * node_f));
   if (e != cudaSuccess) return e;
   const int slot = prof_begin(stream);
-  tsqr_leaf_factor<T><<<p.nodes[0], kTsqrThreads, leaf_f + 2 * ss, stream>>>(p, a, work, R, ldr, st, block);
+  if (kDf)
+    tsqr_leaf_factor_df<<<p.nodes[0], kDfThreads, leaf_f + 2 * ss, stream>>>(p, a, work, R, ldr, st, block);
+  else
+    tsqr_leaf_factor<T><<<p.nodes[0], kTsqrThreads, leaf_f + 2 * ss, stream>>>(p, a, work, R, ldr, st, block);
   for (int l = 1; l < p.nlevels; ++l)
     tsqr_node_factor<<<p.nodes[l], kTsqrThreads, node_f, stream>>>(p, l, work, R, ldr, st, block);
   for (int l = p.nlevels - 1; l >= 1; --l)
     tsqr_node_apply<<<p.nodes[l], kTsqrThreads, 2 * node_f, stream>>>(p, l, work, st);
-  tsqr_leaf_apply<T><<<p.nodes[0], kTsqrThreads, 2 * leaf_f + 3 * ss, stream>>>(p, work, q, ldq, st, qmax);
+  if (kDf)
+    tsqr_leaf_apply_df<<<p.nodes[0], kDfThreads, apply_f, stream>>>(p, work, q, ldq, st, qmax);
+  else
+    tsqr_leaf_apply<T><<<p.nodes[0], kTsqrThreads, apply_f, stream>>>(p, work, q, ldq, st, qmax);
   // Householder QR and explicit Q of the m x s block: 2 m s^2 flops each.
   prof_end(slot, kProfTsqr, stream, 4.0 * (double)p.m * p.s * p.s,
            2.0 * (double)p.m * p.s * sizeof(T) + 2.0 * (double)p.nodes[0] * p.mt * p.s * 8.0);
