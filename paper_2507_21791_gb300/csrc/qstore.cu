@@ -498,20 +498,43 @@ __global__ void __launch_bounds__(Roles<NOUT>::kThreads, 1) proj_store_kernel(St
     // named barriers are still passed by all splitter threads)
     constexpr int kSp = 32 * kSplitWarps;
     const int sp = tid - 32 * kSplit0;          // 0..kSp-1
-    // F pass: column j = lane, rows k = sw, sw + kSplitWarps, ...
+    // The block's exponents and F come from global memory; for K <= kPre * kSp
+    // those of block bi + 1 are loaded into registers while block bi is split,
+    // so a block's start does not wait for them (small K: a block's splits are
+    // shorter than that latency).
+    constexpr int kPre = 3;
+    const bool pre = K <= kPre * kSp;
+    int pe[kPre], pf = 0;
+    auto fetch = [&](int64_t b) {
+#pragma unroll
+      for (int u = 0; u < kPre; ++u) {
+        const int k = sp + u * kSp;
+        pe[u] = k < K ? d.qs.exps[b * d.qs.ld_exp + k] : 0;
+      }
+      pf = sp < NBT ? d.fexp[b * NBT + sp] : 0;
+    };
+    if (pre && nbl > 0) fetch(blk_of(0));
     for (int bi = 0; bi < nbl; ++bi) {
       const int64_t b = blk_of(bi);
       // this block's exponents (the previous block's splits are all done: same warps)
       named_bar_sync(1, kSp);
-      if (!s_abort)
-        for (int k = sp; k < K; k += kSp) s_exp[k] = d.qs.exps[b * d.qs.ld_exp + k];
+      if (!s_abort) {
+        if (pre) {
+#pragma unroll
+          for (int u = 0; u < kPre; ++u)
+            if (sp + u * kSp < K) s_exp[sp + u * kSp] = pe[u];
+        } else {
+          for (int k = sp; k < K; k += kSp) s_exp[k] = d.qs.exps[b * d.qs.ld_exp + k];
+        }
+      }
       named_bar_sync(1, kSp);
       // F of block bi (proj_fexp_kernel) goes to buffer bi & 1, free once block bi - 2 is unfolded
       if (bi >= 2) wait_or_abort(&ffree[bi & 1], ((bi >> 1) - 1) & 1, &s_abort);
       named_bar_sync(1, kSp);
-      if (sp < NBT && !s_abort) s_F[bi & 1][sp] = d.fexp[b * NBT + sp];
+      if (sp < NBT && !s_abort) s_F[bi & 1][sp] = pre ? pf : d.fexp[b * NBT + sp];
       named_bar_sync(1, kSp);
       if (sp == 0) mbar_arrive(&fready[bi & 1]);
+      if (pre && bi + 1 < nbl && !s_abort) fetch(blk_of(bi + 1));
       const int* sF = s_F[bi & 1];
       for (int kc = 0; kc < nch; ++kc) {
         const int g = bi * nch + kc, slot = g % C::kBRing;
@@ -736,10 +759,19 @@ __global__ void __launch_bounds__(Roles<NOUT>::kThreads, 1) proj_store_kernel(St
     for (int bi = 0; bi < nbl; ++bi) {
       const int64_t r = blk_of(bi) * kRows + i;
       const bool inrow = r < d.m;
-      // V of this row is loaded while the read-back finishes the block
+      // V of this row is loaded while the read-back finishes the block, and the
+      // next block's rows of V are sent toward L2 (when these warps set the pace
+      // the wait below is short and the load latency would show)
       double v[kSm];
 #pragma unroll
       for (int j = 0; j < kSm; ++j) v[j] = (out.v != nullptr && inrow && j < s) ? vload(out, r + (int64_t)j * out.ldv) : 0.0;
+      if (out.v != nullptr && bi + 1 < nbl) {
+        const int64_t rn = blk_of(bi + 1) * kRows + i;
+        if (rn < d.m)
+          for (int j = 0; j < s; ++j)
+            asm volatile("prefetch.global.L2 [%0];\n" ::"l"(reinterpret_cast<const char*>(out.v) +
+                                                            (rn + (int64_t)j * out.ldv) * (F32 ? 4 : 8)));
+      }
       const bool ok = wait_or_abort(&wfull, bi & 1, &s_abort);
       double w[kSm];
 #pragma unroll
