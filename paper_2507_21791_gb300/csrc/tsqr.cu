@@ -18,6 +18,7 @@
 #include <type_traits>
 
 #include "bcgs_internal.cuh"
+#include "dfloat.cuh"
 
 namespace bcgs {
 
@@ -413,47 +414,9 @@ __global__ void __launch_bounds__(256) rows_times_small_kernel(int64_t m, int32_
 
 // ------------------------------------------------------------ double-float tiles
 // FP32-storage blocks: the tile arithmetic of the leaves (the column updates,
-// V^T V and the explicit-Q product) runs in unevaluated pairs of floats
-// hi + lo (|lo| <= ulp(hi) / 2), built from the error-free transformations of
-// Knuth (TwoSum) and Dekker (the exact product error, here through fmaf), with
-// the single-rounding-pair ("sloppy") addition of Dekker's double-length
-// arithmetic (Numer. Math. 18, 1971): about 44 bits per operation, 2^20 times
-// finer than the FP32 storage, on the FP32 pipe, which GB300 runs about 60
-// times faster than FP64.  Column norms, the reflector scalars, the WY
-// triangle and the tree levels stay FP64; the exponent range is float's (the
-// column norms, computed in FP64, do not overflow).
-struct df {
-  float hi, lo;
-};
-__device__ __forceinline__ double df_dbl(df a) { return (double)a.hi + (double)a.lo; }
-__device__ __forceinline__ df df_from(double x) {
-  const float h = __double2float_rn(x);
-  return df{h, __double2float_rn(x - (double)h)};
-}
-__device__ __forceinline__ df two_sum(float a, float b) {
-  const float s = __fadd_rn(a, b);
-  const float bb = __fsub_rn(s, a);
-  return df{s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
-}
-__device__ __forceinline__ df quick_two_sum(float a, float b) {  // |a| >= |b| or a = 0
-  const float s = __fadd_rn(a, b);
-  return df{s, __fsub_rn(b, __fsub_rn(s, a))};
-}
-__device__ __forceinline__ df df_add(df x, df y) {
-  df s = two_sum(x.hi, y.hi);
-  s.lo = __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo));
-  return quick_two_sum(s.hi, s.lo);
-}
-__device__ __forceinline__ df df_mul(df x, df y) {
-  const float p = __fmul_rn(x.hi, y.hi);
-  float e = fmaf(x.hi, y.hi, -p);
-  e = fmaf(x.hi, y.lo, e);
-  e = fmaf(x.lo, y.hi, e);
-  return quick_two_sum(p, e);
-}
-__device__ __forceinline__ df df_fma(df a, df b, df c) { return df_add(df_mul(a, b), c); }  // a b + c
-__device__ __forceinline__ df df_neg(df a) { return df{-a.hi, -a.lo}; }
-
+// V^T V and the explicit-Q product) runs in double-float (dfloat.cuh).  Column
+// norms, the reflector scalars, the WY triangle and the tree levels stay FP64;
+// the column norms, computed in FP64, do not overflow float's range.
 __device__ __forceinline__ df warp_sum_df(df v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1)
