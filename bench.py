@@ -53,11 +53,6 @@ TRAFFIC_RATIO = {
     # FP64-pipe Gram, ncu capture at m = 524288, 256 x 32 outputs:
     # (1.208285 GB + 3.823 MB) / (524288 * 288 * 8 B + 304 * 256 * 32 * 8 B)
     "gram_partial_kernel": (1.208285e9 + 3.823104e6) / (524288 * 288 * 8 + 304 * 256 * 32 * 8),
-    # store projection, ncu capture at m = 262144, K = 208, s = 16: (916.343 MB + 58.576 MB) / (8 * 262144 * 256 B);
-    # the digit stream is 16 B per element of Q against 8 algorithmic bytes
-    "proj_store_kernel": (916.342784e6 + 58.576128e6) / (8 * 262144 * 256),
-    # store Gram, ncu capture at m = 262144, na = 224, nb = 32: (944.189 MB + 9.524 MB) / (8 * 262144 * 256 B)
-    "gram_store_kernel": (944.189440e6 + 9.524224e6) / (8 * 262144 * 256),
 }
 
 

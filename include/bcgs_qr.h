@@ -108,7 +108,7 @@ BCGS_API int bcgs_version(void);
  * (n < s: TSQR alone).  Writes *bytes; returns BCGS_OK or
  * BCGS_ERR_INVALID_ARG.  With s <= 32 and the tensor engine selected for m
  * rows (BCGS_OPT_GRAM_ENGINE below), under either storage type, the size
- * includes the digit store of Q: 16 bytes per element of the m x n_max basis
+ * includes the digit store of Q: 14 bytes per element of the m x n_max basis
  * (rounded up to 128
  * columns), one 32-bit exponent per 128 rows and column, and 32 more per 128
  * rows.  A factorization given a workspace sized without the store (for example

@@ -137,16 +137,19 @@ cudaError_t launch_project_tc(const ProjDesc& d, DevStatus* st, cudaStream_t str
 bool use_tensor_project(const ProjDesc& d);
 
 // ---------------------------------------------------------------- resident digit store of Q
-// With FP64 storage, Q is kept a second time as exact digit tiles ready for the
-// tensor cores (qstore.cu).  Per 128-row block b and column k: the exponent field
-// exps[b][k] of max_{i in b} |q_ik|, and the eight balanced 8-bit digits
-// (tc_common.cuh) of every q_ik relative to it, as f16.  Tiles of 128 rows x 128
-// columns per (b, column group G), 256 KB each:
-//   [t: digit 0..7][g: 8-column group 0..15][r: 8-row group 0..15][8 rows x 16 B]
+// Q is kept a second time as digit tiles ready for the tensor cores
+// (qstore.cu).  Per 128-row block b and column k: the exponent field exps[b][k]
+// of max_{i in b} |q_ik|, and the seven leading balanced 8-bit digits
+// (tc_common.cuh) of every q_ik relative to it, as f16: the 62-bit fixed-point
+// value without its last digit, which is off by at most 2^-55 of the block's
+// column maximum.  Tiles of 128 rows x 128 columns per (b, column group G),
+// 224 KB each:
+//   [t: digit 0..6][g: 8-column group 0..15][r: 8-row group 0..15][8 rows x 16 B]
 // so a 16-column chunk of one digit is 4 KB of contiguous bytes.
 constexpr int kStoreRows = 128;
 constexpr int kStoreCols = 128;
-constexpr size_t kStoreTileBytes = (size_t)8 * kStoreRows * kStoreCols * 2;
+constexpr int kStoreDigits = 7;
+constexpr size_t kStoreTileBytes = (size_t)kStoreDigits * kStoreRows * kStoreCols * 2;
 struct QStore {
   uint8_t* dig;
   int32_t* exps;

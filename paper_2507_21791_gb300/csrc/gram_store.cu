@@ -5,8 +5,10 @@
 // operands are bulk copies of digit tiles, MN-major for the MMA (the 16-byte
 // lines of the store run along the columns, the contraction along the rows).
 //
-// Per 128-row block b the digit products of one level are exact fp32 sums of
-// 128 terms.  Block b's products carry the exponents E_bk (column k of A) and
+// Both operands carry the store's seven leading digits (each value off by at
+// most 2^-55 of its block column's maximum, so one product term by about
+// 2^-53.9 of the product of the two maxima).  Per 128-row block b the digit
+// products of one level are exact fp32 sums of 128 terms.  Block b's products carry the exponents E_bk (column k of A) and
 // F_bj (column j of B); they are shifted onto the exponents Ec_k = max_b E_bk
 // and Fc_j = max_b F_bj of the CTA's chunk of blocks (an exact right shift of
 // the 128-bit fixed-point value, truncating at 2^-68 of the chunk maxima) and
@@ -40,6 +42,8 @@ template <int NBT>
 struct GSCfg {
   static constexpr int kAStages = NBT == 32 ? 3 : 4;
   static constexpr int kBDigit = NBT / 8 * 2048;  // one digit of B: NBT / 8 column groups
+  // B's eight digit planes: seven from the store, the eighth stays zero (so the
+  // first MMA of a block, digit 0 of A against planes 0..7, sets all eight levels)
   static constexpr int kBBuf = kDigits * kBDigit;
   static constexpr int kAcc = kDigits * NBT;
   static constexpr int kTmem = 2 * kAcc;
@@ -91,9 +95,9 @@ __global__ void __launch_bounds__(kThreads, 1) gram_store_kernel(GramStoreDesc d
   const QStore qs = d.qs;
   const int64_t b_first = (int64_t)ch * d.bpc;
   const int nbl = (int)min((int64_t)d.bpc, qs.nblk - b_first);
-  const int ntot = nbl * kDigits;  // A chunks: (block, digit)
+  const int ntot = nbl * kStoreDigits;  // A chunks: (block, digit)
   auto tile = [&](int64_t b, int g, int t) {
-    return qs.dig + ((size_t)(b * qs.ngroups + g) * kDigits + t) * kDigBytes;
+    return qs.dig + ((size_t)(b * qs.ngroups + g) * kStoreDigits + t) * kDigBytes;
   };
 
   if (tid == 0) {
@@ -150,13 +154,14 @@ __global__ void __launch_bounds__(kThreads, 1) gram_store_kernel(GramStoreDesc d
       auto issue_A = [&](int a) {
         const int slot = a % S;
         mbar_arrive_expect_tx(&fullA[slot], a_bytes);
-        bulk_g2s(Aring + slot * kDigBytes, tile(b_first + a / kDigits, G, a % kDigits), a_bytes, &fullA[slot]);
+        bulk_g2s(Aring + slot * kDigBytes, tile(b_first + a / kStoreDigits, G, a % kStoreDigits), a_bytes,
+                 &fullA[slot]);
       };
       auto issue_B = [&](int bl) {
         const int p = bl & 1;
-        mbar_arrive_expect_tx(&fullB[p], (uint32_t)(kDigits * g_cnt * 2048));
+        mbar_arrive_expect_tx(&fullB[p], (uint32_t)(kStoreDigits * g_cnt * 2048));
         const int64_t b = b_first + bl;
-        for (int u = 0; u < kDigits; ++u) {
+        for (int u = 0; u < kStoreDigits; ++u) {
           uint8_t* dst = Bbuf + p * C::kBBuf + u * C::kBDigit;
           if (n1 > 0) bulk_g2s(dst, tile(b, G1, u) + gs * 2048, n1 * 2048, &fullB[p]);
           if (n2 > 0) bulk_g2s(dst + n1 * 2048, tile(b, G1 + 1, u), n2 * 2048, &fullB[p]);
@@ -170,7 +175,7 @@ __global__ void __launch_bounds__(kThreads, 1) gram_store_kernel(GramStoreDesc d
       // read them are done, and a chunk's MMAs go out as soon as its operands are
       // ready, so every copy slot stays in flight while the tensor core waits.
       // No progress for kWaitCycles ends the loop with a failure.
-      int a = 0, need = 0;  // chunk a = (block a / 8, digit a % 8); need: 0 = B, 1 = accumulator, 2 = A
+      int a = 0, need = 0;  // chunk a = (block a / 7, digit a % 7); need: 0 = B, 1 = accumulator, 2 = A
       long long idle0 = clock64();
       while (a < ntot) {
         bool progress = false;
@@ -182,12 +187,12 @@ __global__ void __launch_bounds__(kThreads, 1) gram_store_kernel(GramStoreDesc d
         }
         // B of block issuedB into the buffer of block issuedB - 2 once all its MMAs are done
         const int xb = issuedB - 2;
-        if (issuedB < nbl && (xb + 1) * kDigits <= a && mbar_test(&accdone[xb & 1], (xb >> 1) & 1)) {
+        if (issuedB < nbl && (xb + 1) * kStoreDigits <= a && mbar_test(&accdone[xb & 1], (xb >> 1) & 1)) {
           issue_B(issuedB);
           ++issuedB;
           progress = true;
         }
-        const int bl = a / kDigits, t = a % kDigits, p = bl & 1, slot = a % S;
+        const int bl = a / kStoreDigits, t = a % kStoreDigits, p = bl & 1, slot = a % S;
         if (need == 0) {
           if (t != 0) {
             need = 1;
@@ -204,13 +209,15 @@ __global__ void __launch_bounds__(kThreads, 1) gram_store_kernel(GramStoreDesc d
           const uint32_t a0 = smem_u32(Aring + slot * kDigBytes);
           const uint32_t b0 = smem_u32(Bbuf + p * C::kBBuf);
           // both operands MN-major: (LBO, SBO) = (K-direction, MN-direction) core strides
+          // digit t of A (t < 7: the store keeps seven) times B's planes u <= 7 - t
+          // (plane 7 is zero): levels t .. 7
           const uint32_t id = idesc_f16(kStoreRows, (kDigits - t) * NBT) | (1u << 15) | (1u << 16);
 #pragma unroll
           for (int ks = 0; ks < kStoreRows / 16; ++ks)
             mma_bf16(acc, desc_interleave(a0 + ks * 256, 128, 2048), desc_interleave(b0 + ks * 256, 128, 2048), id,
                      (t == 0 && ks == 0) ? 0u : 1u);
           mma_commit(&doneA[slot]);
-          if (t == kDigits - 1) mma_commit(&accdone[p]);
+          if (t == kStoreDigits - 1) mma_commit(&accdone[p]);
           ++a;
           need = 0;
           progress = true;

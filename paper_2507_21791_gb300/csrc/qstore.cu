@@ -12,8 +12,10 @@
 // |q_ik|).  In  sum_k q_ik B_kj  the factor 2^E_bk moves onto row k of B, so
 // B'_kj = B_kj 2^E_bk is split against one exponent per column j,
 // F_j > log2 max_k |B'_kj|, and the products of all k add up in one exact
-// fixed-point sum: q_ik B_kj = N_ik M_kj 2^(F_j - 124).  The error of one product
-// term is below 9 2^(F_j - 62) <= 2^-56.8 max_k |B_kj| max_{i in b} |q_ik|.
+// fixed-point sum: q_ik B_kj = N_ik M_kj 2^(F_j - 124).  The store keeps seven of
+// the eight digits of N_ik (off by at most 129 units of 2^(E_bk - 62)); with the
+// truncation of B' and the dropped levels the error of one product term is below
+// 2^-53.9 max_k |B_kj| max_{i in b} |q_ik|.
 //
 // Paired form (BCGSI+P-1S / -2S): the step's two projections share one pass
 // over [Q_{1:k-1} U_k] with B = [[Y, Z - Y M]; [0, M]], M = Y_kk^{-1} W (tail.cu):
@@ -105,10 +107,10 @@ __global__ void __launch_bounds__(kStoreRows) qsplit_kernel(QStore qs, const T* 
       digits_pair_f16((uint32_t)(N[2 * p] >> 32), (uint32_t)N[2 * p], (uint32_t)(N[2 * p + 1] >> 32),
                       (uint32_t)N[2 * p + 1], w[p]);
     const int G = g8 / kStoreCols, g = (g8 % kStoreCols) / 8;
-    uint8_t* dst = qs.dig + ((size_t)(b * qs.ngroups + G) * 8) * (kStoreRows * kStoreCols * 2) +
+    uint8_t* dst = qs.dig + ((size_t)(b * qs.ngroups + G) * kStoreDigits) * (kStoreRows * kStoreCols * 2) +
                    (size_t)(g * 16 + (i >> 3)) * 128 + (i & 7) * 16;
 #pragma unroll
-    for (int t = 0; t < 8; ++t)
+    for (int t = 0; t < kStoreDigits; ++t)
       *reinterpret_cast<uint4*>(dst + (size_t)t * (kStoreRows * kStoreCols * 2)) =
           make_uint4(w[0][t], w[1][t], w[2][t], w[3][t]);
   }
@@ -165,10 +167,10 @@ __global__ void __launch_bounds__(kStoreRows) qsplit_reg_kernel(QStore qs, const
                         (uint32_t)N[2 * p + 1], w[p]);
       const int col = k0 + g8;
       const int G = col / kStoreCols, g = (col % kStoreCols) / 8;
-      uint8_t* dst = qs.dig + ((size_t)(b * qs.ngroups + G) * 8) * (kStoreRows * kStoreCols * 2) +
+      uint8_t* dst = qs.dig + ((size_t)(b * qs.ngroups + G) * kStoreDigits) * (kStoreRows * kStoreCols * 2) +
                      (size_t)(g * 16 + (i >> 3)) * 128 + (i & 7) * 16;
 #pragma unroll
-      for (int t = 0; t < 8; ++t)
+      for (int t = 0; t < kStoreDigits; ++t)
         *reinterpret_cast<uint4*>(dst + (size_t)t * (kStoreRows * kStoreCols * 2)) =
             make_uint4(w[0][t], w[1][t], w[2][t], w[3][t]);
     }
@@ -191,7 +193,7 @@ constexpr int kRows = 128;                       // rows per block (MMA M)
 constexpr int kK = 16;                           // K-values per chunk (one MMA K step)
 constexpr int kStages = 3;                       // chunks in flight
 constexpr int kATileT = kRows * kK * 2;          // one digit of one chunk: 4 KB
-constexpr int kAStage = kDigits * kATileT;       // 32 KB
+constexpr int kAStage = kStoreDigits * kATileT;  // 28 KB: the store's digits of one chunk
 constexpr int kGroupChunks = 8;                  // 128 K-values between read-backs
 constexpr int kMaxK = 2048;                      // store columns of one projection at most
 constexpr size_t kDigTile = (size_t)kStoreRows * kStoreCols * 2;  // one digit of a store tile
@@ -420,8 +422,8 @@ __global__ void __launch_bounds__(Roles<NOUT>::kThreads, 1) proj_store_kernel(St
   if (warp == kCtl) {
     // ------------------------------------------------ copies and MMAs
     if (lane == 0) {
-      // one chunk = the 4 KB piece kc & 7 of the 8 digit tiles of store tile (b, kc >> 3):
-      // one tensor copy through amap (box {256, 2, 1, 8, 1} of u64 at x = 0), else 8 bulk copies
+      // one chunk = the 4 KB piece kc & 7 of the 7 digit tiles of store tile (b, kc >> 3):
+      // one tensor copy through amap (box {256, 2, 1, 7, 1} of u64 at x = 0), else 7 bulk copies
       auto issue_copy = [&](int g) {
         const int slot = g % kStages, kc = g % nch;
         const int64_t b = blk_of(g / nch);
@@ -434,7 +436,7 @@ __global__ void __launch_bounds__(Roles<NOUT>::kThreads, 1) proj_store_kernel(St
         const uint8_t* src = d.qs.dig + (size_t)b * d.qs.ngroups * kStoreTileBytes +
                              (size_t)(kc >> 3) * kStoreTileBytes + (size_t)(kc & 7) * kATileT;
 #pragma unroll
-        for (int t = 0; t < kDigits; ++t)
+        for (int t = 0; t < kStoreDigits; ++t)
           bulk_g2s(Aring + slot * kAStage + t * kATileT, src + (size_t)t * kDigTile, kATileT, &fullA[slot]);
       };
       int issued = 0, got = 0;
@@ -467,9 +469,10 @@ __global__ void __launch_bounds__(Roles<NOUT>::kThreads, 1) proj_store_kernel(St
           const uint32_t a0 = smem_u32(Aring + slot * kAStage);
           const uint32_t b0 = smem_u32(Bring + bslot * C::kBStage);
           const uint32_t acc = tmem + (uint32_t)((gg & 1) * C::kAcc);
-          // digit t of A times digit tiles [B_0 .. B_{7-t}]: tile u lands in level t + u
+          // digit t of A (t < 7: the store keeps seven) times digit tiles
+          // [B_0 .. B_{7-t}] of B' (eight): tile u lands in level t + u
 #pragma unroll 1
-          for (int t = 0; t < kDigits; ++t)
+          for (int t = 0; t < kStoreDigits; ++t)
             mma_bf16(acc + (uint32_t)(t * NBT), desc_interleave(a0 + t * kATileT, 2048, 128),
                      desc_interleave(b0, 128, 256), idesc_f16(kRows, (kDigits - t) * NBT),
                      (first && t == 0) ? 0u : 1u);
@@ -841,14 +844,14 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_tiled() {
 }
 
 // The digit store as a 5-d tensor of u64 (innermost first): 256 x 2 (one 4 KB
-// piece = 16 columns of one digit of a tile), 8 pieces, 8 digits, nblk * ngroups
+// piece = 16 columns of one digit of a tile), 8 pieces, 7 digits, nblk * ngroups
 // tiles; strides 2 KB, 4 KB, 32 KB, 256 KB.  False when it cannot be encoded.
 bool store_tensor_map(const QStore& qs, CUtensorMap* map) {
   PFN_cuTensorMapEncodeTiled_v12000 fn = encode_tiled();
   if (fn == nullptr) return false;
-  const cuuint64_t dims[5] = {256, 2, 8, (cuuint64_t)kDigits, (cuuint64_t)qs.nblk * (cuuint64_t)qs.ngroups};
+  const cuuint64_t dims[5] = {256, 2, 8, (cuuint64_t)kStoreDigits, (cuuint64_t)qs.nblk * (cuuint64_t)qs.ngroups};
   const cuuint64_t strides[4] = {2048, (cuuint64_t)kATileT, (cuuint64_t)kDigTile, (cuuint64_t)kStoreTileBytes};
-  const cuuint32_t box[5] = {256, 2, 1, (cuuint32_t)kDigits, 1};
+  const cuuint32_t box[5] = {256, 2, 1, (cuuint32_t)kStoreDigits, 1};
   const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
   if (dims[4] == 0 || dims[4] > (1ull << 32)) return false;
   return fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 5, qs.dig, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -920,8 +923,8 @@ cudaError_t launch_qsplit(const QStore& qs, const void* src, int64_t lds, const 
     run(0.0f);
   else
     run(0.0);
-  // reads the s new columns, writes 16 bytes of digits per element
-  prof_end(slot, kProfStoreSplit, stream, 0.0, (double)m * s * ((fp32 ? 4.0 : 8.0) + 16.0));
+  // reads the s new columns, writes 2 kStoreDigits bytes of digits per element
+  prof_end(slot, kProfStoreSplit, stream, 0.0, (double)m * s * ((fp32 ? 4.0 : 8.0) + 2.0 * kStoreDigits));
   note_launch(1);
   return cudaGetLastError();
 }

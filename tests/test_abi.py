@@ -62,15 +62,16 @@ def test_workspace_size_queries():
         small32 = bcgs.workspace_size(2 ** 22, 256, 16, "bcgsi+p-1s", "fp32")
         bcgs.set_gram_engine("tensor")
         big = bcgs.workspace_size(2 ** 22, 256, 16, "bcgsi+p-1s")
-        # the tensor engine adds the digit store of Q: 16 bytes per element
-        # plus one exponent per 128 rows and column, for both storage types
+        # the tensor engine adds the digit store of Q: 14 bytes per element
+        # (seven f16 digits) plus one exponent per 128 rows and column, for
+        # both storage types
         fp32 = bcgs.workspace_size(2 ** 22, 256, 16, "bcgsi+p-1s", "fp32")
     finally:
         bcgs.set_gram_engine(old)
     assert 2 ** 22 * 16 * 8 < small < 2 ** 22 * 16 * 8 * 3
     # digits, one exponent per 128 rows and column, and 32 exponents per row
     # block for the coefficient side of the projections
-    store = 2 ** 22 * 256 * 16 + (2 ** 22 // 128) * 256 * 4 + (2 ** 22 // 128) * 32 * 4
+    store = 2 ** 22 * 256 * 14 + (2 ** 22 // 128) * 256 * 4 + (2 ** 22 // 128) * 32 * 4
     assert big - small == pytest.approx(store, abs=2 ** 12)
     assert fp32 - small32 == pytest.approx(store, abs=2 ** 12)
     assert small32 < small and fp32 < big  # FP32 blocks of U and V
