@@ -205,6 +205,8 @@ __device__ __forceinline__ double unfold(long long hi, long long lo, int cexp_a,
 // so a digit product is at most 2^14 and a level of at most eight pairs summed
 // over 128 K-values is at most 7 2^21 < 2^24: exact in fp32 for 128 K-values
 // between read-backs.  Digits are stored as f16 (integers up to 2048 are exact).
+// The store keeps d_0 .. d_6 (kStoreDigits); the coefficient side of a
+// projection, split in shared memory, keeps all eight.
 
 // N + 0x8080808080808080 for a with biased exponent `e`, magnitude bits `mant`
 // (implicit bit included) and sign `neg`, relative to the exponent field `cexp`
