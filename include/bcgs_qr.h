@@ -375,10 +375,11 @@ BCGS_API int bcgs_chol(int32_t s, const double* A, int32_t lda, double* R, int32
  *      of Q), digit pairs are multiplied on the tensor cores
  *      with exact integer sums, and one FP64 rounding per row chunk remains
  *      (error per product term <= 2^-57.1 max|a_i| max|b_j|).  A factorization
- *      with FP64 storage and s <= 32 keeps Q as such digits (balanced digits in
- *      [-128, 127], one exponent per 128 rows and column, error per term
- *      <= 2^-56.8 max|a| max|b| over the 128-row block) and computes its Grams
- *      (s a multiple of 8) and projections from them;
+ *      with s <= 32 (either storage type) keeps Q as such digits (the seven
+ *      leading balanced digits in [-128, 127], one exponent per 128 rows and
+ *      column, error per term about 2^-53.9 max|a| max|b| over the 128-row
+ *      block, below the FP64 unit roundoff) and computes its Grams (s a
+ *      multiple of 8) and projections from them;
  *   2  tensor cores whenever the shape allows it.
  * A factorization reads the engine when it is initialized (bcgs_qr_init,
  * bcgs_qr_factor): that fixes whether it keeps the digit store.

@@ -845,7 +845,7 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_tiled() {
 
 // The digit store as a 5-d tensor of u64 (innermost first): 256 x 2 (one 4 KB
 // piece = 16 columns of one digit of a tile), 8 pieces, 7 digits, nblk * ngroups
-// tiles; strides 2 KB, 4 KB, 32 KB, 256 KB.  False when it cannot be encoded.
+// tiles; strides 2 KB, 4 KB, 32 KB, 224 KB.  False when it cannot be encoded.
 bool store_tensor_map(const QStore& qs, CUtensorMap* map) {
   PFN_cuTensorMapEncodeTiled_v12000 fn = encode_tiled();
   if (fn == nullptr) return false;
