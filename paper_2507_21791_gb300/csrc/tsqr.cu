@@ -48,6 +48,47 @@ __device__ __forceinline__ double dot4(const double* a, const double* b, int r0,
   return (w0 + w1) + (w2 + w3);
 }
 
+// The sums over r = r0, r0 + 32, ... < rows of a[r] b0[r] and a[r] b1[r] (b1
+// may be null: its sum is 0), with two interleaved accumulators each, then one
+// warp reduce-scatter for both (lanes 0..15 finish b0's, 16..31 b1's): five FP64
+// additions per lane for the pair instead of five per column, on GB300's scarce
+// FP64 pipe.  Every lane gets both sums; the order depends on the shape only.
+__device__ __forceinline__ void dot2_pair(const double* a, const double* b0, const double* b1, int r0, int rows,
+                                          int lane, double& s0, double& s1) {
+  double p0 = 0.0, q0 = 0.0, p1 = 0.0, q1 = 0.0;
+  int r = r0;
+  if (b1 != nullptr) {
+    for (; r + 32 < rows; r += 64) {
+      const double x = a[r], y = a[r + 32];
+      p0 = fma(x, b0[r], p0);
+      q0 = fma(y, b0[r + 32], q0);
+      p1 = fma(x, b1[r], p1);
+      q1 = fma(y, b1[r + 32], q1);
+    }
+    for (; r < rows; r += 32) {
+      const double x = a[r];
+      p0 = fma(x, b0[r], p0);
+      p1 = fma(x, b1[r], p1);
+    }
+  } else {
+    for (; r + 32 < rows; r += 64) {
+      p0 = fma(a[r], b0[r], p0);
+      q0 = fma(a[r + 32], b0[r + 32], q0);
+    }
+    for (; r < rows; r += 32) p0 = fma(a[r], b0[r], p0);
+  }
+  p0 += q0;
+  p1 += q1;
+  const bool upper = lane >= 16;
+  double keep = upper ? p1 : p0;
+  const double give = upper ? p0 : p1;
+  keep += __shfl_xor_sync(0xffffffffu, give, 16);
+#pragma unroll
+  for (int o = 8; o > 0; o >>= 1) keep += __shfl_xor_sync(0xffffffffu, keep, o);
+  s0 = __shfl_sync(0xffffffffu, keep, 0);
+  s1 = __shfl_sync(0xffffffffu, keep, 16);
+}
+
 // In-place Householder QR of the rows x s column-major matrix A (ld = rows) in
 // shared memory.  On return A holds R in its upper triangle and v_j below the
 // diagonal (v_j has an implicit 1 at row j); tau[j] the reflector scalars.
@@ -81,19 +122,37 @@ __device__ void block_householder(double* A, int rows, int s, double* tau) {
     // reflector j is final; apply it to the columns l > j.  Warp 0 takes column
     // j + 1 first and forms reflector j + 1 at once (look-ahead), while the other
     // warps finish their columns with reflector j: one barrier per column.
+    // Each warp takes a pair of columns (l0, l0 + 1), sharing the loads of v_j and
+    // one reduction (dot2_pair).
     const double* aj = A + (size_t)j * rows;
     const double t = tau[j];
-    for (int l = j + 1 + warp; l < s; l += kWarps) {
-      double* al = A + (size_t)l * rows;
+    const int npairs = (s - j) / 2;  // ceil((s - j - 1) / 2)
+    for (int pr = warp; pr < npairs; pr += kWarps) {
+      const int l0 = j + 1 + 2 * pr;
+      double* a0 = A + (size_t)l0 * rows;
+      double* a1 = l0 + 1 < s ? a0 + rows : nullptr;
       if (t != 0.0) {
-        double w = warp_sum(dot4(aj, al, j + 1 + lane, rows)) + al[j];
-        w *= t;
-        __syncwarp();  // every lane has read al[j] before lane 0 updates it
-        if (lane == 0) al[j] -= w;
-        for (int r = j + 1 + lane; r < rows; r += 32) al[r] = fma(-aj[r], w, al[r]);
+        double s0, s1;
+        dot2_pair(aj, a0, a1, j + 1 + lane, rows, lane, s0, s1);
+        const double w0 = (s0 + a0[j]) * t;
+        const double w1 = a1 != nullptr ? (s1 + a1[j]) * t : 0.0;
+        __syncwarp();  // every lane has read a0[j], a1[j] before lane 0 updates them
+        if (lane == 0) {
+          a0[j] -= w0;
+          if (a1 != nullptr) a1[j] -= w1;
+        }
+        if (a1 != nullptr) {
+          for (int r = j + 1 + lane; r < rows; r += 32) {
+            const double v = aj[r];
+            a0[r] = fma(-v, w0, a0[r]);
+            a1[r] = fma(-v, w1, a1[r]);
+          }
+        } else {
+          for (int r = j + 1 + lane; r < rows; r += 32) a0[r] = fma(-aj[r], w0, a0[r]);
+        }
         __syncwarp();
       }
-      if (l == j + 1) reflect(l);
+      if (l0 == j + 1) reflect(l0);
     }
     __syncthreads();
   }
@@ -169,14 +228,21 @@ tsqr_leaf_factor(TsqrPlan p, Seg a, double* work, double* R, int32_t ldr, DevSta
     double* VV = A + (size_t)mt * s;  // s x s: (V^T V)_{ij} for i < j
     double* Tl = VV + (size_t)s * s;
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    // (V^T V)_ij = v_i[j] + sum_{r > j} v_i[r] v_j[r]  (v_j[j] = 1, v_j[r < j] = 0)
-    for (int e = warp; e < s * s; e += kWarps) {
-      const int i = e % s, j = e / s;
-      if (i < j) {
+    // (V^T V)_ij = v_i[j] + sum_{r > j} v_i[r] v_j[r]  (v_j[j] = 1, v_j[r < j] = 0):
+    // for each j the entries i < j in pairs (i, i + 1), one task per warp
+    int task = 0;
+    for (int j = 1; j < s; ++j) {
+      const double* vj = A + (size_t)j * mt;
+      for (int i = 0; i < j; i += 2, ++task) {
+        if (task % kWarps != warp) continue;
         const double* vi = A + (size_t)i * mt;
-        const double* vj = A + (size_t)j * mt;
-        const double d = warp_sum(dot4(vi, vj, j + 1 + lane, mt));
-        if (lane == 0) VV[i + (size_t)j * s] = d + vi[j];
+        const double* vi1 = i + 1 < j ? vi + mt : nullptr;
+        double d0, d1;
+        dot2_pair(vj, vi, vi1, j + 1 + lane, mt, lane, d0, d1);
+        if (lane == 0) {
+          VV[i + (size_t)j * s] = d0 + vi[j];
+          if (vi1 != nullptr) VV[i + 1 + (size_t)j * s] = d1 + vi1[j];
+        }
       }
     }
     __syncthreads();
