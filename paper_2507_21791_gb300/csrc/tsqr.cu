@@ -483,26 +483,29 @@ __global__ void __launch_bounds__(256) rows_times_small_kernel(int64_t m, int32_
 // V^T V and the explicit-Q product) runs in double-float (dfloat.cuh).  Column
 // norms, the reflector scalars, the WY triangle and the tree levels stay FP64;
 // the column norms, computed in FP64, do not overflow float's range.
-__device__ __forceinline__ df warp_sum_df(df v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1)
-    v = df_add(v, df{__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)});
-  return v;
-}
-
-// sum over r = r0, r0 + 32, ... < rows of a[r] b[r]: four interleaved
-// accumulators, as dot4 (the order depends on the shape only)
-__device__ __forceinline__ df dot4_df(const df* a, const df* b, int r0, int rows) {
-  df w0{0.f, 0.f}, w1{0.f, 0.f}, w2{0.f, 0.f}, w3{0.f, 0.f};
-  int r = r0;
-  for (; r + 96 < rows; r += 128) {
-    w0 = df_fma(a[r], b[r], w0);
-    w1 = df_fma(a[r + 32], b[r + 32], w1);
-    w2 = df_fma(a[r + 64], b[r + 64], w2);
-    w3 = df_fma(a[r + 96], b[r + 96], w3);
+// dot2_pair in double-float: the sums of a[r] b0[r] and a[r] b1[r] (b1 may be
+// null), one accumulator each, then one warp reduce-scatter for both.
+__device__ __forceinline__ void dot2_pair_df(const df* a, const df* b0, const df* b1, int r0, int rows, int lane,
+                                             df& s0, df& s1) {
+  df p0{0.f, 0.f}, p1{0.f, 0.f};
+  if (b1 != nullptr) {
+    for (int r = r0; r < rows; r += 32) {
+      const df x = a[r];
+      p0 = df_fma(x, b0[r], p0);
+      p1 = df_fma(x, b1[r], p1);
+    }
+  } else {
+    for (int r = r0; r < rows; r += 32) p0 = df_fma(a[r], b0[r], p0);
   }
-  for (; r < rows; r += 32) w0 = df_fma(a[r], b[r], w0);
-  return df_add(df_add(w0, w1), df_add(w2, w3));
+  const bool upper = lane >= 16;
+  df keep = upper ? p1 : p0;
+  const df give = upper ? p0 : p1;
+  keep = df_add(keep, df{__shfl_xor_sync(0xffffffffu, give.hi, 16), __shfl_xor_sync(0xffffffffu, give.lo, 16)});
+#pragma unroll
+  for (int o = 8; o > 0; o >>= 1)
+    keep = df_add(keep, df{__shfl_xor_sync(0xffffffffu, keep.hi, o), __shfl_xor_sync(0xffffffffu, keep.lo, o)});
+  s0 = df{__shfl_sync(0xffffffffu, keep.hi, 0), __shfl_sync(0xffffffffu, keep.lo, 0)};
+  s1 = df{__shfl_sync(0xffffffffu, keep.hi, 16), __shfl_sync(0xffffffffu, keep.lo, 16)};
 }
 
 // block_householder in double-float (the same steps, look-ahead and barriers);
@@ -541,18 +544,36 @@ __device__ void block_householder_df(df* A, int rows, int s, double* tau) {
   for (int j = 0; j < s; ++j) {
     const df* aj = A + (size_t)j * rows;
     const double t = tau[j];
-    for (int l = j + 1 + warp; l < s; l += nwarps) {
-      df* al = A + (size_t)l * rows;
+    // pairs of columns per warp, as in block_householder
+    const int npairs = (s - j) / 2;
+    const df td = df_from(t);
+    for (int pr = warp; pr < npairs; pr += nwarps) {
+      const int l0 = j + 1 + 2 * pr;
+      df* a0 = A + (size_t)l0 * rows;
+      df* a1 = l0 + 1 < s ? a0 + rows : nullptr;
       if (t != 0.0) {
-        df w = df_add(warp_sum_df(dot4_df(aj, al, j + 1 + lane, rows)), al[j]);
-        w = df_mul(w, df_from(t));
-        __syncwarp();  // every lane has read al[j] before lane 0 updates it
-        if (lane == 0) al[j] = df_add(al[j], df_neg(w));
-        const df nw = df_neg(w);
-        for (int r = j + 1 + lane; r < rows; r += 32) al[r] = df_fma(aj[r], nw, al[r]);
+        df s0, s1;
+        dot2_pair_df(aj, a0, a1, j + 1 + lane, rows, lane, s0, s1);
+        const df w0 = df_mul(df_add(s0, a0[j]), td);
+        const df w1 = a1 != nullptr ? df_mul(df_add(s1, a1[j]), td) : df{0.f, 0.f};
+        __syncwarp();  // every lane has read a0[j], a1[j] before lane 0 updates them
+        if (lane == 0) {
+          a0[j] = df_add(a0[j], df_neg(w0));
+          if (a1 != nullptr) a1[j] = df_add(a1[j], df_neg(w1));
+        }
+        const df nw0 = df_neg(w0), nw1 = df_neg(w1);
+        if (a1 != nullptr) {
+          for (int r = j + 1 + lane; r < rows; r += 32) {
+            const df v = aj[r];
+            a0[r] = df_fma(v, nw0, a0[r]);
+            a1[r] = df_fma(v, nw1, a1[r]);
+          }
+        } else {
+          for (int r = j + 1 + lane; r < rows; r += 32) a0[r] = df_fma(aj[r], nw0, a0[r]);
+        }
         __syncwarp();
       }
-      if (l == j + 1) reflect(l);
+      if (l0 == j + 1) reflect(l0);
     }
     __syncthreads();
   }
@@ -588,13 +609,19 @@ tsqr_leaf_factor_df(TsqrPlan p, Seg a, double* work, double* R, int32_t ldr, Dev
   double* Tl = VV + (size_t)s * s;
   {
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    for (int e = warp; e < s * s; e += kDfThreads / 32) {
-      const int i = e % s, j = e / s;
-      if (i < j) {
+    int task = 0;
+    for (int j = 1; j < s; ++j) {
+      const df* vj = A + (size_t)j * mt;
+      for (int i = 0; i < j; i += 2, ++task) {
+        if (task % (kDfThreads / 32) != warp) continue;
         const df* vi = A + (size_t)i * mt;
-        const df* vj = A + (size_t)j * mt;
-        const df d = warp_sum_df(dot4_df(vi, vj, j + 1 + lane, mt));
-        if (lane == 0) VV[i + (size_t)j * s] = df_dbl(df_add(d, vi[j]));
+        const df* vi1 = i + 1 < j ? vi + mt : nullptr;
+        df d0, d1;
+        dot2_pair_df(vj, vi, vi1, j + 1 + lane, mt, lane, d0, d1);
+        if (lane == 0) {
+          VV[i + (size_t)j * s] = df_dbl(df_add(d0, vi[j]));
+          if (vi1 != nullptr) VV[i + 1 + (size_t)j * s] = df_dbl(df_add(d1, vi1[j]));
+        }
       }
     }
     __syncthreads();
