@@ -158,20 +158,38 @@ __device__ void block_householder(double* A, int rows, int s, double* tau) {
   }
 }
 
-// E <- H_0 H_1 ... H_{s-1} E for reflectors stored as by block_householder.
+// E <- H_0 H_1 ... H_{s-1} E for reflectors stored as by block_householder
+// (pairs of columns of E per warp, as there).
 __device__ void block_apply_q(const double* V, const double* tau, double* E, int rows, int s) {
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int nwarps = blockDim.x / 32;
+  const int npairs = (s + 1) / 2;
   for (int j = s - 1; j >= 0; --j) {
     const double t = tau[j];
     if (t != 0.0) {
       const double* vj = V + (size_t)j * rows;
-      for (int c = warp; c < s; c += kWarps) {
-        double* ec = E + (size_t)c * rows;
-        double w = warp_sum(dot4(vj, ec, j + 1 + lane, rows)) + ec[j];
-        w *= t;
+      for (int pr = warp; pr < npairs; pr += nwarps) {
+        double* e0 = E + (size_t)(2 * pr) * rows;
+        double* e1 = 2 * pr + 1 < s ? e0 + rows : nullptr;
+        double s0, s1;
+        dot2_pair(vj, e0, e1, j + 1 + lane, rows, lane, s0, s1);
+        const double w0 = (s0 + e0[j]) * t;
+        const double w1 = e1 != nullptr ? (s1 + e1[j]) * t : 0.0;
         __syncwarp();
-        if (lane == 0) ec[j] -= w;
-        for (int r = j + 1 + lane; r < rows; r += 32) ec[r] = fma(-vj[r], w, ec[r]);
+        if (lane == 0) {
+          e0[j] -= w0;
+          if (e1 != nullptr) e1[j] -= w1;
+        }
+        if (e1 != nullptr) {
+          for (int r = j + 1 + lane; r < rows; r += 32) {
+            const double v = vj[r];
+            e0[r] = fma(-v, w0, e0[r]);
+            e1[r] = fma(-v, w1, e1[r]);
+          }
+        } else {
+          for (int r = j + 1 + lane; r < rows; r += 32) e0[r] = fma(-vj[r], w0, e0[r]);
+        }
+        __syncwarp();
       }
     }
     __syncthreads();
@@ -742,6 +760,123 @@ tsqr_leaf_apply_df(TsqrPlan p, const double* work, void* q, int64_t ldq, const D
   }
 }
 
+// block_apply_q in double-float.
+__device__ void block_apply_q_df(const df* V, const double* tau, df* E, int rows, int s) {
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int nwarps = blockDim.x / 32;
+  const int npairs = (s + 1) / 2;
+  for (int j = s - 1; j >= 0; --j) {
+    const double t = tau[j];
+    if (t != 0.0) {
+      const df td = df_from(t);
+      const df* vj = V + (size_t)j * rows;
+      for (int pr = warp; pr < npairs; pr += nwarps) {
+        df* e0 = E + (size_t)(2 * pr) * rows;
+        df* e1 = 2 * pr + 1 < s ? e0 + rows : nullptr;
+        df s0, s1;
+        dot2_pair_df(vj, e0, e1, j + 1 + lane, rows, lane, s0, s1);
+        const df w0 = df_mul(df_add(s0, e0[j]), td);
+        const df w1 = e1 != nullptr ? df_mul(df_add(s1, e1[j]), td) : df{0.f, 0.f};
+        __syncwarp();
+        if (lane == 0) {
+          e0[j] = df_add(e0[j], df_neg(w0));
+          if (e1 != nullptr) e1[j] = df_add(e1[j], df_neg(w1));
+        }
+        const df nw0 = df_neg(w0), nw1 = df_neg(w1);
+        if (e1 != nullptr) {
+          for (int r = j + 1 + lane; r < rows; r += 32) {
+            const df v = vj[r];
+            e0[r] = df_fma(v, nw0, e0[r]);
+            e1[r] = df_fma(v, nw1, e1[r]);
+          }
+        } else {
+          for (int r = j + 1 + lane; r < rows; r += 32) e0[r] = df_fma(vj[r], nw0, e0[r]);
+        }
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// tsqr_node_factor for the tree of an FP32 block: the stacked R factors (FP64)
+// factored in double-float; the reflectors go back into the level's slots as
+// double-float pairs (read only by tsqr_node_apply_df), tau and the R factor
+// passed up in FP64.  Dynamic shared memory: the node matrix plus s x s doubles.
+__global__ void __launch_bounds__(kDfThreads)
+tsqr_node_factor_df(TsqrPlan p, int32_t level, double* work, double* R, int32_t ldr, DevStatus* st,
+                    int32_t block) {
+  if (failed(st)) return;
+  extern __shared__ double sm[];
+  __shared__ double tau[64];
+  const int s = p.s, fan = p.fan, rows = fan * s;
+  const int n = blockIdx.x;
+  const int nchild = min(fan, p.nodes[level - 1] - n * fan);
+  const int re = nchild * s;
+  df* A = reinterpret_cast<df*>(sm);
+  double* Rb = sm + (size_t)rows * s;  // s x s: the root's R in FP64
+  double* G = work + p.off_lvl[level] + (size_t)n * rows * s;
+  for (int e = threadIdx.x; e < re * s; e += kDfThreads) {
+    const int r = e % re, j = e / re;
+    A[e] = df_from(G[r + (size_t)j * rows]);
+  }
+  __syncthreads();
+  block_householder_df(A, re, s, tau);
+  df* Gd = reinterpret_cast<df*>(G);
+  for (int e = threadIdx.x; e < re * s; e += kDfThreads) {
+    const int r = e % re, j = e / re;
+    Gd[r + (size_t)j * rows] = A[e];
+  }
+  double* tg = work + p.off_tau[level] + (size_t)n * s;
+  for (int j = threadIdx.x; j < s; j += kDfThreads) tg[j] = tau[j];
+  if (level == p.nlevels - 1) {
+    for (int e = threadIdx.x; e < s * s; e += kDfThreads) {
+      const int i = e % s, j = e / s;
+      Rb[e] = df_dbl(A[i + (size_t)j * re]);
+    }
+    __syncthreads();
+    finish_root(Rb, s, s, R, ldr, work + p.off_b[level], st, block);
+    return;
+  }
+  double* P = work + p.off_lvl[level + 1] + (size_t)(n / fan) * rows * s;
+  const int rbase = (n % fan) * s;
+  for (int e = threadIdx.x; e < s * s; e += kDfThreads) {
+    const int i = e % s, j = e / s;
+    P[rbase + i + (size_t)j * rows] = i <= j ? df_dbl(A[i + (size_t)j * re]) : 0.0;
+  }
+}
+
+// tsqr_node_apply for the tree of an FP32 block, in double-float; the children's
+// coefficient blocks go out in FP64.
+__global__ void __launch_bounds__(kDfThreads)
+tsqr_node_apply_df(TsqrPlan p, int32_t level, double* work, const DevStatus* st) {
+  if (failed(st)) return;
+  extern __shared__ double sm[];
+  __shared__ double tau[64];
+  const int s = p.s, fan = p.fan, rows = fan * s;
+  const int n = blockIdx.x;
+  const int nchild = min(fan, p.nodes[level - 1] - n * fan);
+  const int re = nchild * s;
+  df* V = reinterpret_cast<df*>(sm);
+  df* E = V + (size_t)re * s;
+  const df* Gd = reinterpret_cast<const df*>(work + p.off_lvl[level] + (size_t)n * rows * s);
+  const double* B = work + p.off_b[level] + (size_t)n * s * s;
+  for (int e = threadIdx.x; e < re * s; e += kDfThreads) {
+    const int r = e % re, j = e / re;
+    V[e] = Gd[r + (size_t)j * rows];
+    E[e] = df_from(r < s ? B[r + (size_t)j * s] : 0.0);
+  }
+  for (int j = threadIdx.x; j < s; j += kDfThreads) tau[j] = work[p.off_tau[level] + (size_t)n * s + j];
+  __syncthreads();
+  block_apply_q_df(V, tau, E, re, s);
+  for (int e = threadIdx.x; e < nchild * s * s; e += kDfThreads) {
+    const int g = e / (s * s), rem = e % (s * s);
+    const int i = rem % s, j = rem / s;
+    work[p.off_b[level - 1] + (size_t)(n * fan + g) * s * s + i + (size_t)j * s] =
+        df_dbl(E[g * s + i + (size_t)j * re]);
+  }
+}
+
 template <typename T>
 cudaError_t launch_tsqr_t(const TsqrPlan& p, Seg a, void* q, int64_t ldq, double* R, int32_t ldr,
                           double* work, DevStatus* st, int32_t block, cudaStream_t stream, MaxOut qmax) {
@@ -756,9 +891,9 @@ cudaError_t launch_tsqr_t(const TsqrPlan& p, Seg a, void* q, int64_t ldq, double
   if (e != cudaSuccess) return e;
   e = kDf ? ensure_dyn_smem(tsqr_leaf_apply_df, apply_f) : ensure_dyn_smem(tsqr_leaf_apply<T>, apply_f);
   if (e != cudaSuccess) return e;
-  e = ensure_dyn_smem(tsqr_node_factor, (size_t)(node_f));
+  e = kDf ? ensure_dyn_smem(tsqr_node_factor_df, node_f + ss) : ensure_dyn_smem(tsqr_node_factor, node_f);
   if (e != cudaSuccess) return e;
-  e = ensure_dyn_smem(tsqr_node_apply, (size_t)(2 * node_f));
+  e = kDf ? ensure_dyn_smem(tsqr_node_apply_df, 2 * node_f) : ensure_dyn_smem(tsqr_node_apply, 2 * node_f);
   if (e != cudaSuccess) return e;
   const int slot = prof_begin(stream);
   if (kDf)
@@ -766,9 +901,15 @@ cudaError_t launch_tsqr_t(const TsqrPlan& p, Seg a, void* q, int64_t ldq, double
   else
     tsqr_leaf_factor<T><<<p.nodes[0], kTsqrThreads, leaf_f + 2 * ss, stream>>>(p, a, work, R, ldr, st, block);
   for (int l = 1; l < p.nlevels; ++l)
-    tsqr_node_factor<<<p.nodes[l], kTsqrThreads, node_f, stream>>>(p, l, work, R, ldr, st, block);
+    if (kDf)
+      tsqr_node_factor_df<<<p.nodes[l], kDfThreads, node_f + ss, stream>>>(p, l, work, R, ldr, st, block);
+    else
+      tsqr_node_factor<<<p.nodes[l], kTsqrThreads, node_f, stream>>>(p, l, work, R, ldr, st, block);
   for (int l = p.nlevels - 1; l >= 1; --l)
-    tsqr_node_apply<<<p.nodes[l], kTsqrThreads, 2 * node_f, stream>>>(p, l, work, st);
+    if (kDf)
+      tsqr_node_apply_df<<<p.nodes[l], kDfThreads, 2 * node_f, stream>>>(p, l, work, st);
+    else
+      tsqr_node_apply<<<p.nodes[l], kTsqrThreads, 2 * node_f, stream>>>(p, l, work, st);
   if (kDf)
     tsqr_leaf_apply_df<<<p.nodes[0], kDfThreads, apply_f, stream>>>(p, work, q, ldq, st, qmax);
   else
