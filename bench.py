@@ -24,6 +24,7 @@ on a bounded sample of the same workload instead.
 from __future__ import annotations
 
 import argparse
+import gc
 import json
 import math
 import os
@@ -370,7 +371,15 @@ def main_ours(args):
         unknown = [f for f in wanted if f not in runners]
         if unknown:
             raise SystemExit(f"unknown forms: {unknown}")
-        forms = {f: runners[f]() for f in wanted}
+        forms = {}
+        gc.collect()
+        torch.cuda.empty_cache()
+        for f in wanted:
+            forms[f] = runners[f]()
+            # each form's buffers (and the private pools of its captured graphs)
+            # go back before the next form allocates
+            gc.collect()
+            torch.cuda.empty_cache()
 
     prof = main["prof"]
     peaks = measured_peaks()
@@ -644,6 +653,8 @@ def bench_serving(args, dev):
     """Serving form: Poisson requests (Krylov-like bases: m = 2^U(14,20), q ~ U{4..32}
     blocks of s in {4, 8, 16}, kappa up to 1e8), one block per call, Q and R
     resident, admission against a 120 GB budget, BCGSI+P-2S."""
+    import torch
+
     from paper_2507_21791_gb300.serving import GpuBackend, Server, draw_sources, make_requests
 
     sources, meta = draw_sources(24, seed=1400, device=str(dev))
@@ -658,6 +669,10 @@ def bench_serving(args, dev):
         rep["offered_req_per_s"] = rate
         rep["arrivals"] = len(reqs)
         out[key] = rep
+        # the resident bases of this run go back before the next run admits its own
+        del srv, be
+        gc.collect()
+        torch.cuda.empty_cache()
     return {"workload": "Poisson Krylov-basis requests, m=2^U(14,20), q~U{4..32}, s in {4,8,16}, "
                         "120 GB budget, BCGSI+P-2S (lazy) or BCGSI+ (eager finalize), pool of 24 "
                         "pre-generated bases", **out}
