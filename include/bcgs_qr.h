@@ -120,7 +120,14 @@ BCGS_API int bcgs_qr_workspace_size(int64_t m, int32_t n_max, int32_t s, int var
  * ldr): the whole of Alg. 2 (or the chosen variant) enqueued on `stream`.
  * `workspace` is a device buffer of at least bcgs_qr_workspace_size bytes,
  * 256-byte aligned, not shared with any other call in flight.  Returns after
- * enqueueing; read the outcome with bcgs_qr_factor_status. */
+ * enqueueing; read the outcome with bcgs_qr_factor_status.  From 2^17 rows,
+ * with the digit store and s a multiple of 16, the digit split of each next
+ * block of X runs ahead on a side stream of the calling thread while the
+ * current step's small FP64 tail runs: it is forked from `stream` by an event
+ * after the step's Gram and joined back before the step's projection, so all
+ * work stays ordered on `stream` (also inside a graph capture of `stream`; the
+ * side stream is created on a first call outside capture, and a first call
+ * under capture runs without it).  The results are the same bits either way. */
 BCGS_API int bcgs_qr_factor(int64_t m, int32_t n, int32_t s, int variant, int precision,
                    const void* X, int64_t ldx, void* Q, int64_t ldq, double* R,
                    int32_t ldr, void* workspace, size_t ws_bytes, void* stream);

@@ -24,7 +24,7 @@ constexpr int kMaxS = 64;
 constexpr int kMaxN = 2048;
 
 struct Layout {
-  size_t status, S[2], Sd[2], Yd, Rt1, Rt2, G, G2, Bp, partial, amax, amaxQ, amaxU, rowmaxQ, U, V, tsqr,
+  size_t status, status_side, S[2], Sd[2], Yd, Rt1, Rt2, G, G2, Bp, partial, amax, amaxQ, amaxU, rowmaxQ, U, V, tsqr,
       qstore, fexp, total;
   // row-partitioned form (nranks > 1): gathered copies, the stacked R factors,
   // the stacked factor's Q, the local TSQR factor and R, and the stacked TSQR's work
@@ -63,6 +63,8 @@ void make_layout(int64_t m, int32_t n_max, int32_t s, int variant, int precision
     return o;
   };
   L->status = take(sizeof(DevStatus));
+  // failures of work run ahead on the side stream, merged in stream order
+  L->status_side = take(sizeof(DevStatus));
   const size_t ss = (size_t)s * s * sizeof(double);
   for (int i = 0; i < 2; ++i) L->S[i] = take((size_t)n_max * s * sizeof(double));
   for (int i = 0; i < 2; ++i) L->Sd[i] = take(ss);
@@ -192,8 +194,15 @@ struct bcgs_qr_s {
   bcgs_allgather_fn allgather;
   void* ag_ctx;
   int32_t comm_failed;
+  // one-call factorization: the next block of X (null when unknown or not to
+  // be split ahead), and whether the current block's digits are already in the
+  // store (split ahead on the side stream during the previous step's tail)
+  const void* next_X;
+  int64_t next_ldx;
+  int32_t x_put;
 
   DevStatus* st() { return reinterpret_cast<DevStatus*>(ws + L.status); }
+  DevStatus* st_side() { return reinterpret_cast<DevStatus*>(ws + L.status_side); }
   double* buf(size_t off) { return reinterpret_cast<double*>(ws + off); }
   void* U() { return ws + L.U; }
   void* V() { return ws + L.V; }
@@ -332,6 +341,43 @@ cudaError_t store_put(bcgs_qr_s* h, const void* src, int64_t ld, int k0, int sb 
   return launch_qsplit(h->qs(), src, ld, h->Q, h->ldq, h->m, k0, sb ? sb : h->s, h->fp32, h->st(), h->j + 1,
                        h->stream);
 }
+
+// A side stream of the calling host thread (one per device) with the two events
+// that fork it from a factorization's stream and join it back.  Created on first
+// use, never while the factorization's stream is being captured into a graph.
+struct SideStream {
+  cudaStream_t s = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+};
+struct SidePool {
+  static constexpr int kDevices = 64;
+  SideStream dev[kDevices];
+  ~SidePool() {
+    for (SideStream& d : dev) {
+      if (d.join != nullptr) cudaEventDestroy(d.join);
+      if (d.fork != nullptr) cudaEventDestroy(d.fork);
+      if (d.s != nullptr) cudaStreamDestroy(d.s);
+    }
+  }
+};
+SideStream* side_stream(cudaStream_t main) {
+  thread_local SidePool pool;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= SidePool::kDevices) return nullptr;
+  SideStream& d = pool.dev[dev];
+  if (d.join != nullptr) return &d;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(main, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return nullptr;
+  if (d.s == nullptr && cudaStreamCreateWithFlags(&d.s, cudaStreamNonBlocking) != cudaSuccess) d.s = nullptr;
+  if (d.s != nullptr && d.fork == nullptr && cudaEventCreateWithFlags(&d.fork, cudaEventDisableTiming) != cudaSuccess)
+    d.fork = nullptr;
+  if (d.fork != nullptr && cudaEventCreateWithFlags(&d.join, cudaEventDisableTiming) != cudaSuccess) d.join = nullptr;
+  return d.join != nullptr ? &d : nullptr;
+}
+
+// Rows from which the next block's digit split runs ahead, during the tail
+// (a single-CTA kernel that leaves the GPU's bandwidth idle).
+constexpr int64_t kAheadMinRows = 1 << 17;
 
 // G = A^T B: from the store (A = store columns [0, na), B = [b0, b0 + nb)) when
 // the factorization keeps its Grams there, else from the segments.
@@ -495,11 +541,34 @@ int step_p(bcgs_qr_s* h, const void* X, int64_t ldx) {
   const Seg Xs = seg(X, ldx, s, h->fp32);
   double* G = h->buf(h->L.G);
   const int ldg = h->L.ldg;
-  TRY(store_put(h, X, ldx, c + s));
+  if (h->x_put) {
+    // X_j's digits went into the store ahead (previous step): only its failure,
+    // if any, is recorded now, where the split itself would have recorded it
+    TRY(launch_merge_status(h->st(), h->st_side(), h->stream));
+    h->x_put = 0;
+  } else {
+    TRY(store_put(h, X, ldx, c + s));
+  }
   if (one_sync)
     TRY(gram_cols(h, c + 2 * s, c, 2 * s, {h->Qseg(c), h->Useg(), Xs}, {h->Useg(), Xs}, G));
   else
     TRY(gram_cols(h, c + s, c, 2 * s, {h->Qseg(c), h->Useg()}, {h->Useg(), Xs}, G));
+  // X_{j+1}'s digits (store columns [c + 2s, c + 3s), which nothing reads before
+  // the next Gram) are split on the side stream while the tail runs; the
+  // factorization's stream waits for them before the projection.  Only for s a
+  // multiple of 16: a split fills its 16-column chunk up with zero digits, so
+  // with s = 8 the split of U_{k+1} at the end of this step would clear them.
+  SideStream* side = nullptr;
+  if (h->next_X != nullptr && h->sgram && s % 16 == 0 && h->m >= kAheadMinRows && h->width(j + 1) == s)
+    side = side_stream(h->stream);
+  if (side != nullptr) {
+    TRY(cudaEventRecord(side->fork, h->stream));
+    TRY(cudaStreamWaitEvent(side->s, side->fork, 0));
+    TRY(launch_qsplit(h->qs(), h->next_X, h->next_ldx, h->Q, h->ldq, h->m, c + 2 * s, s, h->fp32, h->st_side(),
+                      j + 1, side->s));
+    TRY(cudaEventRecord(side->join, side->s));
+    h->x_put = 1;
+  }
   const int nxt = 1 - h->cur;
   TailDesc t;
   memset(&t, 0, sizeof(t));
@@ -542,6 +611,7 @@ int step_p(bcgs_qr_s* h, const void* X, int64_t ldx) {
     t.ldb = h->n_max;
   }
   TRY(launch_tail_1s2s(t, h->st(), h->stream));
+  if (side != nullptr) TRY(cudaStreamWaitEvent(h->stream, side->join, 0));
   if (paired || two_pass) {
     TRY(zero_umax(h));
     StoreProjDesc p;
@@ -786,7 +856,7 @@ int init_handle(bcgs_qr_s* h, int64_t m, int32_t n_max, int32_t s, int variant, 
   h->j = 0;
   h->cur = 0;
   h->finished = 0;
-  TRY(launch_reset_status(h->st(), h->stream));
+  TRY(launch_reset_status(h->st(), h->stream, h->st_side()));
   TRY(launch_zero_lower(n_max, R, ldr, h->stream));
   TRY(launch_zero_u64(h->amaxQ(), n_max, h->stream));
   TRY(launch_zero_u64(h->rowmaxQ(), m, h->stream));
@@ -900,6 +970,34 @@ int copy_streams(CopyStreams** out) {
 
 }  // namespace
 
+namespace {
+// One-call factorization; `ahead`: split each next block of X into the store
+// while the current step's tail runs (on this thread's side stream).
+int factor_impl(int64_t m, int32_t n, int32_t s, int variant, int precision, const void* X, int64_t ldx, void* Q,
+                int64_t ldq, double* R, int32_t ldr, void* workspace, size_t ws_bytes, void* stream, bool ahead) {
+  if (X == nullptr || ldx < m) return BCGS_ERR_INVALID_ARG;
+  // in-place factorization (Q overlapping X) is not supported
+  if (precision >= 0 && precision <= 1 &&
+      overlaps(X, ldx, Q, ldq, m, n, precision == BCGS_FP32_STORAGE ? 4 : 8))
+    return BCGS_ERR_INVALID_ARG;
+  bcgs_qr_s hs;
+  bcgs_qr_s* h = &hs;
+  int rc = init_handle(h, m, n, s, variant, precision, Q, ldq, R, ldr, workspace, ws_bytes, stream);
+  if (rc != BCGS_OK) return rc;
+  const size_t esz = precision == BCGS_FP32_STORAGE ? 4 : 8;
+  const char* Xc = reinterpret_cast<const char*>(X);
+  const int q = (n + s - 1) / s;  // the last block may be ragged
+  for (int k = 0; k < q; ++k) {
+    h->next_X = ahead && k + 1 < q ? Xc + (size_t)(k + 1) * s * ldx * esz : nullptr;
+    h->next_ldx = ldx;
+    rc = step_handle(h, Xc + (size_t)k * s * ldx * esz, ldx);
+    if (rc != BCGS_OK) return rc;
+  }
+  h->next_X = nullptr;
+  return finish_handle(h);
+}
+}  // namespace
+
 extern "C" {
 
 const char* bcgs_status_string(int status) {
@@ -957,26 +1055,11 @@ int bcgs_qr_workspace_size(int64_t m, int32_t n_max, int32_t s, int variant, int
   return BCGS_OK;
 }
 
+
 int bcgs_qr_factor(int64_t m, int32_t n, int32_t s, int variant, int precision, const void* X,
                    int64_t ldx, void* Q, int64_t ldq, double* R, int32_t ldr, void* workspace,
                    size_t ws_bytes, void* stream) {
-  if (X == nullptr || ldx < m) return BCGS_ERR_INVALID_ARG;
-  // in-place factorization (Q overlapping X) is not supported
-  if (precision >= 0 && precision <= 1 &&
-      overlaps(X, ldx, Q, ldq, m, n, precision == BCGS_FP32_STORAGE ? 4 : 8))
-    return BCGS_ERR_INVALID_ARG;
-  bcgs_qr_s hs;
-  bcgs_qr_s* h = &hs;
-  int rc = init_handle(h, m, n, s, variant, precision, Q, ldq, R, ldr, workspace, ws_bytes, stream);
-  if (rc != BCGS_OK) return rc;
-  const size_t esz = precision == BCGS_FP32_STORAGE ? 4 : 8;
-  const char* Xc = reinterpret_cast<const char*>(X);
-  const int q = (n + s - 1) / s;  // the last block may be ragged
-  for (int k = 0; k < q; ++k) {
-    rc = step_handle(h, Xc + (size_t)k * s * ldx * esz, ldx);
-    if (rc != BCGS_OK) return rc;
-  }
-  return finish_handle(h);
+  return factor_impl(m, n, s, variant, precision, X, ldx, Q, ldq, R, ldr, workspace, ws_bytes, stream, true);
 }
 
 int bcgs_row_partition(int64_t m, int32_t nranks, int32_t rank, int64_t* row0, int64_t* rows) {
@@ -1367,8 +1450,9 @@ int bcgs_qr_factor_batched(int32_t count, const bcgs_problem* probs, void* works
     size_t b = 0;
     bcgs_qr_workspace_size(p.m, p.n, p.s, p.variant, p.precision, &b);
     cudaStream_t ls = bs->lane[lane];
-    rc = bcgs_qr_factor(p.m, p.n, p.s, p.variant, p.precision, p.X, p.ldx, p.Q, p.ldq, p.R, p.ldr,
-                        ws + offs[i], align256(b), ls);
+    // no run-ahead: every lane would share this thread's one side stream
+    rc = factor_impl(p.m, p.n, p.s, p.variant, p.precision, p.X, p.ldx, p.Q, p.ldq, p.R, p.ldr, ws + offs[i],
+                     align256(b), ls, false);
     if (rc == BCGS_OK &&
         cudaMemcpyAsync(ws + (size_t)i * sizeof(DevStatus), ws + offs[i], sizeof(DevStatus),
                         cudaMemcpyDeviceToDevice, ls) != cudaSuccess)

@@ -277,7 +277,8 @@ cudaError_t launch_chol(int32_t s, const double* A, int32_t lda, double* R, int3
                         int32_t block, DevStatus* st, cudaStream_t stream);
 cudaError_t launch_zero_lower(int32_t n, double* R, int32_t ldr, cudaStream_t stream);
 cudaError_t launch_zero_u64(unsigned long long* p, int64_t n, cudaStream_t stream);
-cudaError_t launch_reset_status(DevStatus* st, cudaStream_t stream);
+cudaError_t launch_reset_status(DevStatus* st, cudaStream_t stream, DevStatus* st2 = nullptr);
+cudaError_t launch_merge_status(DevStatus* st, DevStatus* side, cudaStream_t stream);
 // A = I (s x s, leading dimension s).
 cudaError_t launch_set_identity(int32_t s, double* A, cudaStream_t stream);
 // One bounded wait that runs out after `cycles`: records BCGS_ERR_TIMEOUT.

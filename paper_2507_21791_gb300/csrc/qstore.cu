@@ -424,62 +424,75 @@ __global__ void __launch_bounds__(Roles<NOUT>::kThreads, 1) proj_store_kernel(St
     if (lane == 0) {
       // one chunk = the 4 KB piece kc & 7 of the 7 digit tiles of store tile (b, kc >> 3):
       // one tensor copy through amap (box {256, 2, 1, 7, 1} of u64 at x = 0), else 7 bulk copies
-      auto issue_copy = [&](int g) {
-        const int slot = g % kStages, kc = g % nch;
-        const int64_t b = blk_of(g / nch);
-        mbar_arrive_expect_tx(&fullA[slot], kAStage);
+      // The loop keeps every index as a counter (chunk, slot, phase, block) that
+      // steps by one: no division by the run-time chunk count on this thread,
+      // whose per-chunk instructions set the pace of the MMAs.
+      // copy side: chunk `issued` = piece ikc of block ibi, into slot islot (phase iph)
+      int issued = 0, islot = 0, iph = 0, ikc = 0, ibi = 0, got = 0;
+      auto issue_copy = [&]() {
+        const int64_t b = blk_of(ibi);
+        mbar_arrive_expect_tx(&fullA[islot], kAStage);
         if (use_amap) {
-          tma_load_5d(Aring + slot * kAStage, &amap, 0, 0, kc & 7, 0, (int32_t)(b * d.qs.ngroups + (kc >> 3)),
-                      &fullA[slot]);
-          return;
-        }
-        const uint8_t* src = d.qs.dig + (size_t)b * d.qs.ngroups * kStoreTileBytes +
-                             (size_t)(kc >> 3) * kStoreTileBytes + (size_t)(kc & 7) * kATileT;
+          tma_load_5d(Aring + islot * kAStage, &amap, 0, 0, ikc & 7, 0,
+                      (int32_t)(b * d.qs.ngroups + (ikc >> 3)), &fullA[islot]);
+        } else {
+          const uint8_t* src = d.qs.dig + (size_t)b * d.qs.ngroups * kStoreTileBytes +
+                               (size_t)(ikc >> 3) * kStoreTileBytes + (size_t)(ikc & 7) * kATileT;
 #pragma unroll
-        for (int t = 0; t < kStoreDigits; ++t)
-          bulk_g2s(Aring + slot * kAStage + t * kATileT, src + (size_t)t * kDigTile, kATileT, &fullA[slot]);
+          for (int t = 0; t < kStoreDigits; ++t)
+            bulk_g2s(Aring + islot * kAStage + t * kATileT, src + (size_t)t * kDigTile, kATileT, &fullA[islot]);
+        }
+        ++issued;
+        if (++islot == kStages) islot = 0, iph ^= 1;
+        if (++ikc == nch) ikc = 0, ++ibi;
       };
-      int issued = 0, got = 0;
-      for (; issued < kStages && issued < total; ++issued) issue_copy(issued);
+      while (issued < kStages && issued < total) issue_copy();
       // Event loop: a slot is refilled as soon as the MMAs of its last chunk are
       // done, and a chunk's MMAs go out as soon as its operands are ready, so all
       // kStages copies stay in flight while the tensor core waits for data.  No
       // progress for kWaitCycles (or an abort elsewhere) ends the loop.
-      int g = 0, need = 0;  // need: 0 = A of chunk g, 1 = its B' digits, 2 = a free accumulator set
+      // MMA side: chunk g = piece kc of block bi, A slot `slot` (phase aph), B slot
+      // `bslot` (phase bph), accumulator group gg (first chunk of its group: kq == 0)
+      int g = 0, slot = 0, aph = 0, bslot = 0, bph = 0, kc = 0, kq = 0, gg = 0;
+      int need = 0;  // 0 = A of chunk g, 1 = its B' digits, 2 = a free accumulator set
       long long idle0 = clock64();
       while (g < total) {
         bool progress = false;
-        const int x = issued - kStages;  // the chunk that last used the slot of chunk `issued`
-        if (issued < total && x < g && mbar_test(&done[x % kStages], (x / kStages) & 1)) {
-          issue_copy(issued);
-          ++issued;
+        // the slot of chunk `issued` last held chunk issued - kStages (< g: its MMAs went out)
+        if (issued < total && issued - kStages < g && mbar_test(&done[islot], iph ^ 1)) {
+          issue_copy();
           progress = true;
         }
-        const int slot = g % kStages, kc = g % nch, bi = g / nch;
-        const int gg = bi * ngrp + kc / kGroupChunks;
-        const bool first = kc % kGroupChunks == 0;
-        const int bslot = g % C::kBRing;
-        if (need == 0 && mbar_test(&fullA[slot], (g / kStages) & 1)) {
+        if (need == 0 && mbar_test(&fullA[slot], aph)) {
           need = 1;
           got = g + 1;
         }
-        if (need == 1 && mbar_test(&bready[bslot], (g / C::kBRing) & 1)) need = 2;
-        if (need == 2 && (!first || gg < 2 || mbar_test(&accfree[gg & 1], ((gg >> 1) - 1) & 1))) {
+        if (need == 1 && mbar_test(&bready[bslot], bph)) need = 2;
+        if (need == 2 && (kq != 0 || gg < 2 || mbar_test(&accfree[gg & 1], ((gg >> 1) - 1) & 1))) {
           tc_after_sync();
           const uint32_t a0 = smem_u32(Aring + slot * kAStage);
           const uint32_t b0 = smem_u32(Bring + bslot * C::kBStage);
           const uint32_t acc = tmem + (uint32_t)((gg & 1) * C::kAcc);
           // digit t of A (t < 7: the store keeps seven) times digit tiles
           // [B_0 .. B_{7-t}] of B' (eight): tile u lands in level t + u
-#pragma unroll 1
+#pragma unroll
           for (int t = 0; t < kStoreDigits; ++t)
             mma_bf16(acc + (uint32_t)(t * NBT), desc_interleave(a0 + t * kATileT, 2048, 128),
                      desc_interleave(b0, 128, 256), idesc_f16(kRows, (kDigits - t) * NBT),
-                     (first && t == 0) ? 0u : 1u);
+                     (kq == 0 && t == 0) ? 0u : 1u);
           mma_commit(&done[slot]);
           mma_commit(&bdone[bslot]);
-          if (kc % kGroupChunks == kGroupChunks - 1 || kc == nch - 1) mma_commit(&accdone[gg & 1]);
+          const bool blk_end = kc == nch - 1;
+          if (kq == kGroupChunks - 1 || blk_end) mma_commit(&accdone[gg & 1]);
           ++g;
+          if (++slot == kStages) slot = 0, aph ^= 1;
+          if (++bslot == C::kBRing) bslot = 0, bph ^= 1;
+          if (blk_end) {
+            kc = 0, kq = 0, ++gg;
+          } else {
+            ++kc;
+            if (++kq == kGroupChunks) kq = 0, ++gg;
+          }
           need = 0;
           progress = true;
         }

@@ -343,10 +343,24 @@ __global__ void zero_u64_words(unsigned long long* p, int64_t n) {
     p[i] = 0ull;
 }
 
-__global__ void reset_status_kernel(DevStatus* st) {
+__global__ void reset_status_kernel(DevStatus* st, DevStatus* st2) {
   if (threadIdx.x == 0) {
     st->code = 0;
     st->block = 0;
+    if (st2 != nullptr) {
+      st2->code = 0;
+      st2->block = 0;
+    }
+  }
+}
+
+// A failure recorded in `side` (work run ahead on another stream) becomes the
+// factorization's failure, unless one is already recorded; `side` is cleared.
+__global__ void merge_status_kernel(DevStatus* st, DevStatus* side) {
+  if (threadIdx.x == 0 && side->code != 0) {
+    set_failure(st, side->code, side->block);
+    side->code = 0;
+    side->block = 0;
   }
 }
 
@@ -430,8 +444,14 @@ cudaError_t launch_set_identity(int32_t s, double* A, cudaStream_t stream) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_reset_status(DevStatus* st, cudaStream_t stream) {
-  reset_status_kernel<<<1, 32, 0, stream>>>(st);
+cudaError_t launch_reset_status(DevStatus* st, cudaStream_t stream, DevStatus* st2) {
+  reset_status_kernel<<<1, 32, 0, stream>>>(st, st2);
+  note_launch(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_merge_status(DevStatus* st, DevStatus* side, cudaStream_t stream) {
+  merge_status_kernel<<<1, 32, 0, stream>>>(st, side);
   note_launch(1);
   return cudaGetLastError();
 }

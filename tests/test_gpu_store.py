@@ -109,3 +109,49 @@ def test_store_path_step_by_step_handle(tensor):
     assert np.array_equal(h.Q.cpu().numpy(), Qf.cpu().numpy())
     assert np.array_equal(h.R.cpu().numpy(), Rf.cpu().numpy())
     h.close()
+
+
+@pytest.mark.parametrize("variant,s,precision", [("bcgsi+p-1s", 16, "fp64"), ("bcgsi+p-2s", 16, "fp64"),
+                                                 ("bcgsi+1s", 16, "fp64"), ("bcgsi+p-2s", 32, "fp64"),
+                                                 ("bcgsi+p-1s", 32, "fp32")])
+def test_run_ahead_split_gives_the_step_by_step_bits(tensor, variant, s, precision):
+    """From 2^17 rows a one-call factorization splits each next block of X into
+    the store on a side stream while the current step's tail runs; the handle,
+    fed one block per call, does not know the next block and splits it in its own
+    step.  Both give the same bits, and the oracle's factors."""
+    import torch
+
+    m, n = 140000, 6 * s
+    X = synth.make_matrix_np(m, n, 1e4, seed=s + 7)
+    Xd = tensor.to_device_colmajor(X, dtype=torch.float32 if precision == "fp32" else None)
+    Qf, Rf, code, _ = tensor.factor(Xd, s, variant)
+    assert code == 0
+    h = tensor.QRHandle(m, n, s, variant, precision)
+    for j in range(n // s):
+        h.step(Xd[:, j * s:(j + 1) * s])
+    h.finish()
+    code, nfin, _ = h.sync()
+    assert code == 0 and nfin == n
+    assert np.array_equal(h.Q.cpu().numpy(), Qf.cpu().numpy())
+    assert np.array_equal(h.R.cpu().numpy(), Rf.cpu().numpy())
+    if precision == "fp64":
+        check_against_oracle(X, s, variant, Qf, Rf)
+
+
+@pytest.mark.parametrize("variant", ["bcgsi+p-1s", "bcgsi+p-2s", "bcgsi+1s"])
+def test_run_ahead_split_reports_nonfinite_in_its_own_block(tensor, variant):
+    """A NaN in block 5 of X is found by the split run ahead during step 4; the
+    failure is recorded where the block's own split would have recorded it, so
+    the status names block 5 as it does step by step."""
+    m, n, s = 140000, 112, 16
+    X = synth.make_matrix_np(m, n, 1e3, seed=3)
+    X[77777, 4 * s + 3] = np.nan
+    Xd = tensor.to_device_colmajor(X)
+    _, _, code, blk = tensor.factor(Xd, s, variant)
+    h = tensor.QRHandle(m, n, s, variant)
+    for j in range(n // s):
+        h.step(Xd[:, j * s:(j + 1) * s])
+    h.finish()
+    hcode, _, hblk = h.sync()
+    assert tensor.STATUS[code] == "nonfinite" and blk == 5
+    assert (hcode, hblk) == (code, blk)
