@@ -54,9 +54,9 @@ TRAFFIC_RATIO = {
     # FP64-pipe Gram, ncu capture at m = 524288, 256 x 32 outputs:
     # (1.208285 GB + 3.823 MB) / (524288 * 288 * 8 B + 304 * 256 * 32 * 8 B)
     "gram_partial_kernel": (1.208285e9 + 3.823104e6) / (524288 * 288 * 8 + 304 * 256 * 32 * 8),
-    # store projection, ncu capture at m = 262144, K = 208, s = 16: (804.460 MB + 58.218 MB) / (8 * 262144 * 256 B);
+    # store projection, ncu capture at m = 262144, K = 208, s = 16: (804.284 MB + 57.819 MB) / (8 * 262144 * 256 B);
     # the seven-digit stream is 14 B per element of Q against 8 algorithmic bytes
-    "proj_store_kernel": (804.460032e6 + 58.218496e6) / (8 * 262144 * 256),
+    "proj_store_kernel": (804.283904e6 + 57.819136e6) / (8 * 262144 * 256),
     # store Gram, ncu capture at m = 262144, na = 224, nb = 32: (825.621 MB + 9.010 MB) / (8 * 262144 * 256 B)
     "gram_store_kernel": (825.621248e6 + 9.010432e6) / (8 * 262144 * 256),
 }
