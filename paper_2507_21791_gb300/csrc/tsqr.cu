@@ -929,13 +929,36 @@ void tsqr_plan(int64_t m, int32_t s, TsqrPlan* p) {
   // Leaf tiles of at most about 8192 doubles (64 KB of shared memory), and no
   // taller than needed for about two tiles per SM of a 152-SM GB300: a tile's
   // Householder runs its columns one after the other on the FP64 pipe of one
-  // SM, so a few tall tiles would leave most SMs idle on small blocks.  At
+  // SM, so a few tall tiles would leave most SMs idle on large blocks.  At
   // least 2s rows (a fan-in of two), a multiple of 32.
-  int64_t mt = round_up(8192 / s, 32);
-  if (mt > 1024) mt = 1024;
+  const int64_t cap = round_up(8192 / s, 32) > 1024 ? 1024 : round_up(8192 / s, 32);
+  int64_t mt = cap;
   const int64_t spread = round_up(ceil_div(m, 304), 32);
   if (mt > spread) mt = spread;
   if (mt < round_up(2 * s, 32)) mt = round_up(2 * s, 32);
+  // On small blocks every tree level is a pair of latency-bound launches (about
+  // 27 + 16 us measured, whatever the node size), so taller leaves pay when they
+  // save a level.  Estimated time of leaf height h (us, measured on GB300: 35 us
+  // for a leaf's chain of reflectors plus its FP64 work at 2 DFMA per cycle and
+  // SM, 2.07 GHz; the whole leaf level at the FP64 rate of 152 SMs; 43 us per
+  // level): the h from the one above up to the cap with the smallest estimate.
+  auto levels_of = [&](int64_t h) {
+    const int64_t f = h / s < 2 ? 2 : h / s;
+    int64_t nodes = ceil_div(m, h);
+    int lv = 0;
+    while (nodes > 1) {
+      nodes = ceil_div(nodes, f);
+      ++lv;
+    }
+    return lv;
+  };
+  auto estimate = [&](int64_t h) {
+    const double one_leaf = 35.0 + (double)h * s * s / 2070.0;
+    const double all_leaves = (double)m * s * s / (152.0 * 2070.0);
+    return (one_leaf > all_leaves ? one_leaf : all_leaves) + 43.0 * levels_of(h);
+  };
+  for (int64_t h = mt + 32; h <= cap && h <= round_up(m, 32); h += 32)
+    if (estimate(h) < estimate(mt)) mt = h;
   if (mt > round_up(m, 32)) mt = round_up(m, 32) < s ? s : round_up(m, 32);
   p->mt = (int32_t)mt;
   int fan = (int)(mt / s);
