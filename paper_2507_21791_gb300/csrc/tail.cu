@@ -59,9 +59,13 @@ __device__ void small_tn(int rows, int s, const double* A, int lda, const double
 
 // Upper Cholesky factor of the s x s matrix M (smem, ld s, upper triangle read)
 // into Rc (smem, ld s).  Returns 0, BCGS_ERR_NOT_SPD or BCGS_ERR_NONFINITE
-// (uniform across the block).
+// (uniform across the block).  The pivot's reciprocal square root r gives
+// R_jj = d r and the row's entries (M_ji - dot) r: one FP64 function call on
+// the serial chain of each column and a multiplication, not a division, per
+// entry (GB300's FP64 divide is a long dependent sequence on a slow pipe).
 __device__ int small_chol(int s, const double* M, double* Rc) {
   __shared__ int code;
+  __shared__ double rinv;
   if (threadIdx.x == 0) code = 0;
   for (int e = threadIdx.x; e < s * s; e += blockDim.x) Rc[e] = 0.0;
   __syncthreads();
@@ -72,15 +76,17 @@ __device__ int small_chol(int s, const double* M, double* Rc) {
       const double d = M[j + j * s] - dot;
       if (!isfinite(d)) code = BCGS_ERR_NONFINITE;
       else if (!(d > 0.0)) code = BCGS_ERR_NOT_SPD;
-      Rc[j + j * s] = code ? 1.0 : sqrt(d);
+      const double r = code ? 1.0 : rsqrt(d);
+      rinv = r;
+      Rc[j + j * s] = code ? 1.0 : d * r;
     }
     __syncthreads();
     if (code) return code;
-    const double rjj = Rc[j + j * s];
+    const double r = rinv;
     for (int i = j + 1 + threadIdx.x; i < s; i += blockDim.x) {
       double dot = 0.0;
       for (int l = 0; l < j; ++l) dot = fma(Rc[l + j * s], Rc[l + i * s], dot);
-      Rc[j + i * s] = (M[j + i * s] - dot) / rjj;
+      Rc[j + i * s] = (M[j + i * s] - dot) * r;
     }
     __syncthreads();
   }
@@ -119,6 +125,10 @@ __device__ void tail_1s2s_body(const TailDesc& d, DevStatus* st, double* dyn) {
     Sd[e] = d.Sd_prev[e];
     d.Yd[e] = Yd[e];
   }
+  // reciprocals of Y_kk's diagonal for the triangular solves below: their
+  // serial chains then multiply instead of dividing
+  __shared__ double rdiag[kMaxS];
+  for (int i = threadIdx.x; i < s; i += blockDim.x) rdiag[i] = 1.0 / Yd[i + i * s];
   __syncthreads();
   // R_{1:k-1,k} = S + Y S_kk ; R_kk = Y_kk S_kk
   for (int e = threadIdx.x; e < (c + s) * s; e += blockDim.x) {
@@ -146,7 +156,7 @@ __device__ void tail_1s2s_body(const TailDesc& d, DevStatus* st, double* dyn) {
       for (int i = s - 1; i >= 0; --i) {
         double x = i == j ? 1.0 : 0.0;
         for (int l = i + 1; l <= j; ++l) x = fma(-Yd[i + l * s], Yi[l + j * s], x);
-        Yi[i + j * s] = i > j ? 0.0 : x / Yd[i + i * s];
+        Yi[i + j * s] = i > j ? 0.0 : x * rdiag[i];
       }
     }
     __syncthreads();
@@ -177,7 +187,7 @@ __device__ void tail_1s2s_body(const TailDesc& d, DevStatus* st, double* dyn) {
     for (int i = 0; i < s; ++i) {
       double dot = 0.0;
       for (int l = 0; l < i; ++l) dot = fma(Yd[l + i * s], Wb[l + j * s], dot);
-      Wb[i + j * s] = (Ms[i + j * s] - dot) / Yd[i + i * s];
+      Wb[i + j * s] = (Ms[i + j * s] - dot) * rdiag[i];
     }
   }
   __syncthreads();
@@ -196,7 +206,7 @@ __device__ void tail_1s2s_body(const TailDesc& d, DevStatus* st, double* dyn) {
       for (int i = s - 1; i >= 0; --i) {
         double x = Wb[i + j * s];
         for (int l = i + 1; l < s; ++l) x = fma(-Yd[i + l * s], Ms[l + j * s], x);
-        Ms[i + j * s] = x / Yd[i + i * s];
+        Ms[i + j * s] = x * rdiag[i];
       }
     }
     __syncthreads();
